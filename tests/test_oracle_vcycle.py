@@ -1,0 +1,216 @@
+"""Pins of the oracle's V-cycle (Sec. 5), level policy (Sec. 5) and Bi-CGSTAB (Sec. 6)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import oracle as o
+from paper_1312_2880_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- dense restatement
+
+
+def _gs_affine(A, n, first):
+    """Dense (G, S) of one Gauss-Seidel sweep u <- G u + S f in the ordering colour `first`, then the other:
+    with D + L the lower triangle and U the strict upper triangle of the permuted matrix,
+    u_new = (D + L)^{-1} (f - U u)."""
+    col = o.red_black_colours(n)
+    perm = np.concatenate([np.nonzero(col == first)[0], np.nonzero(col == 1 - first)[0]])
+    Ap = A[np.ix_(perm, perm)]
+    T = np.tril(Ap)
+    Uu = np.triu(Ap, 1)
+    Ti = sla.solve_triangular(T, np.eye(len(perm)), lower=True)
+    Pm = np.eye(len(perm))[perm]  # Pm @ u = u[perm]
+    return -Pm.T @ Ti @ Uu @ Pm, Pm.T @ Ti @ Pm
+
+
+def _kaczmarz_affine(A, n, order):
+    """Dense (G, S) of one sweep of row projections u <- u + a_p^H (f_p - a_p u) / |a_p|^2, rows in colour order."""
+    N = A.shape[0]
+    G, S = np.eye(N, dtype=complex), np.zeros((N, N), complex)
+    col = o.kaczmarz_colours(n)
+    for c in order:
+        for p in np.nonzero(col == c)[0]:
+            a = A[p]
+            w = np.conj(a) / np.vdot(a, a).real
+            G = G - np.outer(w, a @ G)
+            S = S - np.outer(w, a @ S)
+            S[:, p] += w
+    return G, S
+
+
+def _dense_vcycle(h, level=0):
+    lv = h.levels[level]
+    if lv.smoother == "direct":
+        return np.linalg.inv(lv.A.toarray())
+    A, B = lv.A.toarray(), lv.B.toarray()
+    N = A.shape[0]
+    if lv.smoother == "gs":
+        pre, post = _gs_affine(A, lv.n, 0), _gs_affine(A, lv.n, 1)
+    else:
+        pre, post = _kaczmarz_affine(A, lv.n, (0, 1, 2, 3, 4)), _kaczmarz_affine(A, lv.n, (4, 3, 2, 1, 0))
+    U = np.zeros((N, N), complex)
+    for _ in range(lv.nu):
+        U = pre[0] @ U + pre[1]
+    Kc = _dense_vcycle(h, level + 1)
+    U = U + lv.P.toarray() @ Kc @ lv.R.toarray() @ (np.eye(N) - B @ U)
+    for _ in range(lv.nu):
+        U = post[0] @ U + post[1]
+    return U
+
+
+@pytest.mark.parametrize(
+    "n,levels,ops",
+    [
+        (8, 2, [("M", "gs", "M")]),
+        (8, 2, [("M", "gs", "L")]),
+        (16, 3, [("L", "gs", "L"), ("M", "kaczmarz", "L")]),
+        (16, 3, [("M", "kaczmarz", "M"), ("L", "gs", "L")]),
+    ],
+)
+def test_vcycle_equals_product_of_dense_operators(n, levels, ops):
+    """From a zero guess the V-cycle is linear in f; its matrix equals the composition
+    S_post (u + P K_c R (f - B u)) of S_pre, built here from dense triangular solves and
+    dense row projections, with K_c the next level's operator (the inverse on the coarsest)."""
+    rng = np.random.default_rng(7)
+    kf = 1.1 * n + 0.3 * n * rng.random((n + 1, n + 1))
+    h = o.build_hierarchy(n, kf, k_ref=1.25 * n, variant="hyb", levels=levels, ops=ops)
+    N = (n + 1) ** 2
+    Kv = np.stack([o.vcycle(h, np.eye(N, dtype=complex)[:, j]) for j in range(N)], axis=1)
+    Kd = _dense_vcycle(h)
+    np.testing.assert_allclose(Kv, Kd, rtol=1e-10, atol=1e-10 * np.abs(Kd).max())
+
+
+def test_coarsest_lu_backward_error():
+    n = 8
+    kf = np.full((n + 1, n + 1), 40.0)
+    h = o.build_hierarchy(n, kf, 40.0, "hyb", levels=1)
+    A = h.levels[0].A.toarray()
+    f = np.random.default_rng(0).standard_normal(A.shape[0]) + 0j
+    u = o.vcycle(h, f)
+    assert np.linalg.norm(A @ u - f) <= 1e-13 * np.linalg.norm(A) * np.linalg.norm(u)
+
+
+# --------------------------------------------------------------------------- policy
+
+
+def _sched(h):
+    return [(lv.relax_op, lv.smoother, lv.resid_op) for lv in h.levels]
+
+
+def test_policy_table1_setting():
+    """k = 40, h = 1/64 (Table 1): scales kH = 0.625, 1.25, 2.5, 5. HYB relaxes M at 0.625 and 1.25
+    (Kaczmarz at 1.25), L residuals everywhere, L on the coarsest; SL is M throughout; HLM is L."""
+    kf = I.constant_k(64, 40.0)
+    hyb = _sched(o.build_hierarchy(64, kf, 40.0, "hyb", 4))
+    assert hyb[0] == ("M", "gs", "L") and hyb[1] == ("M", "kaczmarz", "L")
+    assert hyb[2] == ("M", "gs", "L")  # guard: 1 < kH = 2.5 < 2 sqrt 2
+    assert hyb[3] == ("L", "direct", "L")
+    assert _sched(o.build_hierarchy(64, kf, 40.0, "sl", 4)) == [("M", "gs", "M"), ("M", "kaczmarz", "M"), ("M", "gs", "M"), ("M", "direct", "M")]
+    assert _sched(o.build_hierarchy(64, kf, 40.0, "hlm", 4)) == [("L", "gs", "L"), ("L", "kaczmarz", "L"), ("L", "gs", "L"), ("L", "direct", "L")]
+    assert o.build_hierarchy(64, kf, 40.0, "hyb", 4, guard=False).levels[2].relax_op == "L"
+
+
+def test_policy_wedge_n512():
+    wl = I.wedge_n512()
+    h = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    assert [lv.n for lv in h.levels] == [512, 256, 128, 64, 32, 16, 8, 4]
+    ops = [(a[0] + ("k" if a[1] == "kaczmarz" else "")) for a in _sched(h)]
+    assert ops == ["L", "L", "M", "Mk", "M", "L", "L", "L"]
+    assert all(lv.resid_op == "L" for lv in h.levels)
+
+
+def test_policy_fine_hyb_uses_l():
+    """kH = 0.3125 (Table 2 finest scales): HYB relaxes with L."""
+    kf = I.constant_k(128, 40.0)
+    assert o.build_hierarchy(128, kf, 40.0, "hyb", 5).levels[0].relax_op == "L"
+
+
+def test_auto_levels():
+    assert [lv.n for lv in o.build_hierarchy(96, I.constant_k(96, 50.0), 50.0).levels] == [96, 48, 24, 12, 6]
+    assert [lv.n for lv in o.build_hierarchy(64, I.constant_k(64, 20.0), 20.0).levels] == [64, 32, 16, 8]
+
+
+# --------------------------------------------------------------------------- Bi-CGSTAB
+
+
+def _problem(n=32, k=20.0):
+    kf = I.constant_k(n, k)
+    A = o.helmholtz_matrix(n, kf)
+    b = I.centre_source_rhs(n).ravel()
+    return n, kf, A, b
+
+
+def test_bicgstab_with_exact_preconditioner_stops_at_the_first_half_step():
+    n, kf, A, b = _problem()
+    lu = spla.splu(A.tocsc())
+    res = o.bicgstab(A, b, lu.solve, tol=1e-10)
+    assert res.iterations == 0.5 and res.status == "converged"
+    np.testing.assert_allclose(res.x, lu.solve(b), rtol=1e-12)
+
+
+@pytest.mark.parametrize("precond", ["none", "sl_vcycle"])
+def test_bicgstab_iterates_match_an_independent_implementation(precond):
+    """With the same shadow residual (r^ = b, as scipy uses) the iterates equal scipy's Bi-CGSTAB,
+    which is also right-preconditioned with the inner product conjugated in its first argument."""
+    n, kf, A, b = _problem()
+    if precond == "none":
+        K = None
+        M = None
+    else:
+        h = o.build_hierarchy(n, kf, 20.0, "sl")
+        K = lambda v: o.vcycle(h, v)  # noqa: E731
+        M = spla.LinearOperator(A.shape, matvec=K, dtype=complex)
+    mine, ref = [], []
+    o.bicgstab(A, b, K, tol=1e-30, maxit=8, callback=lambda x: mine.append(x.copy()), rhat=b)
+    spla.bicgstab(A, b, M=M, rtol=1e-30, atol=0, maxiter=8, callback=lambda x: ref.append(x.copy()))
+    assert len(mine) == len(ref) == 8
+    for a, r in zip(mine, ref):
+        np.testing.assert_allclose(a, r, rtol=1e-9, atol=1e-9 * np.abs(r).max())
+
+
+def test_bicgstab_solution_matches_direct_solve():
+    n, kf, A, b = _problem(48, 30.0)
+    h = o.build_hierarchy(n, kf, 30.0, "hyb")
+    res = o.bicgstab(A, b, lambda v: o.vcycle(h, v), tol=1e-8, maxit=200)
+    assert res.status == "converged" and res.true_relres <= 1e-8
+    xs = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-5
+    # history: one entry per half step, the last at or below tol
+    assert len(res.history) == int(2 * res.iterations)
+    assert res.history[-1] <= 1e-8
+
+
+def test_shadow_residual_generator_matches_published_vectors():
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64_vectors.json")))
+    for v in g["vectors"]:
+        outs = [int(x, 0) for x in v["outputs"]]
+        u = o.splitmix64_u01(v["seed"], np.arange(len(outs)))
+        np.testing.assert_array_equal(u, [(x >> 11) * 2.0**-53 for x in outs])
+        np.testing.assert_array_equal(I.splitmix64(v["seed"], len(outs)), np.array(outs, dtype=np.uint64))
+    r = o.shadow_residual(5)
+    assert r.dtype == np.complex128 and np.all(np.abs(r.real) <= 0.5) and np.all(np.abs(r.imag) <= 0.5)
+
+
+def test_paper_trends():
+    """Table 1 trends (iteration counts themselves are not pinned): HYB-V needs no more iterations
+    than SL-V, and counts grow with k at fixed kh = 0.625."""
+    t = json.load(open(os.path.join(GOLDEN, "paper_iterations.json")))["table1"]
+    counts = {}
+    for k, n in zip(t["k"][:3:2], t["n"][:3:2]):  # k = 40 and 80
+        kf = I.constant_k(n, k)
+        A = o.helmholtz_matrix(n, kf)
+        b = I.centre_source_rhs(n, 1.0).ravel()
+        for var in ("sl", "hyb"):
+            h = o.build_hierarchy(n, kf, k, var)
+            counts[(k, var)] = o.bicgstab(A, b, lambda v: o.vcycle(h, v), tol=1e-7, maxit=300).iterations
+    assert counts[(40, "hyb")] <= counts[(40, "sl")]
+    assert counts[(80, "hyb")] <= counts[(80, "sl")]
+    assert counts[(80, "sl")] > counts[(40, "sl")] and counts[(80, "hyb")] > counts[(40, "hyb")]
