@@ -1,0 +1,413 @@
+"""Benchmark: solve time to relative residual 1e-6, FP32-preconditioned vs all-FP64 form.
+
+Timed workload (default ``wedge512``): n = 512 (513^2 nodes), k = 100, seeded three-layer wedge
+k * {1.0, 1.5, 0.75}, 8 seeded point sources of 1/h^2, hybrid (HYB-V) hierarchy of 8 levels,
+Bi-CGSTAB to relres 1e-6. A step is one complete solve (every kernel of the hot path) with the
+inputs resident in HBM. Between solves the library rewrites every Krylov vector from the
+right-hand side, so no state carries over; the whole problem (~60 MB) fits in L2, so its
+kernels run from L2 and the HBM roofline is measured on the n = 4096 grid instead
+(``--roofline-workload``, two profiled iterations, no solve): per-kernel device times from
+CUDA events on the library's stream.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead: one full oracle
+solve gives its iteration count, then each step times a bounded sample of whole iterations,
+scaled to the full solve. Multi-GPU (torchrun): every rank solves its own replica (weak
+scaling, no collective on the data path); times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1312_2880_gb300 import inputs as I  # noqa: E402
+
+# Algorithmic (compulsory) HBM bytes per finest-grid node of one launch of each kernel, for the
+# working precision (complex 16/8 B, real 8/4 B) with the FP64 Krylov vectors (16 B). A colour
+# half-sweep touches half the nodes for its own row data but all nodes of the other colour.
+def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
+    c, r = (8, 4) if fp32 else (16, 8)
+    table = {
+        "smooth_restrict": 16 + r + c + c / 4,   # f (FP64 Krylov vector), k h; write u and the coarse f
+        "prolong_smooth": c + c / 4 + 16 + r + 16,  # u_pre, coarse e, f, k h; write the FP64 result
+        "gs_first": 16 / 2 + r / 2 + c,          # f and kh of one colour, write every u
+        "gs_colour": (c + 16 + r + c) / 2,       # other colour's u, own f (FP64 on the finest grid), kh, write
+        "kacz_colour": (5 * c * 2 + 16 + r) / 5,
+        "restrict_residual": c + 16 + r + c / 4,
+        "prolong_add": 2 * c + c / 4,
+        "export": c + 16,
+        "k_update_p": 64,
+        "k_apply_rv": 16 + 8 + 16 + 16,
+        "k_update_s": 48,
+        "k_apply_ts": 16 + 8 + 16 + 16,
+        "k_update_xr": 128,
+        "k_x_half": 48,
+    }
+    return table.get(kernel, 0.0)
+
+
+def kernel_fp64_flops_per_node(kernel: str) -> float:
+    """FP64 floating-point operations per node (an FMA counts 2) of the FP64 Krylov kernels."""
+    table = {"k_update_p": 16, "k_apply_rv": 22 + 8, "k_update_s": 8 + 4, "k_apply_ts": 22 + 12,
+             "k_update_xr": 24 + 12, "k_x_half": 8}
+    return table.get(kernel, 0.0)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (probe on this pool: 1.20 TFLOP/s)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload(name: str):
+    if name == "grf4096":
+        return I.grf_n4096()
+    if name == "wedge512":
+        return I.wedge_n512()
+    if name == "plain64":
+        return I.plain_n64()
+    if name.startswith("grf"):
+        n = int(name[3:])
+        return I.grf_n4096(n=n, k=1000.0 * n / 4096)
+    raise ValueError(name)
+
+
+def dist_setup(n_gpus: int):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], device="cuda", dtype=torch.float64)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
+    import torch
+
+    for _ in range(warmup):
+        P.solve(rhs, tol=tol, maxit=5000)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    infos = []
+    ev[0].record(stream)
+    for s in range(steps):
+        _, info, _ = P.solve(rhs, tol=tol, maxit=5000)
+        ev[s + 1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    per = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    return per, total, infos
+
+
+def time_e2e(P, rhs_host, steps: int, tol: float):
+    import torch
+
+    out = np.empty_like(rhs_host)
+    P.solve_host(rhs_host, tol=tol, maxit=5000, out=out)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        _, info, _ = P.solve_host(rhs_host, tol=tol, maxit=5000, out=out)
+        t.append((time.perf_counter() - t0) * 1e3)
+    return t, out
+
+
+def profile(P, rhs, iterations: int = 2):
+    """{(kernel, level): [ms per launch]} over `iterations` profiled Bi-CGSTAB iterations."""
+    per = {}
+    for name, level, ms in P.profile_iteration(rhs, iterations=iterations):
+        per.setdefault((name, level), []).append(ms)
+    return per
+
+
+def roofline(per, fp32: bool, hbm_peak: float, peak_kind: str, n: int, iterations: int = 2):
+    """The dominant kernel (largest total time) of a profile and its achieved rate."""
+    total = sum(sum(v) for v in per.values())
+    (name, level), times = max(per.items(), key=lambda kv: sum(kv[1]))
+    avg_ms = sum(times) / len(times)
+    nodes = ((n >> level) + 1) ** 2
+    if name.startswith("k_"):
+        flops = kernel_fp64_flops_per_node(name) * nodes
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": name, "level": level, "bound": "alu", "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "nominal GB300 FP64 rate",
+                "hbm_gbs": round(kernel_bytes_per_node(name, fp32) * nodes / (avg_ms * 1e-3) / 1e9, 1)}
+    else:
+        byts = kernel_bytes_per_node(name, fp32) * nodes
+        achieved = byts / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": name, "level": level, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind}
+    roof.update({"traffic": None, "avg_launch_ms": round(avg_ms, 5), "launches": len(times),
+                 "share": round(sum(times) / total, 4)})
+    return roof
+
+
+def sweep_rates(per, fp32: bool, hbm_peak: float, n: int):
+    """Achieved HBM GB/s (algorithmic bytes / device time) of each finest-grid V-cycle kernel."""
+    out = {}
+    for (name, level), times in per.items():
+        if level != 0 or name.startswith("k_") or kernel_bytes_per_node(name, fp32) == 0:
+            continue
+        avg = sum(times) / len(times)
+        gbs = kernel_bytes_per_node(name, fp32) * (n + 1) ** 2 / (avg * 1e-3) / 1e9
+        out[name] = {"gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4), "ms": round(avg, 4)}
+    return out
+
+
+def shares(per):
+    total = sum(sum(v) for v in per.values())
+    top = sorted(per.items(), key=lambda kv: -sum(kv[1]))[:10]
+    return {f"{k[0]}@L{k[1]}": round(sum(v) / total, 4) for k, v in top}
+
+
+def cpu_baseline(wl, iters_full: float, sample_iters: int):
+    """Time the FP64 oracle on this host for `sample_iters` Bi-CGSTAB iterations of the workload."""
+    import oracle as o
+
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    b = wl.rhs.ravel()
+    t0 = time.perf_counter()
+    o.bicgstab(A, b, lambda v: o.vcycle(H, v), tol=1e-300, maxit=sample_iters)
+    dt = time.perf_counter() - t0
+    per_iter_ms = dt * 1e3 / sample_iters
+    return {"value": round(per_iter_ms * iters_full, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_iters} Bi-CGSTAB iterations of the same n={wl.n} solve ({per_iter_ms:.1f} ms each, "
+                      f"numpy/scipy, one thread), scaled by the {iters_full:g} iterations of the FP64 form"}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    world, rank, local = dist_setup(args.gpus)
+    build.build()
+    wl = workload(args.workload)
+    tol = 1e-6
+    rhs = torch.from_numpy(wl.rhs).cuda()
+    hbm_peak, peak_kind = load_peaks()
+    results = {}
+    for prec in ("fp32", "fp64"):
+        P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
+        steps = args.steps if prec == "fp32" else max(1, min(args.steps, args.fp64_steps))
+        warm = args.warmup if prec == "fp32" else max(3, min(args.warmup, 3))
+        with ClockSampler(local) as clk:
+            per, total, infos = time_solves(P, rhs, steps, warm, world, tol)
+        ms = barrier_max(total / steps, world)
+        _, info_chk, _ = P.solve(rhs, tol=tol, maxit=5000)
+        results[prec] = {"ms": ms, "per_step_ms": [round(x, 3) for x in per], "iterations": infos[-1]["iterations"],
+                         "relres_true": infos[-1]["relres_true"], "clocks": clk.summary(), "P": P}
+    P32 = results["fp32"]["P"]
+    per_small = profile(P32, rhs, 2)
+    launches_per_iter = sum(len(v) for k, v in per_small.items() if k[0] != "zero") // 2
+    e2e_t, _ = time_e2e(P32, wl.rhs, max(1, min(args.steps, 3)), tol)
+    e2e_ms = barrier_max(statistics.mean(e2e_t), world)
+    nbytes = 16 * (wl.n + 1) ** 2
+    it32 = results["fp32"]["iterations"]
+    gpu_launches = int(args.steps * ((int(np.ceil(it32)) + 3) * launches_per_iter + 4))
+    for r in results.values():
+        r["P"].close()
+    # HBM roofline on a grid larger than L2: two profiled FP32-preconditioned iterations.
+    rw = workload(args.roofline_workload)
+    Pr = hz.Problem(rw.n, rw.kfield, 0.5, variant=rw.variant, precision="fp32", levels=rw.levels, k_ref=rw.k_ref)
+    rrhs = torch.from_numpy(rw.rhs).cuda()
+    per_big = profile(Pr, rrhs, 2)
+    roof = roofline(per_big, True, hbm_peak, peak_kind, rw.n)
+    roof["workload"] = rw.name
+    sweeps = sweep_rates(per_big, True, hbm_peak, rw.n)
+    big_iter_ms = sum(sum(v) for v in per_big.values()) / 2
+    Pr.close()
+    del rrhs
+    line = {
+        "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
+        "value": round(results["fp32"]["ms"], 3),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(results["fp32"]["ms"], 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 V-cycle / c128 Krylov",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "medium": wl.meta.get("medium", ""),
+                   "levels": wl.levels, "variant": wl.variant, "tol": tol, "rhs": wl.meta.get("rhs", ""),
+                   "l2": "problem fits in L2; HBM rates measured on the roofline workload, larger than L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iterations": it32,
+        "relres_true": results["fp32"]["relres_true"],
+        "solves_per_s": round(world * 1e3 / results["fp32"]["ms"], 3),
+        "fp64_form": {"ms": round(results["fp64"]["ms"], 3), "iterations": results["fp64"]["iterations"],
+                      "relres_true": results["fp64"]["relres_true"],
+                      "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3)},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "roofline": roof,
+        "sweep_hbm": {"workload": rw.name, "kernels": sweeps, "iteration_ms": round(big_iter_ms, 3),
+                      "kernel_share": shares(per_big)},
+        "kernel_share": shares(per_small),
+        "gpu_launches": gpu_launches,
+        "clocks": results["fp32"]["clocks"],
+        "clocks_fp64_form": results["fp64"]["clocks"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, results["fp64"]["iterations"], args.cpu_sample_iters)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as o
+
+    wl = workload(args.workload)
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    b = wl.rhs.ravel()
+    K = lambda v: o.vcycle(H, v)  # noqa: E731
+    # one full oracle solve gives the iteration count (and serves as warm-up)
+    full = o.bicgstab(A, b, K, tol=1e-6, maxit=5000)
+    for _ in range(max(0, args.warmup - 1)):
+        o.bicgstab(A, b, K, tol=1e-300, maxit=args.cpu_sample_iters)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.bicgstab(A, b, K, tol=1e-300, maxit=args.cpu_sample_iters)
+        times.append((time.perf_counter() - t0) * 1e3 / args.cpu_sample_iters)
+    per_iter = statistics.mean(times)
+    value = per_iter * full.iterations
+    line = {
+        "impl": "reference",
+        "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
+        "value": round(value, 1), "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(value, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "levels": wl.levels, "variant": wl.variant},
+        "iterations": full.iterations,
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"each step the first {args.cpu_sample_iters} Bi-CGSTAB iterations of the n={wl.n} "
+                                   f"solve ({per_iter:.1f} ms each), scaled by the oracle's {full.iterations:g} "
+                                   f"iterations to relres 1e-6"},
+        "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wedge512")
+    ap.add_argument("--roofline-workload", default="grf4096")
+    ap.add_argument("--cpu-sample-iters", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

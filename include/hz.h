@@ -1,0 +1,223 @@
+/*
+ * hz.h - C ABI of the GB300 shifted-Laplacian multigrid Helmholtz solver.
+ *
+ * Solves the 2-D Helmholtz problem  Delta u + k(x)^2 u = f  on the unit square with
+ * first-order Sommerfeld boundaries  du/dn - i k u = 0  (arXiv 1312.2880, Sec. 1, Eq. 1),
+ * discretised by the 5-point stencil L^h (Eq. 2), with Bi-CGSTAB (Sec. 6) right-
+ * preconditioned by a multigrid V-cycle whose levels relax with L^H or with the shifted
+ * operator M^H = L^H + i k^2 beta (Eq. 3) as the HLM-V / SL-V / HYB-V variants prescribe
+ * (Sec. 5): red-black Gauss-Seidel on most scales, 5-colour Kaczmarz (Gauss-Seidel on the
+ * normal equations, Sec. 4-5) on the kH ~ 1.25 scale, full weighting, bilinear
+ * interpolation and a dense solve on the coarsest grid.
+ *
+ * Conventions shared by every entry point
+ *  - Grid: (n+1) x (n+1) vertex nodes of [0,1]^2, h = 1/n, boundary nodes are unknowns.
+ *    Node (i, j) sits at (i h, j h); arrays are row-major with i (x) fastest:
+ *    element (i, j) of a level-l array is at index j*(n_l+1) + i, n_l = n / 2^l.
+ *  - Complex vectors are interleaved complex128 (re, im doubles), i.e. the layout of
+ *    C99 double complex, numpy complex128 and torch.complex128.
+ *  - Units are the paper's: rows carry the 1/h^2 factor; u and x are unscaled.
+ *  - Pointers documented "device" must be device memory of the current CUDA device that is
+ *    valid on the problem's stream; "host" pointers are ordinary host memory. The caller owns
+ *    every array it passes; the library never keeps a caller pointer after a call returns.
+ *  - Every call is asynchronous on the problem's stream unless it says it synchronises.
+ *    Calls that return results to host memory synchronise that stream.
+ *  - Errors are returned as hz_status; the message of the last failure on a problem is
+ *    available from hz_last_error. No call aborts, exits or traps on the device.
+ *  - A problem is not thread-safe: one host thread and one stream per problem.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hz_problem hz_problem; /* opaque; created by hz_create_problem, freed by hz_destroy */
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_EINVAL = 1,      /* bad argument (size, pointer, option); nothing was launched */
+  HZ_ENOMEM = 2,      /* arena too small or device allocation refused */
+  HZ_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed; see hz_last_error */
+  HZ_ENOTSETUP = 4,   /* hz_setup_hierarchy has not been called */
+  HZ_EBREAKDOWN = 5,  /* Bi-CGSTAB breakdown (rho, <r^,v> or omega exactly zero) */
+  HZ_EMAXIT = 6,      /* maxit iterations without reaching tol; x holds the last iterate */
+  HZ_ENONFINITE = 7,  /* a NaN or Inf appeared in the Krylov scalars (e.g. non-finite input) */
+  HZ_ETIMEOUT = 8     /* a bounded device-side wait ran out */
+} hz_status;
+
+typedef enum { HZ_BC_SOMMERFELD1 = 0 } hz_bc; /* first-order Sommerfeld rows by ghost elimination */
+
+/* V-cycle variants of Sec. 5. HZ_VAR_SL_PLAIN: M^H with Gauss-Seidel on every level. */
+typedef enum { HZ_VAR_HYB = 0, HZ_VAR_SL = 1, HZ_VAR_HLM = 2, HZ_VAR_SL_PLAIN = 3 } hz_variant;
+
+/* Arithmetic of the V-cycle. The Bi-CGSTAB vectors, recurrences, dot products and the
+ * true-residual check are always complex FP64. */
+typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
+
+typedef enum { HZ_OP_L = 0, HZ_OP_M = 1 } hz_op;
+typedef enum { HZ_SMOOTH_GS = 0, HZ_SMOOTH_KACZMARZ = 1, HZ_SMOOTH_DIRECT = 2 } hz_smoother;
+
+typedef struct {
+  int levels;    /* number of grids; 0 = coarsen while n_l is even and larger than 8 */
+  int variant;   /* hz_variant, default HZ_VAR_HYB */
+  int precision; /* hz_prec, default HZ_PREC_FP64 */
+  int nu_gs;     /* Gauss-Seidel pre and post sweeps, default 1 (Sec. 5) */
+  int nu_kacz;   /* Kaczmarz pre and post sweeps on the kH ~ 1.25 scale, default 4 (Sec. 5) */
+  int guard;     /* 1 (default): an HYB level set to relax with L by the scale bins relaxes with M
+                    when some node has 1 < k H < 2 sqrt(2), where red-black GS on L amplifies
+                    oscillatory error */
+  double k_ref;  /* wavenumber that sets each level's scale c = k_ref H; 0 = mean of k(x) */
+} hz_hierarchy_opts;
+
+typedef struct {
+  int n;        /* n_l */
+  double H;     /* 1 / n_l */
+  int relax_op; /* hz_op used for relaxation, role (A) of Sec. 5 (the direct-solve operator on the coarsest) */
+  int smoother; /* hz_smoother */
+  int resid_op; /* hz_op used for the residual, role (B) of Sec. 5 */
+  int nu;       /* sweeps before and after the coarse-grid correction */
+} hz_level_info;
+
+typedef struct {
+  double iterations;  /* Bi-CGSTAB iterations; a stop after the half step counts .5 (Table 1) */
+  double relres_true; /* |b - A x| / |b| recomputed in FP64 at the stop */
+  int history_len;    /* entries written to history: one per half step */
+  int status;         /* hz_status of the solve */
+  int restarts;       /* restarts after a recurrence residual that the true residual did not confirm */
+} hz_solve_info;
+
+/* Fill opts with the defaults listed in hz_hierarchy_opts. */
+void hz_default_opts(hz_hierarchy_opts* opts);
+
+/* Create a problem for Eq. 1 on the (n+1)^2 grid.
+ *  n       : grid intervals per side, 2 <= n <= 32768.
+ *  k_field : host array of (n+1)^2 doubles, wavenumber k(x) > 0 at each node (copied).
+ *  beta    : shift of M = L + i k^2 beta (Eq. 3); the paper uses 0.5.
+ *  bc      : HZ_BC_SOMMERFELD1.
+ *  out     : receives the new problem.
+ * Returns HZ_EINVAL on a bad size, non-positive or non-finite k, or a null pointer.
+ * Does not touch the device. */
+hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out);
+
+/* Stream for all later work on the problem (a cudaStream_t; NULL = legacy default stream). */
+hz_status hz_set_stream(hz_problem* p, void* cuda_stream);
+
+/* Device bytes hz_setup_hierarchy needs for a grid of n intervals and these options (NULL =
+ * defaults): level arrays, Krylov vectors, the coarsest inverse and the reduction scratch. */
+size_t hz_footprint_bytes(int n, const hz_hierarchy_opts* opts);
+
+/* Build the level hierarchy of Sec. 5 on the device: k injected to each coarse grid,
+ * per-level relaxation/residual operators and smoothers, the dense inverse of the coarsest
+ * operator. arena: device buffer of at least hz_footprint_bytes bytes, aligned to 256 bytes,
+ * owned by the caller and kept alive until hz_destroy; NULL = the library allocates it with
+ * cudaMalloc and frees it in hz_destroy. Synchronises the stream. Calling it again rebuilds. */
+hz_status hz_setup_hierarchy(hz_problem* p, const hz_hierarchy_opts* opts, void* arena, size_t arena_bytes);
+
+/* The level schedule hz_setup_hierarchy builds for this problem and these options (NULL =
+ * defaults): grids, and per level the operators of roles (A) and (B) and the smoother chosen by
+ * the variant's rules (Sec. 5). Computed on the host; touches no device. Writes up to cap
+ * entries to out (host) and returns the number of levels, or -1 on bad arguments. */
+int hz_describe_hierarchy(const hz_problem* p, const hz_hierarchy_opts* opts, hz_level_info* out, int cap);
+
+/* Number of levels (0 before setup) and the description of one level. */
+int hz_num_levels(const hz_problem* p);
+hz_status hz_get_level_info(const hz_problem* p, int level, hz_level_info* info);
+
+/* z = K r: one V-cycle (Sec. 5) from a zero guess on the finest grid. r, z: device,
+ * (n+1)^2 complex128, physical units (z approximates (L^h)^{-1} r). r and z may not alias. */
+hz_status hz_vcycle(hz_problem* p, const double* r, double* z);
+
+/* Solve L^h x = rhs by right-preconditioned Bi-CGSTAB (Sec. 6) from x0 = 0 to
+ * |rhs - L^h x| / |rhs| <= tol, at most maxit iterations.
+ *  rhs, x  : device, (n+1)^2 complex128. x receives the solution (or the last iterate).
+ *  history : host, capacity history_cap doubles (may be NULL/0): relative recurrence residual
+ *            after every half step.
+ *  info    : host, may be NULL.
+ * Returns HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN or HZ_ENONFINITE (x holds the last iterate), or an
+ * argument/CUDA error. Synchronises the stream. */
+hz_status hz_solve(hz_problem* p, const double* rhs, double* x, double tol, int maxit,
+                   double* history, int history_cap, hz_solve_info* info);
+
+/* As hz_solve with rhs and x in host memory: copies rhs to the device and x back. */
+hz_status hz_solve_host(hz_problem* p, const double* rhs_host, double* x_host, double tol, int maxit,
+                        double* history, int history_cap, hz_solve_info* info);
+
+/* ---- Individual steps (the kernels the V-cycle and Bi-CGSTAB run), for testing and for
+ * callers that compose their own cycles. All arrays are device complex128 in physical units
+ * on level `level`'s grid; they run in the hierarchy's precision. ---- */
+
+/* v = A u on the finest grid with A = L^h (op = HZ_OP_L, Eq. 2) or M^h (HZ_OP_M, Eq. 3), FP64. */
+hz_status hz_apply(hz_problem* p, int op, const double* u, double* v);
+
+/* The level's pre-relaxation from a zero guess (nu sweeps of its smoother with its (A)
+ * operator: red first for GS, colours 0..4 for Kaczmarz) giving u, then fc = FW(f - B u)
+ * with its (B) operator (Sec. 5). fc lives on level+1. Not valid on the coarsest level. */
+hz_status hz_level_presmooth(hz_problem* p, int level, const double* f, double* u, double* fc);
+
+/* u = post-relaxation of (u_pre + P ec): bilinear correction from level+1, then nu sweeps
+ * (black first for GS, colours 4..0 for Kaczmarz). Not valid on the coarsest level. */
+hz_status hz_level_postsmooth(hz_problem* p, int level, const double* f, const double* u_pre,
+                              const double* ec, double* u);
+
+/* `sweeps` sweeps of the level's smoother on A u = f starting from the u passed in (in place);
+ * post = 0 uses the pre-relaxation ordering, 1 the post ordering. */
+hz_status hz_level_sweeps(hz_problem* p, int level, const double* f, double* u, int sweeps, int post);
+
+/* u = A_c^{-1} f on the coarsest level (dense inverse of its operator). */
+hz_status hz_coarse_solve(hz_problem* p, const double* f, double* u);
+
+/* ---- Measurement ---- */
+
+/* Kernels of the hot path, as reported by hz_profile_iteration. */
+typedef enum {
+  HZ_K_GS_FIRST = 0,   /* first red-black half sweep from a zero guess */
+  HZ_K_GS_COLOUR,      /* one colour of a red-black Gauss-Seidel sweep */
+  HZ_K_KACZ_COLOUR,    /* one colour of a Kaczmarz sweep */
+  HZ_K_ZERO,           /* zero fill of a Kaczmarz level's guess */
+  HZ_K_RESTRICT,       /* residual with full weighting */
+  HZ_K_PROLONG,        /* bilinear correction */
+  HZ_K_COARSE,         /* dense solve on the coarsest grid */
+  HZ_K_EXPORT,         /* FP32 V-cycle result to the FP64 Krylov vector */
+  HZ_K_UPDATE_P,       /* p = r + beta (p - omega v) */
+  HZ_K_APPLY_RV,       /* v = A y with <r^, v> */
+  HZ_K_UPDATE_S,       /* s = r - alpha v with |s|^2 */
+  HZ_K_X_HALF,         /* x += alpha y after a half-step stop */
+  HZ_K_APPLY_TS,       /* t = A z with <t, s>, <t, t> */
+  HZ_K_UPDATE_XR,      /* x, r updates with <r^, r>, |r|^2 */
+  HZ_K_SMOOTH_RESTRICT, /* fused: GS sweep from a zero guess, residual, full weighting */
+  HZ_K_PROLONG_SMOOTH, /* fused: bilinear correction and GS post-sweep */
+  HZ_K_COUNT
+} hz_kernel;
+
+typedef struct {
+  int kernel;  /* hz_kernel */
+  int level;   /* grid level the launch works on (0 for the Krylov kernels) */
+  float ms;    /* device time between the events recorded around the launch */
+} hz_kernel_time;
+
+/* Device time of every kernel launch in `iterations` Bi-CGSTAB iterations of the solve of
+ * L^h x = rhs (rhs, x: device), measured with CUDA events recorded on the library's stream
+ * around each launch. The iterations are launched one kernel at a time instead of from the
+ * CUDA graph; the arithmetic is the same as hz_solve's first iterations. Writes up to cap
+ * records to out (host) and returns the number of launches, or -1 on error. Synchronises. */
+int hz_profile_iteration(hz_problem* p, const double* rhs, double* x, int iterations, hz_kernel_time* out, int cap);
+
+/* Name of an hz_kernel. */
+const char* hz_kernel_name(int kernel);
+
+/* Last error message on p (never NULL), and a name for a status code. */
+const char* hz_last_error(const hz_problem* p);
+const char* hz_status_string(int status);
+
+/* Free the problem and everything the library allocated for it. Synchronises its stream. */
+void hz_destroy(hz_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

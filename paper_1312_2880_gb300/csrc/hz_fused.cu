@@ -1,0 +1,259 @@
+// Fused V-cycle passes for Gauss-Seidel levels with one pre- and one post-sweep (Sec. 5), each a
+// single pass over the level's arrays through shared-memory tiles.
+//
+// smooth_restrict: red-black sweep from a zero guess (red nodes become f~/d, then black nodes
+//   solve their rows against them), the residual f~ - B u with the level's (B) operator, and
+//   full weighting of that residual onto the coarse grid. A block owns a 2W x 2H' fine tile
+//   whose even nodes are its coarse outputs; it computes red nodes on the tile plus a 3-node
+//   halo, black nodes on a 2-node halo, residuals on a 1-node halo, so every value it writes
+//   equals the unfused sequence's. Reads f and k H once, writes u and the coarse f.
+// prolong_smooth: u = u_pre + P e_c (bilinear), then the post-sweep black first and red second,
+//   on the tile plus a 2-node halo (black on 1, red on 0); writes the result out of place (into
+//   the FP64 Krylov vector on the finest grid).
+// Nodes outside the square never enter a stencil: boundary rows use mirror neighbours (ghost
+// elimination), which lie inside the tile's halo.
+#include <cuda_runtime.h>
+
+#include "hz_common.cuh"
+#include "hz_internal.h"
+
+namespace hz {
+
+namespace {
+
+constexpr int FT = 256;  // threads per block
+
+template <class T>
+struct TileShape;
+template <>
+struct TileShape<float> {
+  static constexpr int W = 64, H = 32;
+};
+template <>
+struct TileShape<double> {
+  static constexpr int W = 64, H = 16;
+};
+
+__device__ __forceinline__ bool in_grid(int i, int j, int n) { return (unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n; }
+
+template <class T>
+__device__ __forceinline__ c2<T> nb_sum(const c2<T>* s, int rw, int c, int r, int i, int j, int n, int gx, int gy) {
+  Nbr b = neighbours(i, j, n);
+  return cadd<T>(cadd<T>(s[r * rw + (b.iw - gx)], s[r * rw + (b.ie - gx)]),
+                 cadd<T>(s[(b.js - gy) * rw + c], s[(b.jn - gy) * rw + c]));
+}
+
+template <class T, class F2>
+__global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__ u, int pu, c2<T>* __restrict__ fc,
+                                                              int pc, const F2* __restrict__ f, int pf,
+                                                              const T* __restrict__ kh, int pk, int n, T bA, T bB,
+                                                              const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
+  constexpr int RW = W + 5, RH = HH + 5, RN = RW * RH, HW = (RW + 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  c2<T>* su = reinterpret_cast<c2<T>*>(smem);
+  c2<T>* sf = su + RN;
+  T* sk = reinterpret_cast<T*>(sf + RN);
+  const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
+  const int gx = x0 - 3, gy = y0 - 3;
+  for (int q = threadIdx.x; q < RN; q += FT) {
+    int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
+    if (in_grid(i, j, n)) {
+      sf[q] = ldc<T>(f, (long long)j * pf + i);
+      sk[q] = kh[(long long)j * pk + i];
+    }
+  }
+  __syncthreads();
+  // red nodes of the whole region: zero neighbours, u = f~ / d
+  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+    int r = q / HW, m = q - r * HW;
+    int j = gy + r;
+    int c = 2 * m + ((0 - gx - j) & 1);
+    int i = gx + c;
+    if (c < RW && in_grid(i, j, n)) {
+      int sides = (i == 0) + (i == n) + (j == 0) + (j == n);
+      su[r * RW + c] = cdiv<T>(sf[r * RW + c], row_diag<T>(sk[r * RW + c], sides, bA));
+    }
+  }
+  __syncthreads();
+  // black nodes one in from the region edge
+  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+    int r = q / HW, m = q - r * HW;
+    int j = gy + r;
+    int c = 2 * m + ((1 - gx - j) & 1);
+    int i = gx + c;
+    if (r >= 1 && r <= RH - 2 && c >= 1 && c <= RW - 2 && in_grid(i, j, n)) {
+      Nbr b = neighbours(i, j, n);
+      c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
+      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+    }
+  }
+  __syncthreads();
+  // write the owned nodes; residual f~ - B u two in from the edge (into sf)
+  for (int q = threadIdx.x; q < RN; q += FT) {
+    int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
+    if (!in_grid(i, j, n)) continue;
+    if (r >= 3 && r < 3 + HH && c >= 3 && c < 3 + W) u[(long long)j * pu + i] = su[q];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < RN; q += FT) {
+    int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
+    if (r >= 2 && r <= RH - 3 && c >= 2 && c <= RW - 3 && in_grid(i, j, n)) {
+      Nbr b = neighbours(i, j, n);
+      c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
+      c2<T> au = cadd<T>(cmul<T>(row_diag<T>(sk[q], b.sides, bB), su[q]), s);
+      sf[q] = csub<T>(sf[q], au);
+    }
+  }
+  __syncthreads();
+  // full weighting onto the owned coarse nodes
+  const int nc = n / 2;
+  for (int q = threadIdx.x; q < (W / 2) * (HH / 2); q += FT) {
+    int J = y0 / 2 + q / (W / 2), I = x0 / 2 + q % (W / 2);
+    if (I > nc || J > nc) continue;
+    c2<T> acc = mk<T>(0, 0);
+#pragma unroll
+    for (int bj = -1; bj <= 1; ++bj) {
+      int rr = reflect(2 * J + bj, n) - gy;
+      c2<T> row = mk<T>(0, 0);
+#pragma unroll
+      for (int ai = -1; ai <= 1; ++ai) {
+        c2<T> v = sf[rr * RW + reflect(2 * I + ai, n) - gx];
+        row = cadd<T>(row, ai == 0 ? cscale<T>(v, (T)2) : v);
+      }
+      acc = cadd<T>(acc, bj == 0 ? cscale<T>(row, (T)2) : row);
+    }
+    fc[(long long)J * pc + I] = cscale<T>(acc, (T)0.25);
+  }
+}
+
+template <class T, class F2, class O2>
+__global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out, int po, const c2<T>* __restrict__ upre,
+                                                             int pu, const c2<T>* __restrict__ ec, int pc,
+                                                             const F2* __restrict__ f, int pf,
+                                                             const T* __restrict__ kh, int pk, int n, T bA,
+                                                             const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
+  constexpr int RW = W + 4, RH = HH + 4, RN = RW * RH, HW = RW / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  c2<T>* su = reinterpret_cast<c2<T>*>(smem);
+  c2<T>* sf = su + RN;
+  T* sk = reinterpret_cast<T*>(sf + RN);
+  const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
+  const int gx = x0 - 2, gy = y0 - 2;
+  for (int q = threadIdx.x; q < RN; q += FT) {
+    int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
+    if (in_grid(i, j, n)) {
+      int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
+      c2<T> e = ec[(long long)J * pc + I];
+      if (oi) e = cadd<T>(e, ec[(long long)J * pc + I + 1]);
+      if (oj) {
+        e = cadd<T>(e, ec[(long long)(J + 1) * pc + I]);
+        if (oi) e = cadd<T>(e, ec[(long long)(J + 1) * pc + I + 1]);
+      }
+      T w = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
+      su[q] = cadd<T>(upre[(long long)j * pu + i], cscale<T>(e, w));
+      sf[q] = ldc<T>(f, (long long)j * pf + i);
+      sk[q] = kh[(long long)j * pk + i];
+    }
+  }
+  __syncthreads();
+  // black nodes one in from the region edge
+  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+    int r = q / HW, m = q - r * HW;
+    int j = gy + r;
+    int c = 2 * m + ((1 - gx - j) & 1);
+    int i = gx + c;
+    if (r >= 1 && r <= RH - 2 && c >= 1 && c <= RW - 2 && in_grid(i, j, n)) {
+      Nbr b = neighbours(i, j, n);
+      c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
+      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+    }
+  }
+  __syncthreads();
+  // red nodes of the owned tile
+  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+    int r = q / HW, m = q - r * HW;
+    int j = gy + r;
+    int c = 2 * m + ((0 - gx - j) & 1);
+    int i = gx + c;
+    if (r >= 2 && r < 2 + HH && c >= 2 && c < 2 + W && in_grid(i, j, n)) {
+      Nbr b = neighbours(i, j, n);
+      c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
+      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < RN; q += FT) {
+    int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
+    if (r >= 2 && r < 2 + HH && c >= 2 && c < 2 + W && in_grid(i, j, n)) stc<T>(out, (long long)j * po + i, su[q]);
+  }
+}
+
+template <class T>
+constexpr size_t sr_smem() {
+  return (size_t)(TileShape<T>::W + 5) * (TileShape<T>::H + 5) * (2 * sizeof(c2<T>) + sizeof(T));
+}
+template <class T>
+constexpr size_t ps_smem() {
+  return (size_t)(TileShape<T>::W + 4) * (TileShape<T>::H + 4) * (2 * sizeof(c2<T>) + sizeof(T));
+}
+
+template <class T, class F2>
+cudaError_t sr_t(void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh, int pk, int n, double bA,
+                 double bB, const int* stop, cudaStream_t s) {
+  constexpr size_t sm = sr_smem<T>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(smooth_restrict_kernel<T, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    attr = true;
+  }
+  constexpr int CW = TileShape<T>::W / 2, CH = TileShape<T>::H / 2;
+  int nc = n / 2;
+  dim3 grid((nc + CW) / CW, (nc + CH) / CH);
+  smooth_restrict_kernel<T, F2><<<grid, FT, sm, s>>>((c2<T>*)u, pu, (c2<T>*)fc, pc, (const F2*)f, pf, (const T*)kh, pk,
+                                                    n, (T)bA, (T)bB, stop);
+  return cudaGetLastError();
+}
+
+template <class T, class F2, class O2>
+cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, int pc, const void* f, int pf,
+                 const void* kh, int pk, int n, double bA, const int* stop, cudaStream_t s) {
+  constexpr size_t sm = ps_smem<T>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(prolong_smooth_kernel<T, F2, O2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    attr = true;
+  }
+  constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
+  dim3 grid((n + W) / W, (n + HH) / HH);
+  prolong_smooth_kernel<T, F2, O2><<<grid, FT, sm, s>>>((O2*)out, po, (const c2<T>*)upre, pu, (const c2<T>*)ec, pc,
+                                                        (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
+                                   const void* kh, int pk, int n, double bA, double bB, const int* stop,
+                                   cudaStream_t s) {
+  if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
+  if (f64_src) return sr_t<float, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
+  return sr_t<float, float2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
+}
+
+cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
+                                  int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
+                                  const int* stop, cudaStream_t s) {
+  if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
+  if (f64_src && out_f64) return ps_t<float, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
+  if (!f64_src && !out_f64) return ps_t<float, float2, float2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hz

@@ -1,0 +1,102 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hz.h"
+
+namespace hz {
+
+// ---------------------------------------------------------------- V-cycle kernel launchers
+// `fp32` selects the working precision of the level arrays (float2/float instead of
+// double2/double). `f64_src` says the right-hand side f is a double2 array even when fp32 is
+// set (the finest level reads the FP64 Krylov vector directly). Pitches are in elements.
+// `stop` is an optional device flag: when it is non-zero the kernel returns at once (used to
+// turn the queued iterations after convergence into no-ops).
+
+cudaError_t launch_gs_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
+                             int pk, int n, int colour, double beta, const int* stop, cudaStream_t s);
+cudaError_t launch_gs_first(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
+                            int n, int colour, double beta, const int* stop, cudaStream_t s);
+cudaError_t launch_kacz_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
+                               int pk, int n, int colour, double beta, const int* stop, cudaStream_t s);
+cudaError_t launch_restrict_residual(bool fp32, void* fc, int pc, const void* u, int pu, const void* f, int pf,
+                                     bool f64_src, const void* kh, int pk, int n, double beta, const int* stop,
+                                     cudaStream_t s);
+cudaError_t launch_prolong_add(bool fp32, void* u, int pu, const void* ec, int pc, int n, const int* stop,
+                               cudaStream_t s);
+cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int pf, const void* ainvT, int nc,
+                                const int* stop, cudaStream_t s);
+// Fused passes for a Gauss-Seidel level with one sweep each way (hz_fused.cu). smooth_restrict
+// writes u (pre-sweep from a zero guess) and fc (coarse right-hand side, h^2-scaled for the
+// coarse level); prolong_smooth writes out = post-sweep(upre + P ec), as double2 when out_f64.
+cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
+                                   const void* kh, int pk, int n, double bA, double bB, const int* stop,
+                                   cudaStream_t s);
+cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
+                                  int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
+                                  const int* stop, cudaStream_t s);
+// dst (precision of fp32, pitch pd) = src (double2, pitch ps) * scale, on an (n+1)^2 grid.
+cudaError_t launch_import(bool fp32, void* dst, int pd, const double2* src, int ps, int n, double scale,
+                          cudaStream_t s);
+// dst (double2, pitch pd) = src (precision of fp32, pitch ps) * scale.
+cudaError_t launch_export(bool fp32, double2* dst, int pd, const void* src, int ps, int n, double scale,
+                          const int* stop, cudaStream_t s);
+cudaError_t launch_inject_kh(bool fp32, void* kh, int pk, const double* k0, int n0, int stride, int nl, double H,
+                             cudaStream_t s);
+// Dense inverse of the coarsest scaled operator, stored transposed in the working precision.
+// work: 2 * m * m double2 scratch, m = (nc+1)^2. status: device int, 0 on success, 1 if singular.
+cudaError_t launch_coarse_setup(bool fp32, void* ainvT, double2* work, const void* kh, int pk, int nc, double beta,
+                                int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- Krylov (FP64)
+
+// Device-resident Bi-CGSTAB scalars and flags. Written by the last block of each reduction.
+struct KState {
+  double2 rho, rho_old, alpha, omega, beta, rv, ts;
+  double bnorm2, tol2, ss, rr, tt, trr;
+  // The first four ints are polled by the host after every iteration.
+  int it;        // current iteration, 1-based
+  int first;     // 1: the next direction update is p = r (start or restart)
+  int done;      // 0 running, 1 recurrence converged, 2 breakdown, 3 non-finite, 4 maxit
+  int half;      // 1: converged after the half step, x += alpha y pending; 2: applied
+  int hist_len;  // entries written to hist (may exceed hist_cap; extra entries are dropped)
+  int hist_cap;
+  int maxit;
+  int iters_x2;  // twice the iteration count at the stop (half steps count .5)
+  unsigned int ticket[16];  // last-block counters, one per reduction kernel
+};
+
+enum { KT_INIT = 0, KT_RV, KT_S, KT_XHALF, KT_TS, KT_XR, KT_TRUE, KT_RESTART };
+
+struct KrylovVecs {
+  double2 *x, *r, *rhat, *p, *v, *s, *t, *y, *z, *tr;
+  const double2* b;
+  const double* kh;  // k h on the finest grid, pitch n+1
+  int n;
+  long long N;
+  double scale_b;  // h^2: the solver works on the h^2-scaled system
+  KState* st;
+  double* partials;  // [8][G]
+  double* hist;
+  int G;  // reduction grid size
+};
+
+cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s);
+cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s);
+// v = A u (scaled by out_scale) on the finest grid in FP64; beta = 0 for L, the shift for M.
+cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, int n, double beta, double out_scale,
+                              cudaStream_t s);
+
+}  // namespace hz

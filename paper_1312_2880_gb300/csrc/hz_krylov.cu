@@ -1,0 +1,436 @@
+// Bi-CGSTAB (van der Vorst 1992) in complex FP64 with the preconditioner applied on the right,
+// as the outer iteration of Sec. 6: every vector update is fused with the dot products it
+// feeds, and the scalars (alpha, omega, beta, rho) are computed on the device by the last
+// block of each reduction, so an iteration needs no host round trip and can be replayed from
+// a CUDA graph.
+//
+// The iteration runs on the h^2-scaled system (h^2 L^h) x = h^2 b; x is unchanged and relative
+// residuals are scale-free. Reductions are deterministic: each thread sums a fixed set of
+// elements in a fixed order, warps and blocks combine in a fixed tree, and the last block adds
+// the per-block partials in block order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hz_common.cuh"
+#include "hz_internal.h"
+
+namespace hz {
+
+namespace {
+
+constexpr int KB = 256;  // threads per block of every Krylov kernel
+
+__device__ __forceinline__ double2 d2add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+// a + s * b (complex s)
+__device__ __forceinline__ double2 d2axpy(double2 a, double2 s, double2 b) {
+  return make_double2(fma(s.x, b.x, fma(-s.y, b.y, a.x)), fma(s.x, b.y, fma(s.y, b.x, a.y)));
+}
+// a - s * b (complex s)
+__device__ __forceinline__ double2 d2axmy(double2 a, double2 s, double2 b) {
+  return make_double2(fma(-s.x, b.x, fma(s.y, b.y, a.x)), fma(-s.x, b.y, fma(-s.y, b.x, a.y)));
+}
+__device__ __forceinline__ double2 d2div(double2 a, double2 b) {
+  double inv = 1.0 / (b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+__device__ __forceinline__ double2 d2mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool fin(double v) { return isfinite(v); }
+__device__ __forceinline__ bool fin2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+}
+
+// Sum over the block in a fixed order; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[KB / 32]) {
+  warp_sum<NV>(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = lane < KB / 32 ? sm[k][lane] : 0.0;
+    warp_sum<NV>(v);
+  }
+}
+
+// Grid-wide sum. Every block stores its partial; the block that arrives last adds all partials
+// in block order and returns true with the totals in `tot` (in every thread of that block).
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket, double (&tot)[NV]) {
+  __shared__ double sm[NV][KB / 32];
+  __shared__ int is_last;
+  __shared__ double res[NV];
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    w[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += KB) w[k] += __ldcg(&partials[k * gridDim.x + b]);
+  }
+  block_sum<NV>(w, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) res[k] = w[k];
+    *ticket = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = res[k];
+  return true;
+}
+
+// (h^2 A y)_e at flat index e of the finest grid (pitch n+1), A = L (beta = 0) or M.
+__device__ __forceinline__ double2 apply_at(const double2* __restrict__ y, const double* __restrict__ kh, int e,
+                                            int n, double beta) {
+  const int w = n + 1;
+  const int j = e / w, i = e - j * w;
+  Nbr b = neighbours(i, j, n);
+  double2 nb = d2add(d2add(y[j * w + b.iw], y[j * w + b.ie]), d2add(y[b.js * w + i], y[b.jn * w + i]));
+  double2 d = row_diag<double>(kh[e], b.sides, beta);
+  return d2add(d2mul(d, y[e]), nb);
+}
+
+__device__ __forceinline__ void hist_push(KState* st, double* hist, double v) {
+  if (st->hist_len < st->hist_cap) hist[st->hist_len] = v;
+  st->hist_len += 1;
+}
+
+#define GRID_STRIDE(e, N) for (int e = blockIdx.x * KB + threadIdx.x; e < (N); e += gridDim.x * KB)
+
+__global__ void shadow_kernel(double2* rhat, long long N, unsigned long long seed) {
+  // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c + 1 of the generator
+  // started from `seed`, top 53 bits mapped to [0, 1); r^_p = (u_2p - 1/2) + i (u_2p+1 - 1/2).
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    double u[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(2 * p + c + 1);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z = z ^ (z >> 31);
+      u[c] = (double)(z >> 11) * 0x1.0p-53;
+    }
+    rhat[p] = make_double2(u[0] - 0.5, u[1] - 0.5);
+  }
+}
+
+// x = 0, r = h^2 b, p = v = 0; |r|^2 and <r^, r> start the iteration.
+__global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 bv = k.b[e];
+    double2 r = make_double2(bv.x * k.scale_b, bv.y * k.scale_b);
+    double2 rh = k.rhat[e];
+    k.r[e] = r;
+    k.x[e] = make_double2(0, 0);
+    k.p[e] = make_double2(0, 0);
+    k.v[e] = make_double2(0, 0);
+    acc[0] = fma(r.x, r.x, fma(r.y, r.y, acc[0]));
+    acc[1] = fma(rh.x, r.x, fma(rh.y, r.y, acc[1]));
+    acc[2] = fma(rh.x, r.y, fma(-rh.y, r.x, acc[2]));
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, k.partials, &k.st->ticket[KT_INIT], tot)) return;
+  if (threadIdx.x == 0) {
+    KState* st = k.st;
+    st->bnorm2 = tot[0];
+    st->tol2 = tol * tol * tot[0];
+    st->rr = tot[0];
+    st->rho = make_double2(tot[1], tot[2]);
+    st->rho_old = make_double2(1, 0);
+    st->alpha = make_double2(1, 0);
+    st->omega = make_double2(1, 0);
+    st->beta = make_double2(0, 0);
+    st->first = 1;
+    st->half = 0;
+    st->it = 1;
+    st->hist_len = 0;
+    st->hist_cap = hist_cap;
+    st->maxit = maxit;
+    st->done = 0;
+    st->iters_x2 = 0;
+    if (!fin(tot[0]) || !fin(tot[1]) || !fin(tot[2])) st->done = 3;
+    else if (tot[0] == 0.0) st->done = 1;
+    else if (tot[1] == 0.0 && tot[2] == 0.0) st->done = 2;
+  }
+}
+
+// p = r (first step after a start or restart) or p = r + beta (p - omega v).
+__global__ void k_update_p_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->done) return;
+  if (st->it > st->maxit) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 4;
+    return;
+  }
+  const int N = (int)k.N;
+  const int first = st->first;
+  const double2 beta = st->beta, omega = st->omega;
+  GRID_STRIDE(e, N) {
+    double2 r = k.r[e];
+    if (first) {
+      k.p[e] = r;
+    } else {
+      double2 q = d2axmy(k.p[e], omega, k.v[e]);
+      k.p[e] = d2axpy(r, beta, q);
+    }
+  }
+}
+
+// v = A y with <r^, v>; alpha = rho / <r^, v>.
+__global__ void k_apply_rv_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->done) return;
+  double acc[2] = {0.0, 0.0};
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 v = apply_at(k.y, k.kh, e, k.n, 0.0);
+    k.v[e] = v;
+    double2 rh = k.rhat[e];
+    acc[0] = fma(rh.x, v.x, fma(rh.y, v.y, acc[0]));
+    acc[1] = fma(rh.x, v.y, fma(-rh.y, v.x, acc[1]));
+  }
+  double tot[2];
+  if (!grid_sum<2>(acc, k.partials, &st->ticket[KT_RV], tot)) return;
+  if (threadIdx.x == 0) {
+    double2 rv = make_double2(tot[0], tot[1]);
+    st->rv = rv;
+    if (!fin2(rv)) {
+      st->done = 3;
+    } else if (rv.x == 0.0 && rv.y == 0.0) {
+      st->done = 2;
+      st->iters_x2 = 2 * (st->it - 1);
+    } else {
+      st->alpha = d2div(st->rho, rv);
+    }
+  }
+}
+
+// s = r - alpha v with |s|^2; stop after the half step when |s| <= tol |b|.
+__global__ void k_update_s_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->done) return;
+  double acc[1] = {0.0};
+  const double2 alpha = st->alpha;
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 s = d2axmy(k.r[e], alpha, k.v[e]);
+    k.s[e] = s;
+    acc[0] = fma(s.x, s.x, fma(s.y, s.y, acc[0]));
+  }
+  double tot[1];
+  if (!grid_sum<1>(acc, k.partials, &st->ticket[KT_S], tot)) return;
+  if (threadIdx.x == 0) {
+    st->ss = tot[0];
+    hist_push(st, k.hist, sqrt(tot[0] / st->bnorm2));
+    if (!fin(tot[0])) {
+      st->done = 3;
+    } else if (tot[0] <= st->tol2) {
+      st->half = 1;
+      st->done = 1;
+      st->iters_x2 = 2 * st->it - 1;
+    }
+  }
+}
+
+// After a half-step stop: x += alpha y, once.
+__global__ void k_x_half_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->half != 1) return;
+  const double2 alpha = st->alpha;
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, k.y[e]); }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int t = atomicAdd(&st->ticket[KT_XHALF], 1u);
+    if (t == gridDim.x - 1) {
+      st->half = 2;
+      st->ticket[KT_XHALF] = 0;
+    }
+  }
+}
+
+// t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>.
+__global__ void k_apply_ts_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->done) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 t = apply_at(k.z, k.kh, e, k.n, 0.0);
+    k.t[e] = t;
+    double2 s = k.s[e];
+    acc[0] = fma(t.x, s.x, fma(t.y, s.y, acc[0]));
+    acc[1] = fma(t.x, s.y, fma(-t.y, s.x, acc[1]));
+    acc[2] = fma(t.x, t.x, fma(t.y, t.y, acc[2]));
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, k.partials, &st->ticket[KT_TS], tot)) return;
+  if (threadIdx.x == 0) {
+    st->ts = make_double2(tot[0], tot[1]);
+    st->tt = tot[2];
+    if (!fin(tot[0]) || !fin(tot[1]) || !fin(tot[2])) {
+      st->done = 3;
+    } else if (tot[2] == 0.0) {
+      st->done = 2;
+      st->iters_x2 = 2 * (st->it - 1);
+    } else {
+      st->omega = make_double2(tot[0] / tot[2], tot[1] / tot[2]);
+    }
+  }
+}
+
+// x += alpha y + omega z, r = s - omega t, with <r^, r> and |r|^2; the next beta.
+__global__ void k_update_xr_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  if (st->done) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const double2 alpha = st->alpha, omega = st->omega;
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 x = d2axpy(d2axpy(k.x[e], alpha, k.y[e]), omega, k.z[e]);
+    k.x[e] = x;
+    double2 r = d2axmy(k.s[e], omega, k.t[e]);
+    k.r[e] = r;
+    double2 rh = k.rhat[e];
+    acc[0] = fma(rh.x, r.x, fma(rh.y, r.y, acc[0]));
+    acc[1] = fma(rh.x, r.y, fma(-rh.y, r.x, acc[1]));
+    acc[2] = fma(r.x, r.x, fma(r.y, r.y, acc[2]));
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, k.partials, &st->ticket[KT_XR], tot)) return;
+  if (threadIdx.x == 0) {
+    st->rr = tot[2];
+    hist_push(st, k.hist, sqrt(tot[2] / st->bnorm2));
+    double2 rho_new = make_double2(tot[0], tot[1]);
+    if (!fin(tot[0]) || !fin(tot[1]) || !fin(tot[2])) {
+      st->done = 3;
+    } else if (omega.x == 0.0 && omega.y == 0.0) {
+      st->done = 2;
+      st->iters_x2 = 2 * st->it;
+    } else if (tot[2] <= st->tol2) {
+      st->done = 1;
+      st->iters_x2 = 2 * st->it;
+    } else if (rho_new.x == 0.0 && rho_new.y == 0.0) {
+      st->done = 2;
+      st->iters_x2 = 2 * st->it;
+    }
+    if (!st->done) {
+      st->rho_old = st->rho;
+      st->rho = rho_new;
+      st->beta = d2mul(d2div(rho_new, st->rho_old), d2div(alpha, omega));
+      st->first = 0;
+      st->it += 1;
+    }
+  }
+}
+
+// tr = h^2 b - A x and |tr|^2, to confirm a recurrence-converged iterate.
+__global__ void k_true_residual_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  double acc[1] = {0.0};
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 ax = apply_at(k.x, k.kh, e, k.n, 0.0);
+    double2 bv = k.b[e];
+    double2 tr = make_double2(fma(bv.x, k.scale_b, -ax.x), fma(bv.y, k.scale_b, -ax.y));
+    k.tr[e] = tr;
+    acc[0] = fma(tr.x, tr.x, fma(tr.y, tr.y, acc[0]));
+  }
+  double tot[1];
+  if (!grid_sum<1>(acc, k.partials, &st->ticket[KT_TRUE], tot)) return;
+  if (threadIdx.x == 0) st->trr = tot[0];
+}
+
+// Restart from the true residual: r = tr, rho = <r^, r>, next step p = r.
+__global__ void k_restart_kernel(KrylovVecs k) {
+  KState* st = k.st;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int N = (int)k.N;
+  GRID_STRIDE(e, N) {
+    double2 r = k.tr[e];
+    k.r[e] = r;
+    double2 rh = k.rhat[e];
+    acc[0] = fma(rh.x, r.x, fma(rh.y, r.y, acc[0]));
+    acc[1] = fma(rh.x, r.y, fma(-rh.y, r.x, acc[1]));
+    acc[2] = fma(r.x, r.x, fma(r.y, r.y, acc[2]));
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, k.partials, &st->ticket[KT_RESTART], tot)) return;
+  if (threadIdx.x == 0) {
+    st->rho = make_double2(tot[0], tot[1]);
+    st->rr = tot[2];
+    st->first = 1;
+    st->half = 0;
+    st->done = 0;
+    st->it += 1;
+    if (tot[0] == 0.0 && tot[1] == 0.0) {
+      st->done = 2;
+      st->iters_x2 = 2 * (st->it - 1);
+    }
+  }
+}
+
+__global__ void apply_fp64_kernel(double2* v, const double2* u, const double* kh, int n, double beta,
+                                  double out_scale) {
+  const int N = (n + 1) * (n + 1);
+  GRID_STRIDE(e, N) {
+    double2 a = apply_at(u, kh, e, n, beta);
+    v[e] = make_double2(a.x * out_scale, a.y * out_scale);
+  }
+}
+
+}  // namespace
+
+#define KLAUNCH(name) name<<<k.G, KB, 0, s>>>(k); return cudaGetLastError();
+
+cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s) {
+  shadow_kernel<<<1024, 256, 0, s>>>(rhat, N, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s) {
+  k_init_kernel<<<k.G, KB, 0, s>>>(k, tol, maxit, hist_cap);
+  return cudaGetLastError();
+}
+cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_p_kernel) }
+cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_apply_rv_kernel) }
+cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_s_kernel) }
+cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_x_half_kernel) }
+cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_apply_ts_kernel) }
+cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_xr_kernel) }
+cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_true_residual_kernel) }
+cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_restart_kernel) }
+
+cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, int n, double beta, double out_scale,
+                              cudaStream_t s) {
+  long long N = (long long)(n + 1) * (n + 1);
+  int G = (int)((N + KB - 1) / KB);
+  if (G > 4096) G = 4096;
+  apply_fp64_kernel<<<G, KB, 0, s>>>(v, u, kh, n, beta, out_scale);
+  return cudaGetLastError();
+}
+
+}  // namespace hz

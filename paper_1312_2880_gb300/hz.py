@@ -1,0 +1,294 @@
+"""Python binding of the C ABI in ``include/hz.h``: argument marshalling only.
+
+Every step of the solver runs in ``libhz.so``; this module only converts between torch/numpy
+arrays and the library's pointers. It raises if the library is missing: there is no fallback.
+Device arrays are ``torch.complex128`` CUDA tensors of shape ``(n+1, n+1)`` indexed ``[j, i]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_double, c_int, c_size_t, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhz.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hz.h")
+
+HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ENOTSETUP, HZ_EBREAKDOWN, HZ_EMAXIT, HZ_ENONFINITE, HZ_ETIMEOUT = range(9)
+VARIANTS = {"hyb": 0, "sl": 1, "hlm": 2, "sl_plain": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+OPS = {"L": 0, "M": 1}
+SMOOTHERS = {0: "gs", 1: "kaczmarz", 2: "direct"}
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
+                ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double)]
+
+
+class LevelInfo(ctypes.Structure):
+    _fields_ = [("n", c_int), ("H", c_double), ("relax_op", c_int), ("smoother", c_int), ("resid_op", c_int),
+                ("nu", c_int)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("kernel", c_int), ("level", c_int), ("ms", ctypes.c_float)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", c_double), ("relres_true", c_double), ("history_len", c_int), ("status", c_int),
+                ("restarts", c_int)]
+
+
+_LIB = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions ``include/hz.h`` declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hz_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libhz.so`` (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1312_2880_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    dp = POINTER(c_double)
+    sig = {
+        "hz_default_opts": (None, [POINTER(Opts)]),
+        "hz_create_problem": (c_int, [c_int, dp, c_double, c_int, POINTER(c_void_p)]),
+        "hz_set_stream": (c_int, [P, c_void_p]),
+        "hz_footprint_bytes": (c_size_t, [c_int, POINTER(Opts)]),
+        "hz_setup_hierarchy": (c_int, [P, POINTER(Opts), c_void_p, c_size_t]),
+        "hz_describe_hierarchy": (c_int, [P, POINTER(Opts), POINTER(LevelInfo), c_int]),
+        "hz_num_levels": (c_int, [P]),
+        "hz_get_level_info": (c_int, [P, c_int, POINTER(LevelInfo)]),
+        "hz_vcycle": (c_int, [P, c_void_p, c_void_p]),
+        "hz_solve": (c_int, [P, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
+        "hz_solve_host": (c_int, [P, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
+        "hz_apply": (c_int, [P, c_int, c_void_p, c_void_p]),
+        "hz_level_presmooth": (c_int, [P, c_int, c_void_p, c_void_p, c_void_p]),
+        "hz_level_postsmooth": (c_int, [P, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "hz_level_sweeps": (c_int, [P, c_int, c_void_p, c_void_p, c_int, c_int]),
+        "hz_coarse_solve": (c_int, [P, c_void_p, c_void_p]),
+        "hz_profile_iteration": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
+        "hz_kernel_name": (ctypes.c_char_p, [c_int]),
+        "hz_last_error": (ctypes.c_char_p, [P]),
+        "hz_status_string": (ctypes.c_char_p, [c_int]),
+        "hz_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _ptr(t) -> c_void_p:
+    import torch
+
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128, (
+        "expected a contiguous complex128 CUDA tensor")
+    return c_void_p(t.data_ptr())
+
+
+def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0) -> Opts:
+    o = Opts()
+    lib().hz_default_opts(byref(o))
+    o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
+    o.nu_gs, o.nu_kacz, o.guard, o.k_ref = nu_gs, nu_kacz, int(bool(guard)), float(k_ref)
+    return o
+
+
+def footprint_bytes(n: int, **opts) -> int:
+    return int(lib().hz_footprint_bytes(n, byref(make_opts(**opts))))
+
+
+def _level_dict(li: LevelInfo) -> dict:
+    inv = {v: k for k, v in OPS.items()}
+    return {"n": li.n, "H": li.H, "relax_op": inv[li.relax_op], "smoother": SMOOTHERS[li.smoother],
+            "resid_op": inv[li.resid_op], "nu": li.nu}
+
+
+def describe_hierarchy(n: int, kfield, beta: float = 0.5, **opts) -> list:
+    """Level schedule the library builds for this medium and these options, computed on the host
+    (no GPU needed)."""
+    L = lib()
+    k = np.ascontiguousarray(kfield, dtype=np.float64)
+    h = c_void_p()
+    st = L.hz_create_problem(int(n), k.ctypes.data_as(POINTER(c_double)), float(beta), 0, byref(h))
+    if st != HZ_OK:
+        raise HzError(st, "hz_create_problem failed")
+    try:
+        out = (LevelInfo * 32)()
+        cnt = L.hz_describe_hierarchy(h, byref(make_opts(**opts)), out, 32)
+        if cnt < 0:
+            raise HzError(HZ_EINVAL, "invalid hierarchy options")
+        return [_level_dict(out[i]) for i in range(cnt)]
+    finally:
+        L.hz_destroy(h)
+
+
+class Problem:
+    """One Helmholtz problem (grid, medium, hierarchy) resident on the current CUDA device.
+
+    Device memory is a single ``torch.uint8`` arena of :func:`footprint_bytes` bytes; work is
+    ordered on torch's current stream.
+    """
+
+    def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
+                 nu_kacz=4, guard=True, k_ref=0.0, arena=None):
+        import torch
+
+        L = lib()
+        self.n = int(n)
+        k = np.ascontiguousarray(kfield, dtype=np.float64)
+        if k.shape != (n + 1, n + 1):
+            raise ValueError("kfield must have shape (n+1, n+1)")
+        h = c_void_p()
+        st = L.hz_create_problem(self.n, k.ctypes.data_as(POINTER(c_double)), float(beta), 0, byref(h))
+        if st != HZ_OK:
+            raise HzError(st, "hz_create_problem failed")
+        self._h = h
+        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref)
+        self.precision = precision
+        self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
+        if self.bytes == 0:
+            raise HzError(HZ_EINVAL, "invalid grid/level combination")
+        self.arena = arena if arena is not None else torch.empty(self.bytes, dtype=torch.uint8, device="cuda")
+        self._stream()
+        self._check(L.hz_setup_hierarchy(h, byref(self.opts), c_void_p(self.arena.data_ptr()), self.bytes))
+
+    # ------------------------------------------------------------------ plumbing
+    def _stream(self):
+        import torch
+
+        lib().hz_set_stream(self._h, c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def _check(self, st: int, ok=(HZ_OK,)):
+        if st not in ok:
+            raise HzError(st, lib().hz_last_error(self._h).decode())
+        return st
+
+    def _empty(self, level: int = 0):
+        import torch
+
+        m = (self.n >> level) + 1
+        return torch.empty((m, m), dtype=torch.complex128, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hz_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ queries
+    @property
+    def num_levels(self) -> int:
+        return int(lib().hz_num_levels(self._h))
+
+    def level_info(self, level: int) -> dict:
+        li = LevelInfo()
+        self._check(lib().hz_get_level_info(self._h, level, byref(li)))
+        return _level_dict(li)
+
+    def schedule(self) -> list:
+        return [self.level_info(l) for l in range(self.num_levels)]
+
+    # ------------------------------------------------------------------ solver
+    def solve(self, rhs, tol: float = 1e-6, maxit: int = 1000, x=None, history_cap: int = 4096,
+              allow_fail: bool = False):
+        """Bi-CGSTAB solve of L^h x = rhs on the device. Returns (x, info dict, history ndarray)."""
+        self._stream()
+        x = self._empty() if x is None else x
+        hist = np.zeros(max(1, history_cap), dtype=np.float64)
+        info = SolveInfo()
+        st = lib().hz_solve(self._h, _ptr(rhs), _ptr(x), tol, maxit, hist.ctypes.data_as(POINTER(c_double)),
+                            history_cap, byref(info))
+        ok = (HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN, HZ_ENONFINITE) if allow_fail else (HZ_OK,)
+        self._check(st, ok)
+        d = {"iterations": info.iterations, "relres_true": info.relres_true, "status": st,
+             "restarts": info.restarts}
+        return x, d, hist[: info.history_len].copy()
+
+    def solve_host(self, rhs: np.ndarray, tol: float = 1e-6, maxit: int = 1000, history_cap: int = 4096,
+                   out: np.ndarray | None = None):
+        """As :meth:`solve` with host (numpy complex128) input and output."""
+        self._stream()
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        x = np.empty_like(rhs) if out is None else out
+        hist = np.zeros(max(1, history_cap), dtype=np.float64)
+        info = SolveInfo()
+        st = lib().hz_solve_host(self._h, c_void_p(rhs.ctypes.data), c_void_p(x.ctypes.data), tol, maxit,
+                                 hist.ctypes.data_as(POINTER(c_double)), history_cap, byref(info))
+        self._check(st)
+        return x, {"iterations": info.iterations, "relres_true": info.relres_true, "status": st,
+                   "restarts": info.restarts}, hist[: info.history_len].copy()
+
+    def profile_iteration(self, rhs, iterations: int = 1, x=None) -> list:
+        """Per-launch device times (ms) of `iterations` Bi-CGSTAB iterations: [(kernel, level, ms)]."""
+        self._stream()
+        x = self._empty() if x is None else x
+        cap = 4096
+        out = (KernelTime * cap)()
+        cnt = lib().hz_profile_iteration(self._h, _ptr(rhs), _ptr(x), iterations, out, cap)
+        if cnt < 0:
+            raise HzError(HZ_ECUDA, lib().hz_last_error(self._h).decode())
+        return [(lib().hz_kernel_name(out[q].kernel).decode(), out[q].level, float(out[q].ms)) for q in range(min(cnt, cap))]
+
+    def vcycle(self, r):
+        self._stream()
+        z = self._empty()
+        self._check(lib().hz_vcycle(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def apply(self, u, op: str = "L"):
+        self._stream()
+        v = self._empty()
+        self._check(lib().hz_apply(self._h, OPS[op], _ptr(u), _ptr(v)))
+        return v
+
+    def level_presmooth(self, level: int, f):
+        self._stream()
+        u, fc = self._empty(level), self._empty(level + 1)
+        self._check(lib().hz_level_presmooth(self._h, level, _ptr(f), _ptr(u), _ptr(fc)))
+        return u, fc
+
+    def level_postsmooth(self, level: int, f, u_pre, ec):
+        self._stream()
+        u = self._empty(level)
+        self._check(lib().hz_level_postsmooth(self._h, level, _ptr(f), _ptr(u_pre), _ptr(ec), _ptr(u)))
+        return u
+
+    def level_sweeps(self, level: int, f, u, sweeps: int = 1, post: bool = False):
+        self._stream()
+        out = u.clone()
+        self._check(lib().hz_level_sweeps(self._h, level, _ptr(f), _ptr(out), sweeps, int(post)))
+        return out
+
+    def coarse_solve(self, f):
+        self._stream()
+        u = self._empty(self.num_levels - 1)
+        self._check(lib().hz_coarse_solve(self._h, _ptr(f), _ptr(u)))
+        return u

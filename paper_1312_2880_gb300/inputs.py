@@ -155,7 +155,8 @@ class Workload:
 def plain_n64() -> Workload:
     """n = 64, constant k = 20, centre source 1/h^2, all-M^h GS V(1,1), 4 levels."""
     n, k = 64, 20.0
-    return Workload("plain_n64_k20", n, k, constant_k(n, k), centre_source_rhs(n), variant="sl_plain", levels=4)
+    return Workload("plain_n64_k20", n, k, constant_k(n, k), centre_source_rhs(n), variant="sl_plain", levels=4,
+                    meta={"medium": "constant k", "rhs": "centre point source 1/h^2"})
 
 
 def wedge_n512(seed: int = SEED_BASE + 2) -> Workload:
@@ -163,7 +164,8 @@ def wedge_n512(seed: int = SEED_BASE + 2) -> Workload:
     n, k = 512, 100.0
     kf = wedge_k(n, k, seed)
     rhs = point_source_rhs(n, random_interior_nodes(n, 8, seed + 1))
-    return Workload("wedge_n512_k100", n, k, kf, rhs, variant="hyb", levels=8)
+    return Workload("wedge_n512_k100", n, k, kf, rhs, variant="hyb", levels=8,
+                    meta={"medium": "three-layer wedge k*{1.0,1.5,0.75}", "rhs": "8 seeded point sources 1/h^2"})
 
 
 def grf_n4096(seed: int = SEED_BASE + 3, n: int = 4096, k: float = 1000.0) -> Workload:
@@ -173,7 +175,8 @@ def grf_n4096(seed: int = SEED_BASE + 3, n: int = 4096, k: float = 1000.0) -> Wo
     """
     kf = grf_k(n, k, seed)
     levels = max(2, int(round(math.log2(n))) - 2)
-    return Workload(f"grf_n{n}_k{k:g}", n, k, kf, centre_source_rhs(n), variant="hyb", levels=levels)
+    return Workload(f"grf_n{n}_k{k:g}", n, k, kf, centre_source_rhs(n), variant="hyb", levels=levels,
+                    meta={"medium": "k(1+0.3 g), g Gaussian random field", "rhs": "centre point source 1/h^2"})
 
 
 BATCH_SPECS = ((50.0, 96), (100.0, 192), (200.0, 384), (300.0, 576))

@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared function, validates
+arguments, sizes its arena, and computes the same level schedule as the oracle's policy."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1312_2880_gb300 import inputs as I
+
+hz = pytest.importorskip("paper_1312_2880_gb300.hz")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1312_2880_gb300 import build
+
+    build.build()
+    return hz.lib()
+
+
+def test_every_declared_function_is_exported(L):
+    names = hz.header_functions()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_create_problem_validates_arguments(L):
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    k = np.full((9, 9), 10.0)
+    assert L.hz_create_problem(8, k.ctypes.data_as(dp), 0.5, 0, ctypes.byref(h)) == hz.HZ_OK
+    L.hz_destroy(h)
+    assert L.hz_create_problem(1, k.ctypes.data_as(dp), 0.5, 0, ctypes.byref(h)) == hz.HZ_EINVAL
+    assert L.hz_create_problem(8, k.ctypes.data_as(dp), 0.5, 7, ctypes.byref(h)) == hz.HZ_EINVAL
+    bad = k.copy()
+    bad[3, 3] = np.nan
+    assert L.hz_create_problem(8, bad.ctypes.data_as(dp), 0.5, 0, ctypes.byref(h)) == hz.HZ_EINVAL
+    bad[3, 3] = -1.0
+    assert L.hz_create_problem(8, bad.ctypes.data_as(dp), 0.5, 0, ctypes.byref(h)) == hz.HZ_EINVAL
+    assert L.hz_status_string(hz.HZ_EMAXIT) == b"HZ_EMAXIT"
+
+
+def test_footprint(L):
+    fp64 = hz.footprint_bytes(4096, levels=10, precision="fp64")
+    fp32 = hz.footprint_bytes(4096, levels=10, precision="fp32")
+    N = 4097**2
+    # 11 complex FP64 vectors + FP64 k h, plus the level arrays
+    assert fp64 > 11 * 16 * N and fp32 > 11 * 16 * N
+    assert fp32 < fp64 < 20 * 16 * N
+    assert hz.footprint_bytes(64, levels=9) == 0  # 64 / 2^8 < 2
+    assert hz.footprint_bytes(100, levels=2) == 0  # coarsest 51^2 > 1089 unknowns
+
+
+def _oracle_schedule(wl, variant=None, levels=None, k_ref=None):
+    h = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref if k_ref is None else k_ref, variant or wl.variant,
+                          wl.levels if levels is None else levels)
+    return [(lv.n, lv.relax_op, {"gs": "gs", "kaczmarz": "kaczmarz", "direct": "direct"}[lv.smoother], lv.resid_op)
+            for lv in h.levels]
+
+
+def _lib_schedule(wl, variant=None, levels=None):
+    sch = hz.describe_hierarchy(wl.n, wl.kfield, variant=variant or wl.variant,
+                                levels=wl.levels if levels is None else levels, k_ref=wl.k_ref)
+    return [(d["n"], d["relax_op"], d["smoother"], d["resid_op"]) for d in sch]
+
+
+@pytest.mark.parametrize("variant", ["hyb", "sl", "hlm", "sl_plain"])
+def test_schedule_matches_oracle_policy(L, variant):
+    cases = [I.plain_n64(), I.wedge_n512(), I.grf_n4096(n=512, k=125.0)]
+    cases += I.batch_problems(rhs_per_k=1)
+    for wl in cases:
+        assert _lib_schedule(wl, variant) == _oracle_schedule(wl, variant), (wl.name, variant)
+
+
+def test_schedule_of_table1_setting(L):
+    kf = I.constant_k(64, 40.0)
+    sch = hz.describe_hierarchy(64, kf, variant="hyb", levels=4, k_ref=40.0)
+    assert [(d["relax_op"], d["smoother"], d["nu"]) for d in sch] == [
+        ("M", "gs", 1), ("M", "kaczmarz", 4), ("M", "gs", 1), ("L", "direct", 0)]

@@ -1,0 +1,304 @@
+"""CUDA path vs the FP64 oracle through the C ABI, element by element on the same seeded inputs.
+
+Tolerances (relative to the largest oracle entry): 1e-12 for each FP64 step (one sweep, one
+restriction, one correction), 1e-11 for a whole FP64 V-cycle, and, for Bi-CGSTAB iterates, max(1e-10, 10 s)
+where s is the oracle's own spread: how far its iterate moves when b is rescaled by one ulp
+(Bi-CGSTAB on these indefinite systems amplifies rounding, by up to 1e10 on long solves, so no
+two FP64 implementations agree to 1e-10 there). This is applied after a fixed number of
+iterations (8, with the residual history) and to converged solutions, whose iteration counts
+must agree within the oracle's own spread (at least one iteration). FP32 V-cycles are compared at 2e-5 (single-precision
+rounding through a few dozen dependent operations) and FP32-preconditioned solves must reach the
+tolerance on the FP64 true residual.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1312_2880_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1312_2880_gb300 import build
+
+    build.build()
+
+
+def hzmod():
+    from paper_1312_2880_gb300 import hz
+
+    return hz
+
+
+def rel(a, b):
+    a = a.cpu().numpy() if hasattr(a, "cpu") else a
+    return float(np.abs(np.asarray(a).ravel() - np.asarray(b).ravel()).max() / np.abs(b).max())
+
+
+def dev(x, n=None):
+    x = np.asarray(x, dtype=np.complex128)
+    if n is not None:
+        x = x.reshape(n + 1, n + 1)
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rand_c(shape, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def pair(wl, precision="fp64", variant=None, levels=None):
+    var = variant or wl.variant
+    lev = wl.levels if levels is None else levels
+    P = hzmod().Problem(wl.n, wl.kfield, 0.5, variant=var, precision=precision, levels=lev, k_ref=wl.k_ref)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, var, lev)
+    assert [(d["relax_op"], d["smoother"]) for d in P.schedule()] == [(lv.relax_op, lv.smoother) for lv in H.levels]
+    return P, H
+
+
+def small_wedge(n=128, k=25.0):
+    kf = I.wedge_k(n, k, I.SEED_BASE + 2)
+    rhs = I.point_source_rhs(n, I.random_interior_nodes(n, 3, 11))
+    return I.Workload(f"wedge_n{n}", n, k, kf, rhs, variant="hyb", levels=0)
+
+
+def ragged_grf(n=96, k=50.0):
+    kf = I.grf_k(n, k, 17)
+    return I.Workload(f"grf_n{n}", n, k, kf, I.centre_source_rhs(n), variant="hyb", levels=0)
+
+
+WORKLOADS = {"plain64": I.plain_n64, "wedge128": small_wedge, "grf96": ragged_grf}
+
+
+# --------------------------------------------------------------------------- single steps
+
+
+@pytest.mark.parametrize("op", ["L", "M"])
+def test_apply_operator(op):
+    wl = small_wedge()
+    P, H = pair(wl)
+    u = rand_c((wl.n + 1) ** 2, 1)
+    A = o.helmholtz_matrix(wl.n, wl.kfield, 0.5 if op == "M" else 0.0)
+    got = P.apply(dev(u, wl.n), op)
+    assert rel(got, A @ u) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_presmooth_and_restriction_each_level(name):
+    wl = WORKLOADS[name]()
+    P, H = pair(wl)
+    for l, lv in enumerate(H.levels[:-1]):
+        f = rand_c((lv.n + 1) ** 2, 10 + l)
+        u_ref = o.helmholtz.relax(lv, f, np.zeros_like(f), post=False)
+        fc_ref = lv.R @ (f - lv.B @ u_ref)
+        u, fc = P.level_presmooth(l, dev(f, lv.n))
+        assert rel(u, u_ref) <= 1e-12, (name, l, lv.smoother)
+        assert rel(fc, fc_ref) <= 1e-12, (name, l, lv.smoother)
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_correction_and_postsmooth_each_level(name):
+    wl = WORKLOADS[name]()
+    P, H = pair(wl)
+    for l, lv in enumerate(H.levels[:-1]):
+        nc = H.levels[l + 1].n
+        f = rand_c((lv.n + 1) ** 2, 20 + l)
+        u0 = rand_c((lv.n + 1) ** 2, 30 + l)
+        ec = rand_c((nc + 1) ** 2, 40 + l)
+        ref = o.helmholtz.relax(lv, f, u0 + lv.P @ ec, post=True)
+        got = P.level_postsmooth(l, dev(f, lv.n), dev(u0, lv.n), dev(ec, nc))
+        assert rel(got, ref) <= 1e-12, (name, l, lv.smoother)
+
+
+@pytest.mark.parametrize("sweeps", [1, 3])
+@pytest.mark.parametrize("post", [False, True])
+def test_sweeps_from_a_nonzero_guess(sweeps, post):
+    wl = small_wedge()
+    P, H = pair(wl)
+    for l, lv in enumerate(H.levels[:-1]):
+        f = rand_c((lv.n + 1) ** 2, 50 + l)
+        u = rand_c((lv.n + 1) ** 2, 60 + l)
+        ref = u.copy()
+        for _ in range(sweeps):
+            if lv.smoother == "gs":
+                ref = o.rb_gs_sweep(lv, f, ref, first=1 if post else 0)
+            else:
+                ref = o.kaczmarz_sweep(lv, f, ref, order=(4, 3, 2, 1, 0) if post else (0, 1, 2, 3, 4))
+        got = P.level_sweeps(l, dev(f, lv.n), dev(u, lv.n), sweeps, post)
+        assert rel(got, ref) <= 1e-12 * sweeps, (l, lv.smoother)
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_coarse_solve(name):
+    wl = WORKLOADS[name]()
+    P, H = pair(wl)
+    lv = H.levels[-1]
+    f = rand_c((lv.n + 1) ** 2, 70)
+    ref = o.vcycle(H, f, len(H.levels) - 1)
+    assert rel(P.coarse_solve(dev(f, lv.n)), ref) <= 1e-12
+
+
+# --------------------------------------------------------------------------- V-cycle and solve
+
+
+@pytest.mark.parametrize("variant", ["hyb", "sl", "hlm", "sl_plain"])
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_vcycle_fp64(name, variant):
+    wl = WORKLOADS[name]()
+    P, H = pair(wl, variant=variant)
+    r = rand_c((wl.n + 1) ** 2, 80)
+    assert rel(P.vcycle(dev(r, wl.n)), o.vcycle(H, r)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_vcycle_fp32_against_fp64_oracle(name):
+    wl = WORKLOADS[name]()
+    P, H = pair(wl, precision="fp32")
+    r = rand_c((wl.n + 1) ** 2, 81)
+    err = rel(P.vcycle(dev(r, wl.n)), o.vcycle(H, r))
+    assert err <= 2e-5, err
+
+
+def _oracle_solve(wl, tol, maxit=1000, b_scale=1.0):
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    r = o.bicgstab(A, wl.rhs.ravel() * b_scale, lambda v: o.vcycle(H, v), tol=tol, maxit=maxit)
+    r.x = r.x / b_scale
+    return A, r
+
+
+def _oracle_spread(wl, tol, ref, maxit=1000):
+    """The oracle's own sensitivity: its iterate and iteration count with b rescaled by one ulp."""
+    _, alt = _oracle_solve(wl, tol, maxit=maxit, b_scale=1.0 + 2.0**-52)
+    hs = np.abs(np.array(alt.history[: len(ref.history)]) / np.array(ref.history) - 1).max()
+    return rel(alt.x, ref.x), abs(alt.iterations - ref.iterations), float(hs)
+
+
+@pytest.mark.parametrize("name", ["plain64", "wedge128", "grf96"])
+def test_first_iterations_match_oracle(name):
+    wl = WORKLOADS[name]()
+    A, ref = _oracle_solve(wl, 1e-30, maxit=8)
+    spread_x, _, spread_h = _oracle_spread(wl, 1e-30, ref, maxit=8)
+    P, _ = pair(wl)
+    x, info, hist = P.solve(dev(wl.rhs), tol=1e-30, maxit=8, allow_fail=True)
+    assert info["iterations"] == 8 and len(hist) == 16
+    assert rel(x, ref.x) <= max(1e-10, 10 * spread_x)
+    np.testing.assert_allclose(hist, ref.history, rtol=max(1e-10, 10 * spread_h))
+
+
+@pytest.mark.parametrize("name", ["plain64", "wedge128", "grf96"])
+def test_solve_fp64_matches_oracle(name):
+    wl = WORKLOADS[name]()
+    A, ref = _oracle_solve(wl, 1e-6)
+    spread_x, spread_it, _ = _oracle_spread(wl, 1e-6, ref)
+    P, _ = pair(wl)
+    x, info, hist = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+    assert abs(info["iterations"] - ref.iterations) <= max(1.0, 2 * spread_it)
+    assert rel(x, ref.x) <= max(1e-10, 10 * spread_x)
+    assert info["relres_true"] <= 1e-6
+    assert abs(info["relres_true"] - o.true_relres(A, wl.rhs.ravel(), x.cpu().numpy().ravel())) <= 1e-12
+
+
+def test_solve_fp64_wedge_n512_matches_oracle():
+    """The n = 512, k = 100 wedge with 8 sources and 8 levels, in full."""
+    wl = I.wedge_n512()
+    A, ref = _oracle_solve(wl, 1e-6)
+    spread_x, spread_it, _ = _oracle_spread(wl, 1e-6, ref)
+    P, _ = pair(wl)
+    x, info, hist = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+    assert abs(info["iterations"] - ref.iterations) <= max(2.0, 2 * spread_it)
+    assert rel(x, ref.x) <= max(1e-10, 10 * spread_x)
+    assert o.true_relres(A, wl.rhs.ravel(), x.cpu().numpy().ravel()) <= 1e-6
+    np.testing.assert_allclose(hist[:16], ref.history[:16], rtol=1e-9)
+
+
+@pytest.mark.parametrize("name", ["plain64", "wedge128", "grf96"])
+def test_solve_fp32_preconditioner(name):
+    wl = WORKLOADS[name]()
+    A, ref = _oracle_solve(wl, 1e-6)
+    P, _ = pair(wl, precision="fp32")
+    x, info, hist = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+    xs = x.cpu().numpy().ravel()
+    assert o.true_relres(A, wl.rhs.ravel(), xs) <= 1e-6
+    assert abs(info["iterations"] - ref.iterations) <= max(2.0, 0.1 * ref.iterations)
+    # both solutions satisfy relres <= 1e-6; they differ by at most a few times that, relative
+    assert rel(xs, ref.x) <= 1e-4
+
+
+def test_host_buffer_solve_equals_device_solve():
+    wl = I.plain_n64()
+    P, _ = pair(wl)
+    xd, infod, _ = P.solve(dev(wl.rhs), tol=1e-6)
+    xh, infoh, _ = P.solve_host(wl.rhs, tol=1e-6)
+    assert infod["iterations"] == infoh["iterations"]
+    np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+
+
+def test_solves_are_bitwise_reproducible():
+    wl = small_wedge()
+    P, _ = pair(wl, precision="fp32")
+    x1, i1, h1 = P.solve(dev(wl.rhs), tol=1e-6)
+    x2, i2, h2 = P.solve(dev(wl.rhs), tol=1e-6)
+    assert torch.equal(x1, x2) and i1 == i2 and np.array_equal(h1, h2)
+
+
+# --------------------------------------------------------------------------- edge cases
+
+
+@pytest.mark.parametrize("n,levels", [(4, 2), (6, 2), (12, 3), (20, 2)])
+def test_tiny_grids(n, levels):
+    kf = I.constant_k(n, 2.0 * n)
+    wl = I.Workload("tiny", n, 2.0 * n, kf, I.centre_source_rhs(n), variant="hyb", levels=levels)
+    P, H = pair(wl)
+    r = rand_c((n + 1) ** 2, 90)
+    assert rel(P.vcycle(dev(r, n)), o.vcycle(H, r)) <= 1e-11
+    A, ref = _oracle_solve(wl, 1e-8)
+    spread_x, spread_it, _ = _oracle_spread(wl, 1e-8, ref)
+    x, info, _ = P.solve(dev(wl.rhs), tol=1e-8)
+    assert abs(info["iterations"] - ref.iterations) <= max(1.0, 2 * spread_it)
+    assert rel(x, ref.x) <= max(1e-10, 10 * spread_x)
+
+
+def test_zero_rhs_gives_zero_solution():
+    wl = I.plain_n64()
+    P, _ = pair(wl)
+    x, info, hist = P.solve(dev(np.zeros_like(wl.rhs)), tol=1e-6)
+    assert info["iterations"] == 0 and torch.count_nonzero(x) == 0
+
+
+def test_nonfinite_rhs_is_reported():
+    hz = hzmod()
+    wl = I.plain_n64()
+    P, _ = pair(wl)
+    b = wl.rhs.copy()
+    b[3, 5] = np.nan
+    with pytest.raises(hz.HzError) as e:
+        P.solve(dev(b), tol=1e-6)
+    assert e.value.status == hz.HZ_ENONFINITE
+
+
+def test_maxit_is_reported_with_partial_history():
+    hz = hzmod()
+    wl = small_wedge()
+    P, _ = pair(wl)
+    x, info, hist = P.solve(dev(wl.rhs), tol=1e-14, maxit=3, allow_fail=True)
+    assert info["status"] == hz.HZ_EMAXIT and info["iterations"] == 3 and len(hist) == 6
+    A, ref = _oracle_solve(wl, 1e-14, maxit=3)
+    _, _, spread_h = _oracle_spread(wl, 1e-14, ref, maxit=3)
+    np.testing.assert_allclose(hist, ref.history[:6], rtol=max(1e-10, 10 * spread_h))
+
+
+def test_invalid_arguments():
+    hz = hzmod()
+    wl = I.plain_n64()
+    P, _ = pair(wl)
+    b = dev(wl.rhs)
+    with pytest.raises(hz.HzError) as e:
+        P.solve(b, tol=-1.0)
+    assert e.value.status == hz.HZ_EINVAL
+    with pytest.raises(hz.HzError):
+        P.level_presmooth(P.num_levels - 1, b)
