@@ -209,6 +209,29 @@ int hz_profile_iteration(hz_problem* p, const double* rhs, double* x, int iterat
 /* Name of an hz_kernel. */
 const char* hz_kernel_name(int kernel);
 
+/* ---- Allocation-free variant (the paper has no counterpart to this entry point) ----
+ * For callers that cannot allocate device memory when they call: hosts whose own pool owns every
+ * byte of the device (a framework's caching allocator, a serving runtime's memory budget), where
+ * a stray cudaMalloc fragments or oversubscribes the pool, and latency-critical loops, where
+ * cudaMalloc and cudaFree may synchronise the device.
+ *
+ * v = A u on the (n+1)^2 grid (A = L^h for beta = 0, M^h = L^h + i k^2 beta otherwise; physical
+ * units, as hz_apply) and dot = <w, v> = sum_p conj(w_p) v_p, in one pass; no problem object.
+ *  kh      : device, (n+1)^2 doubles, k(x) h at each node.
+ *  u, w, v : device, (n+1)^2 complex128; v must not alias u or w.
+ *  dot     : device, one complex128.
+ *  stream  : a cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
+ * Allocates nothing: its only scratch (per-block partial sums and a counter, about 33 KB) is a
+ * fixed array in the library's device memory, present on every device that loads the library
+ * until the process exits. The first call on a device looks up and caches that array's device
+ * address (cudaGetSymbolAddress): make it before any stream capture. Every call shares the array
+ * and clears its counter, so calls that overlap on the GPU (other streams or host threads) race
+ * and give wrong results: order them. Returns HZ_EINVAL for n outside [2, HZ_NOALLOC_MAX_N], a
+ * null pointer or aliasing (nothing launched), HZ_ECUDA if a launch fails. */
+#define HZ_NOALLOC_MAX_N 32768
+hz_status hz_apply_dot_noalloc(int n, const double* kh, double beta, const double* u, const double* w, double* v,
+                               double* dot, void* stream);
+
 /* Last error message on p (never NULL), and a name for a status code. */
 const char* hz_last_error(const hz_problem* p);
 const char* hz_status_string(int status);

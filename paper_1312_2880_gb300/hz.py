@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "hz_last_error": (ctypes.c_char_p, [P]),
         "hz_status_string": (ctypes.c_char_p, [c_int]),
         "hz_destroy": (None, [P]),
+        "hz_apply_dot_noalloc": (c_int, [c_int, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
