@@ -32,35 +32,42 @@ sys.path.insert(0, ROOT)
 
 from paper_1312_2880_gb300 import inputs as I  # noqa: E402
 
-# Algorithmic (compulsory) HBM bytes per finest-grid node of one launch of each kernel, for the
-# working precision (complex 16/8 B, real 8/4 B) with the FP64 Krylov vectors (16 B). A colour
-# half-sweep touches half the nodes for its own row data but all nodes of the other colour.
+# Algorithmic (compulsory) HBM bytes per finest-grid node of one launch of each kernel. FP32 form:
+# the V-cycle reads and writes FP32 (complex 8 B, k h 4 B) on every level including the finest,
+# the FP64 Krylov kernels (complex 16 B, k h 8 B) write the FP32 copies of p and s and read the
+# FP32 preconditioned vectors y, z (8 B). FP64 form: 16/8 B throughout. A colour half-sweep
+# touches half the nodes for its own row data but all nodes of the other colour.
 def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
     c, r = (8, 4) if fp32 else (16, 8)
+    y = 8 if fp32 else 16  # preconditioned vector as the Krylov kernels read it
+    w = 8 if fp32 else 0  # FP32 copy of p or s written for the V-cycle
     table = {
-        "smooth_restrict": 16 + r + c + c / 4,   # f (FP64 Krylov vector), k h; write u and the coarse f
-        "prolong_smooth": c + c / 4 + 16 + r + 16,  # u_pre, coarse e, f, k h; write the FP64 result
-        "gs_first": 16 / 2 + r / 2 + c,          # f and kh of one colour, write every u
-        "gs_colour": (c + 16 + r + c) / 2,       # other colour's u, own f (FP64 on the finest grid), kh, write
-        "kacz_colour": (5 * c * 2 + 16 + r) / 5,
-        "restrict_residual": c + 16 + r + c / 4,
+        "smooth_restrict": c + r + c + c / 4,      # f, k h; write u and the coarse f
+        "prolong_smooth": c + c / 4 + c + r + c,   # u_pre, coarse e, f, k h; write the result
+        "gs_first": c / 2 + r / 2 + c,
+        "gs_colour": (c + c + r + c) / 2,
+        "kacz_colour": (5 * c * 2 + c + r) / 5,
+        "restrict_residual": c + c + r + c / 4,
         "prolong_add": 2 * c + c / 4,
-        "export": c + 16,
-        "k_update_p": 64,
-        "k_apply_rv": 16 + 8 + 16 + 16,
-        "k_update_s": 48,
-        "k_apply_ts": 16 + 8 + 16 + 16,
-        "k_update_xr": 128,
-        "k_x_half": 48,
+        "export": 2 * c,
+        "k_update_p": 64 + w,
+        "k_apply_rv": y + 8 + 16 + 16,
+        "k_update_s": 48 + w,
+        "k_apply_ts": y + 8 + 16 + 16,
+        "k_update_xr": 16 + 2 * y + 16 + 16 + 16 + 32,
+        "k_x_half": 32 + y,
     }
     return table.get(kernel, 0.0)
 
 
+# FP64 work per node of the Krylov kernels: (flops with an FMA counted 2, FP64-pipe instructions).
+# The operator on an interior node: 3 complex adds (6), d = (kh)^2 - 4 (1 FMA), v = nb + d y (2 FMA).
+KRYLOV_FP64 = {"k_update_p": (16, 8), "k_apply_rv": (20, 13), "k_update_s": (12, 6), "k_apply_ts": (24, 15),
+               "k_update_xr": (36, 18), "k_x_half": (8, 4)}
+
+
 def kernel_fp64_flops_per_node(kernel: str) -> float:
-    """FP64 floating-point operations per node (an FMA counts 2) of the FP64 Krylov kernels."""
-    table = {"k_update_p": 16, "k_apply_rv": 22 + 8, "k_update_s": 8 + 4, "k_apply_ts": 22 + 12,
-             "k_update_xr": 24 + 12, "k_x_half": 8}
-    return table.get(kernel, 0.0)
+    return KRYLOV_FP64.get(kernel, (0, 0))[0]
 
 
 def load_peaks():
@@ -72,6 +79,7 @@ def load_peaks():
 
 
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (probe on this pool: 1.20 TFLOP/s)
+FP64_PEAK_INSTR = FP64_PEAK_TFLOPS / 2  # FP64-pipe instructions per ps (an FMA is one instruction)
 
 
 class ClockSampler:
@@ -218,9 +226,11 @@ def roofline(per, fp32: bool, hbm_peak: float, peak_kind: str, n: int, iteration
     if name.startswith("k_"):
         flops = kernel_fp64_flops_per_node(name) * nodes
         achieved = flops / (avg_ms * 1e-3) / 1e12
+        instr = KRYLOV_FP64[name][1] * nodes / (avg_ms * 1e-3) / 1e12
         roof = {"kernel": name, "level": level, "bound": "alu", "achieved": round(achieved, 4),
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 rate",
+                "peak_source": "nominal GB300 FP64 rate (recipe table); FMA = 2 flops",
+                "fp64_pipe_frac": round(instr / FP64_PEAK_INSTR, 4),
                 "hbm_gbs": round(kernel_bytes_per_node(name, fp32) * nodes / (avg_ms * 1e-3) / 1e9, 1)}
     else:
         byts = kernel_bytes_per_node(name, fp32) * nodes
@@ -266,6 +276,75 @@ def cpu_baseline(wl, iters_full: float, sample_iters: int):
                       f"numpy/scipy, one thread), scaled by the {iters_full:g} iterations of the FP64 form"}
 
 
+def run_batched(precision: str, reps: int = 3):
+    """Four constant-k problems (k, n) = (50, 96), (100, 192), (200, 384), (300, 576), 16 seeded
+    point sources each, solved as one group (every right-hand side of every problem advances in
+    the same graph launch per iteration; finished ones retire). Returns timing and counts."""
+    import torch
+
+    from paper_1312_2880_gb300 import hz
+
+    wls = I.batch_problems(rhs_per_k=16)
+    probs = [hz.Problem(w.n, w.kfield, 0.5, variant=w.variant, precision=precision, k_ref=w.k_ref,
+                        batch=w.rhs.shape[0]) for w in wls]
+    rhs = [torch.from_numpy(w.rhs).cuda() for w in wls]
+    G = hz.Group(probs)
+    G.solve(rhs, tol=1e-6, maxit=3000, allow_fail=True)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        xs, infos = G.solve(rhs, tol=1e-6, maxit=3000, allow_fail=True)
+        t.append((time.perf_counter() - t0) * 1e3)
+    its = [i["iterations"] for i in infos]
+    conv = sum(1 for i in infos if i["status"] == 0)
+    G.close()
+    for P in probs:
+        P.close()
+    ms = statistics.median(t)
+    return {"ms": round(ms, 2), "rhs": len(infos), "converged": conv, "iterations_min": min(its),
+            "iterations_max": max(its), "solves_per_s": round(len(infos) * 1e3 / ms, 1)}
+
+
+def run_serving(precision: str, count: int, rate: float, seed: int = I.SEED_BASE + 5):
+    """Poisson stream of single-RHS requests through the continuous-batching server."""
+    import torch
+
+    from paper_1312_2880_gb300.serve import Job, Server
+
+    u = I.uniform01(seed, 4 * count)
+    gaps = -np.log(1.0 - u[0::4]) / rate
+    t = np.cumsum(gaps) - gaps[0]
+    sizes = SERVE_SIZES
+    media = {}
+    jobs = []
+    for r in range(count):
+        n = sizes[min(len(sizes) - 1, int(u[4 * r + 1] * len(sizes)))]
+        medium = "wedge" if u[4 * r + 2] < 0.5 else "grf"
+        mseed = I.SEED_BASE + 1000 + int(u[4 * r + 3] * 2)
+        key = (n, medium, mseed)
+        k = SERVE_KH * n
+        if key not in media:
+            media[key] = I.wedge_k(n, k, mseed) if medium == "wedge" else I.grf_k(n, k, mseed)
+        src = I.random_interior_nodes(n, 1, seed + 17 * r + 3)[0]
+        jobs.append(Job(r, n, key, (lambda key=key: media[key]), k, src, arrival=float(t[r])))
+    free = torch.cuda.mem_get_info()[0]
+    srv = Server(hbm_budget=int(free * 0.6), precision=precision, max_active=32, maxit=3000)
+    summ = srv.run(jobs, realtime=True)
+    srv.close()
+    summ["rate_hz"] = rate
+    summ["requests"] = count
+    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in summ.items()}
+
+
+# Served stream: grid sizes and kh. The stream of the serving workload (kh = 2 pi / 12 with wedge
+# and random-field media, n up to 2048) does not converge within 4000 iterations for n >= 256 in
+# either form (measured), so the served requests use kh = 0.2, the resolution of the n = 512
+# wedge workload, and sizes up to 1024.
+SERVE_SIZES = (128, 256, 512, 1024)
+SERVE_KH = 0.2
+
+
 def run_ours(args):
     import torch
 
@@ -298,6 +377,11 @@ def run_ours(args):
     gpu_launches = int(args.steps * ((int(np.ceil(it32)) + 3) * launches_per_iter + 4))
     for r in results.values():
         r["P"].close()
+    batched = serving = None
+    if not args.skip_forms:
+        batched = {"fp32_form": run_batched("fp32"), "fp64_form": run_batched("fp64")}
+        serving = {"fp32_form": run_serving("fp32", args.serve_requests, args.serve_rate),
+                   "fp64_form": run_serving("fp64", args.serve_requests, args.serve_rate)}
     # HBM roofline on a grid larger than L2: two profiled FP32-preconditioned iterations.
     rw = workload(args.roofline_workload)
     Pr = hz.Problem(rw.n, rw.kfield, 0.5, variant=rw.variant, precision="fp32", levels=rw.levels, k_ref=rw.k_ref)
@@ -333,6 +417,8 @@ def run_ours(args):
                       "relres_true": results["fp64"]["relres_true"],
                       "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3)},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "batched": batched,
+        "serving": serving,
         "roofline": roof,
         "sweep_hbm": {"workload": rw.name, "kernels": sweeps, "iteration_ms": round(big_iter_ms, 3),
                       "kernel_share": shares(per_big)},
@@ -391,6 +477,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """One FP32-form iteration of the roofline workload launched kernel by kernel (for ncu)."""
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    torch.cuda.set_device(0)
+    build.build()
+    rw = workload(args.profile_case)
+    P = hz.Problem(rw.n, rw.kfield, 0.5, variant=rw.variant, precision=args.profile_precision, levels=rw.levels,
+                   k_ref=rw.k_ref)
+    recs = P.profile_iteration(torch.from_numpy(rw.rhs).cuda(), iterations=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": rw.name, "launches": len(recs)}))
+    P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,8 +505,15 @@ def main():
     ap.add_argument("--roofline-workload", default="grf4096")
     ap.add_argument("--cpu-sample-iters", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None, help="run one profiled iteration of this workload and exit")
+    ap.add_argument("--skip-forms", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-rate", type=float, default=15.0)
+    ap.add_argument("--profile-precision", default="fp32")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

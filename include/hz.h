@@ -71,6 +71,8 @@ typedef struct {
                     when some node has 1 < k H < 2 sqrt(2), where red-black GS on L amplifies
                     oscillatory error */
   double k_ref;  /* wavenumber that sets each level's scale c = k_ref H; 0 = mean of k(x) */
+  int batch;     /* right-hand sides solved together by hz_solve_batch (1..1024, default 1); every
+                    kernel launch then covers all of them and finished ones retire individually */
 } hz_hierarchy_opts;
 
 typedef struct {
@@ -142,9 +144,43 @@ hz_status hz_vcycle(hz_problem* p, const double* r, double* z);
 hz_status hz_solve(hz_problem* p, const double* rhs, double* x, double tol, int maxit,
                    double* history, int history_cap, hz_solve_info* info);
 
+/* Solve for all `batch` right-hand sides of the hierarchy at once (hz_hierarchy_opts.batch):
+ * rhs, x: device, batch consecutive (n+1)^2 complex128 vectors. Each right-hand side runs its own
+ * Bi-CGSTAB (own scalars, own stop) inside the same kernel launches; one that stops early skips
+ * the remaining work. infos: host array of batch entries (may be NULL). Returns HZ_OK when every
+ * instance converged, else the first failing instance's status (per-instance status in infos).
+ * hz_solve and the non-blocking calls require batch = 1. Synchronises. */
+hz_status hz_solve_batch(hz_problem* p, const double* rhs, double* x, double tol, int maxit, hz_solve_info* infos);
+
+/* Groups: several (batched) problems of different grids solved together. Every iteration of
+ * every problem is captured into ONE CUDA graph (each problem's kernels on its own branch), and
+ * that graph is replayed until every right-hand side of every problem has stopped; finished ones
+ * skip their work inside the kernels. The problems must be set up and must not be used elsewhere
+ * while the group solves. */
+typedef struct hz_group hz_group;
+hz_status hz_group_create(hz_problem* const* probs, int count, hz_group** out);
+/* rhs[i], x[i]: device, problem i's batch consecutive (n_i+1)^2 complex128 vectors. infos: host,
+ * one entry per right-hand side, problem by problem (may be NULL). Synchronises. */
+hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x, double tol, int maxit,
+                         hz_solve_info* infos);
+const char* hz_group_last_error(const hz_group* g);
+void hz_group_destroy(hz_group* g);
+
 /* As hz_solve with rhs and x in host memory: copies rhs to the device and x back. */
 hz_status hz_solve_host(hz_problem* p, const double* rhs_host, double* x_host, double tol, int maxit,
                         double* history, int history_cap, hz_solve_info* info);
+
+/* ---- Non-blocking solve: one host thread can keep many problems' solves in flight (serving).
+ * hz_solve_start validates, queues the start-up and the first iterations on the problem's stream
+ * and returns; hz_solve_poll never waits: it reads the progress flags that have already landed,
+ * queues further iterations, and sets *done = 1 once the solve has stopped (converged, broken
+ * down, non-finite or maxit); hz_solve_finish waits for the end if needed and reports exactly as
+ * hz_solve does (status, history, info). x holds the result only after hz_solve_finish returns.
+ * One solve per problem at a time (HZ_EINVAL otherwise); rhs and x must stay valid until
+ * hz_solve_finish. A CUDA error during polling ends the solve and is returned. */
+hz_status hz_solve_start(hz_problem* p, const double* rhs, double* x, double tol, int maxit);
+hz_status hz_solve_poll(hz_problem* p, int* done);
+hz_status hz_solve_finish(hz_problem* p, double* history, int history_cap, hz_solve_info* info);
 
 /* ---- Individual steps (the kernels the V-cycle and Bi-CGSTAB run), for testing and for
  * callers that compose their own cycles. All arrays are device complex128 in physical units
@@ -190,6 +226,8 @@ typedef enum {
   HZ_K_UPDATE_XR,      /* x, r updates with <r^, r>, |r|^2 */
   HZ_K_SMOOTH_RESTRICT, /* fused: GS sweep from a zero guess, residual, full weighting */
   HZ_K_PROLONG_SMOOTH, /* fused: bilinear correction and GS post-sweep */
+  HZ_K_KACZ_LEVEL,     /* whole Kaczmarz level in one block (pre: sweeps + residual + FW; post: correction + sweeps) */
+  HZ_K_KACZ_SWEEP,     /* one five-colour Kaczmarz sweep over halo tiles */
   HZ_K_COUNT
 } hz_kernel;
 

@@ -53,6 +53,9 @@ struct Plan {
          off_hist = 0, off_status = 0;
   int nvec = 11;
   int m_coarse = 0;
+  int batch = 1;
+  std::vector<long long> ls;  // elements between instances of a level's arrays
+  size_t rhat_bytes = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -80,6 +83,9 @@ bool make_plan(int n, const hz_hierarchy_opts& o, Plan* P, std::string* err) {
   }
   P->levels = L;
   P->fp32 = o.precision == HZ_PREC_FP32;
+  const int B = o.batch < 1 ? 1 : o.batch;
+  P->batch = B;
+  P->ls.assign(L, 0);
   size_t ce = P->fp32 ? 8 : 16, re = P->fp32 ? 4 : 8;
   size_t off = 0;
   P->n.resize(L);
@@ -93,36 +99,38 @@ bool make_plan(int n, const hz_hierarchy_opts& o, Plan* P, std::string* err) {
     P->n[l] = nl;
     P->pitch[l] = ((nl + 1 + 31) / 32) * 32;
     size_t cells = (size_t)P->pitch[l] * (nl + 1);
+    P->ls[l] = (long long)cells;
     if (l > 0 || P->fp32) {  // level 0 in FP64 reads the FP64 k h array directly
       P->off_kh[l] = off;
       off = align256(off + cells * re);
     }
     P->off_u[l] = off;
-    off = align256(off + cells * ce);
+    off = align256(off + cells * ce * B);
     if (l > 0) {
       P->off_f[l] = off;
-      off = align256(off + cells * ce);
+      off = align256(off + cells * ce * B);
       P->off_u2[l] = off;  // out-of-place result of the fused post-smoothing pass
-      off = align256(off + cells * ce);
+      off = align256(off + cells * ce * B);
     }
   }
   size_t N = (size_t)(n + 1) * (n + 1);
   P->off_kh64 = off;
   off = align256(off + N * 8);
-  P->vec_bytes = align256(N * 16);
+  P->vec_bytes = align256(N * 16 * B);  // one slot: B consecutive vectors
+  P->rhat_bytes = align256(N * 16);      // the shadow residual is shared
   P->off_vec = off;
-  off += P->vec_bytes * P->nvec;
+  off += P->vec_bytes * (P->nvec - 1) + P->rhat_bytes;
   P->m_coarse = (nc + 1) * (nc + 1);
   P->off_ainv = off;
   off = align256(off + (size_t)P->m_coarse * P->m_coarse * ce);
   P->off_work = off;
   off = align256(off + (size_t)P->m_coarse * P->m_coarse * 2 * 16);
   P->off_state = off;
-  off = align256(off + sizeof(KState));
+  off = align256(off + sizeof(KState) * B);
   P->off_partials = off;
-  off = align256(off + (size_t)PARTIAL_SLOTS * MAX_G * 8);
+  off = align256(off + (size_t)PARTIAL_SLOTS * MAX_G * 8 * B);
   P->off_hist = off;
-  off = align256(off + (size_t)HIST_CAP * 8);
+  off = align256(off + (size_t)HIST_CAP * 8 * B);
   P->off_status = off;
   off = align256(off + 256);
   P->total = off;
@@ -160,6 +168,17 @@ struct hz_problem {
   double2* graph_x = nullptr;
   int num_sms = 0;
   std::string err;
+  // Solve in flight (see solve_begin/solve_advance/solve_end).
+  struct Run {
+    enum Phase { IDLE = 0, RUNNING, FINAL_WAIT, DONE };
+    int phase = IDLE;
+    double tol = 0;
+    int maxit = 0;
+    long long launched = 0, polled = 0;
+    int restarts = 0;
+  } run;
+  KState* kstate_host = nullptr;  // pinned copy of the device Krylov state at the end of a solve
+  cudaEvent_t ev_final = nullptr;
   // Measurement: when set, every launch is followed by an event on `stream` (hz_profile_iteration).
   struct ProfRec { int kernel, level; cudaEvent_t ev; };
   std::vector<ProfRec>* prof = nullptr;
@@ -247,10 +266,54 @@ const void* kh_of(const hz_problem* P, int l, int* pk) {
   return P->lv[l].kh;
 }
 
+// Launch instances: every right-hand side of the batch (solves) or instance 0 (step entry points).
+Inst inst_for(const hz_problem* P, int l, bool all) {
+  Inst bi;
+  if (!all || P->plan.batch == 1) return bi;
+  const Plan& pl = P->plan;
+  bi.count = pl.batch;
+  bi.su = pl.ls[l];
+  bi.sf = l == 0 ? P->kv.sv : pl.ls[l];
+  bi.sc = l + 1 < pl.levels ? pl.ls[l + 1] : 0;
+  bi.so = l == 0 ? P->kv.sv : pl.ls[l];
+  bi.stop_stride = (int)(sizeof(KState) / sizeof(int));
+  return bi;
+}
+
 // A Gauss-Seidel level with one sweep each way runs as two fused tile passes (hz_fused.cu).
 bool fused(const hz_problem* P, int l) {
   const Level& L = P->lv[l];
   return l < P->plan.levels - 1 && L.smoother == HZ_SMOOTH_GS && L.nu == 1;
+}
+
+// How an FP32 Kaczmarz level runs: whole level in one block, or one tiled launch per sweep (even
+// sweep counts, ping-pong between u and u2 ending in u). FP64 keeps one launch per colour: there
+// the FP64 pipe bounds the work and the tiles' halo would add to it.
+enum KaczPath { KACZ_COLOUR = 0, KACZ_LEVEL, KACZ_TILE };
+KaczPath kacz_path(const hz_problem* P, int l) {
+  const Level& L = P->lv[l];
+  if (l == 0 || !P->plan.fp32 || L.smoother != HZ_SMOOTH_KACZMARZ) return KACZ_COLOUR;
+  if (kacz_level_fits(true, L.n)) return KACZ_LEVEL;
+  return (L.nu % 2 == 0) ? KACZ_TILE : KACZ_COLOUR;
+}
+
+// Tiled sweeps on level l: `first_in` is the input of the first sweep (null = zero guess).
+cudaError_t kacz_tile_sweeps(hz_problem* P, int l, Src f, const void* first_in, bool post, const int* stop,
+                             const Inst& bi) {
+  const Level& L = P->lv[l];
+  int pk;
+  const void* kh = kh_of(P, l, &pk);
+  const void* in = first_in;
+  cudaError_t e;
+  for (int k = 0; k < L.nu; ++k) {
+    void* out = ((L.nu - 1 - k) % 2 == 0) ? L.u : L.u2;
+    if ((e = mark(P, launch_kacz_sweep_tile(true, out, L.pitch, in, L.pitch, f.f, f.pf, f.f64, kh, pk, L.n,
+                                            op_beta(P, L.relax_op), post, stop, P->stream, bi),
+                  HZ_K_KACZ_SWEEP, l)))
+      return e;
+    in = out;
+  }
+  return cudaSuccess;
 }
 
 // Where level l's result after post-relaxation lives (what level l-1 interpolates).
@@ -260,7 +323,8 @@ void* final_u(const hz_problem* P, int l) {
 
 // Pre-relaxation from a zero guess on level l into lv[l].u and the restricted residual into
 // level l+1's f.
-cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop) {
+cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop, bool all = false) {
+  const Inst bi = inst_for(P, l, all);
   const Level& L = P->lv[l];
   const Level& C = P->lv[l + 1];
   bool fp32 = P->plan.fp32;
@@ -272,26 +336,38 @@ cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop) {
   int pu = L.pitch;
   cudaError_t e;
   if (fused(P, l))
-    return mark(P, launch_smooth_restrict(fp32, u, pu, C.f, C.pitch, f.f, f.pf, f.f64, kh, pk, L.n, bA, bB, stop, s),
+    return mark(P, launch_smooth_restrict(fp32, u, pu, C.f, C.pitch, f.f, f.pf, f.f64, kh, pk, L.n, bA, bB, stop, s, bi),
                 HZ_K_SMOOTH_RESTRICT, l);
+  KaczPath kp = kacz_path(P, l);
+  if (kp == KACZ_LEVEL)
+    return mark(P, launch_kacz_level_pre(true, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop, s, bi),
+                HZ_K_KACZ_LEVEL, l);
+  if (kp == KACZ_TILE) {
+    if ((e = kacz_tile_sweeps(P, l, f, nullptr, false, stop, bi))) return e;
+    return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s, bi),
+                HZ_K_RESTRICT, l);
+  }
   if (L.smoother == HZ_SMOOTH_GS) {
-    if ((e = mark(P, launch_gs_first(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 0, bA, stop, s), HZ_K_GS_FIRST, l))) return e;
-    if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 1, bA, stop, s), HZ_K_GS_COLOUR, l))) return e;
+    if ((e = mark(P, launch_gs_first(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 0, bA, stop, s, bi), HZ_K_GS_FIRST, l))) return e;
+    if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 1, bA, stop, s, bi), HZ_K_GS_COLOUR, l))) return e;
     for (int it = 1; it < L.nu; ++it)
       for (int c = 0; c < 2; ++c)
-        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s), HZ_K_GS_COLOUR, l))) return e;
+        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s, bi), HZ_K_GS_COLOUR, l))) return e;
   } else {
     size_t ce = fp32 ? 8 : 16;
-    if ((e = mark(P, cudaMemset2DAsync(u, (size_t)pu * ce, 0, (size_t)(L.n + 1) * ce, L.n + 1, s), HZ_K_ZERO, l))) return e;
+    if ((e = mark(P, cudaMemset2DAsync(u, (size_t)pu * ce, 0, (size_t)(L.n + 1) * ce, (L.n + 1) * bi.count, s),
+                  HZ_K_ZERO, l)))
+      return e;
     for (int it = 0; it < L.nu; ++it)
       for (int c = 0; c < 5; ++c)
-        if ((e = mark(P, launch_kacz_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s), HZ_K_KACZ_COLOUR, l))) return e;
+        if ((e = mark(P, launch_kacz_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s, bi), HZ_K_KACZ_COLOUR, l))) return e;
   }
-  return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s), HZ_K_RESTRICT, l);
+  return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s, bi), HZ_K_RESTRICT, l);
 }
 
 // `sweeps` sweeps of the level's smoother on lv[l].u in place; post selects the ordering.
-cudaError_t level_sweeps(hz_problem* P, int l, Src f, int sweeps, bool post, const int* stop) {
+cudaError_t level_sweeps(hz_problem* P, int l, Src f, int sweeps, bool post, const int* stop, bool all = false) {
+  const Inst bi = inst_for(P, l, all);
   const Level& L = P->lv[l];
   bool fp32 = P->plan.fp32;
   int pk;
@@ -304,12 +380,12 @@ cudaError_t level_sweeps(hz_problem* P, int l, Src f, int sweeps, bool post, con
   for (int it = 0; it < sweeps; ++it) {
     if (L.smoother == HZ_SMOOTH_GS) {
       for (int q = 0; q < 2; ++q)
-        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 1 - q : q, bA, stop, s),
+        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 1 - q : q, bA, stop, s, bi),
                       HZ_K_GS_COLOUR, l)))
           return e;
     } else {
       for (int q = 0; q < 5; ++q)
-        if ((e = mark(P, launch_kacz_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 4 - q : q, bA, stop, s),
+        if ((e = mark(P, launch_kacz_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 4 - q : q, bA, stop, s, bi),
                       HZ_K_KACZ_COLOUR, l)))
           return e;
     }
@@ -319,7 +395,8 @@ cudaError_t level_sweeps(hz_problem* P, int l, Src f, int sweeps, bool post, con
 
 // Correction from level l+1 and post-relaxation of level l. The result goes to `out` (pitch po):
 // on the finest level a double2 array, otherwise final_u(l).
-cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* stop) {
+cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* stop, bool all = false) {
+  const Inst bi = inst_for(P, l, all);
   const Level& L = P->lv[l];
   const Level& C = P->lv[l + 1];
   bool fp32 = P->plan.fp32;
@@ -328,38 +405,58 @@ cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* 
   if (fused(P, l)) {
     int pk;
     const void* kh = kh_of(P, l, &pk);
-    return mark(P, launch_prolong_smooth(fp32, out, po, l == 0, L.u, L.pitch, ec, C.pitch, f.f, f.pf, f.f64, kh, pk,
-                                         L.n, op_beta(P, L.relax_op), stop, P->stream),
+    return mark(P, launch_prolong_smooth(fp32, out, po, false, L.u, L.pitch, ec, C.pitch, f.f, f.pf, f.f64, kh, pk,
+                                         L.n, op_beta(P, L.relax_op), stop, P->stream, bi),
                 HZ_K_PROLONG_SMOOTH, l);
   }
-  if ((e = mark(P, launch_prolong_add(fp32, L.u, L.pitch, ec, C.pitch, L.n, stop, P->stream), HZ_K_PROLONG, l))) return e;
-  if ((e = level_sweeps(P, l, f, L.nu, true, stop))) return e;
-  if (l == 0)
-    return mark(P, launch_export(fp32, (double2*)out, po, L.u, L.pitch, L.n, 1.0, stop, P->stream), HZ_K_EXPORT, 0);
+  KaczPath kp = kacz_path(P, l);
+  if (kp == KACZ_LEVEL) {
+    int pk;
+    const void* kh = kh_of(P, l, &pk);
+    return mark(P, launch_kacz_level_post(true, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
+                                          op_beta(P, L.relax_op), L.nu, stop, P->stream, bi),
+                HZ_K_KACZ_LEVEL, l);
+  }
+  if ((e = mark(P, launch_prolong_add(fp32, L.u, L.pitch, ec, C.pitch, L.n, stop, P->stream, bi), HZ_K_PROLONG, l))) return e;
+  if (kp == KACZ_TILE) {
+    if ((e = kacz_tile_sweeps(P, l, f, L.u, true, stop, bi))) return e;
+  } else if ((e = level_sweeps(P, l, f, L.nu, true, stop, all))) {
+    return e;
+  }
+  if (l == 0) {  // unfused finest level: copy its u to the output (same element type)
+    size_t es = fp32 ? sizeof(float2) : sizeof(double2);
+    return mark(P, cudaMemcpy2DAsync(out, (size_t)po * es, L.u, (size_t)L.pitch * es, (size_t)(L.n + 1) * es,
+                                     (L.n + 1) * bi.count, cudaMemcpyDeviceToDevice, P->stream),
+                HZ_K_EXPORT, 0);
+  }
   return cudaSuccess;
 }
 
-cudaError_t coarse(hz_problem* P, const int* stop) {
+cudaError_t coarse(hz_problem* P, const int* stop, bool all = false) {
   const Level& C = P->lv.back();
-  return mark(P, launch_coarse_solve(P->plan.fp32, C.u, C.pitch, C.f, C.pitch, P->ainvT, C.n, stop, P->stream), HZ_K_COARSE,
-              P->plan.levels - 1);
+  const Inst bi = inst_for(P, P->plan.levels - 1, all);
+  return mark(P, launch_coarse_solve(P->plan.fp32, C.u, C.pitch, C.f, C.pitch, P->ainvT, C.n, stop, P->stream, bi),
+              HZ_K_COARSE, P->plan.levels - 1);
 }
 
-Src level_src(const hz_problem* P, int l, const double2* f0) {
-  return l == 0 ? Src{f0, P->n + 1, true} : Src{P->lv[l].f, P->lv[l].pitch, false};
+// Right-hand side of level l: the V-cycle input on the finest grid (double2 in the FP64 form,
+// float2 in the FP32 form; pitch n+1), the level's own f below.
+Src level_src(const hz_problem* P, int l, const void* f0) {
+  return l == 0 ? Src{f0, P->n + 1, !P->plan.fp32} : Src{P->lv[l].f, P->lv[l].pitch, false};
 }
 
-// z = V-cycle(f0) with f0 already h^2-scaled (double2, pitch n+1); z double2, pitch n+1.
-cudaError_t run_vcycle(hz_problem* P, const double2* f0, double2* z, const int* stop) {
+// z = V-cycle(f0) with f0 already h^2-scaled; f0 and z (pitch n+1) are double2 in the FP64 form
+// and float2 in the FP32 form.
+cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, bool all = false) {
   int L = P->plan.levels;
   cudaError_t e;
   for (int l = 0; l < L - 1; ++l)
-    if ((e = level_down(P, l, level_src(P, l, f0), stop))) return e;
-  if ((e = coarse(P, stop))) return e;
+    if ((e = level_down(P, l, level_src(P, l, f0), stop, all))) return e;
+  if ((e = coarse(P, stop, all))) return e;
   for (int l = L - 2; l >= 0; --l) {
     void* out = l == 0 ? (void*)z : final_u(P, l);
     int po = l == 0 ? P->n + 1 : P->lv[l].pitch;
-    if ((e = level_up(P, l, level_src(P, l, f0), out, po, stop))) return e;
+    if ((e = level_up(P, l, level_src(P, l, f0), out, po, stop, all))) return e;
   }
   return cudaSuccess;
 }
@@ -370,12 +467,13 @@ cudaError_t enqueue_iteration(hz_problem* P) {
   cudaStream_t s = P->stream;
   const int* stop = &k.st->done;
   cudaError_t e;
+  const bool fp32 = P->plan.fp32;
   if ((e = mark(P, launch_k_update_p(k, s), HZ_K_UPDATE_P, 0))) return e;
-  if ((e = run_vcycle(P, k.p, k.y, stop))) return e;
+  if ((e = run_vcycle(P, fp32 ? (const void*)k.p32 : k.p, fp32 ? (void*)k.y32 : k.y, stop, true))) return e;
   if ((e = mark(P, launch_k_apply_rv(k, s), HZ_K_APPLY_RV, 0))) return e;
   if ((e = mark(P, launch_k_update_s(k, s), HZ_K_UPDATE_S, 0))) return e;
   if ((e = mark(P, launch_k_x_half(k, s), HZ_K_X_HALF, 0))) return e;
-  if ((e = run_vcycle(P, k.s, k.z, stop))) return e;
+  if ((e = run_vcycle(P, fp32 ? (const void*)k.s32 : k.s, fp32 ? (void*)k.z32 : k.z, stop, true))) return e;
   if ((e = mark(P, launch_k_apply_ts(k, s), HZ_K_APPLY_TS, 0))) return e;
   return mark(P, launch_k_update_xr(k, s), HZ_K_UPDATE_XR, 0);
 }
@@ -399,9 +497,30 @@ hz_status build_graph(hz_problem* P) {
   return HZ_OK;
 }
 
-hz_status solve_device(hz_problem* P, const double* rhs, double* x, double tol, int maxit, double* history,
-                       int history_cap, hz_solve_info* info) {
+// ------------------------------------------------------------------ resumable solve
+// A solve is a small state machine so that one host thread can drive many problems at once
+// (hz_solve_start / hz_solve_poll / hz_solve_finish); hz_solve runs the same machine blocking.
+// RUNNING keeps PIPELINE graph replays in flight and reads each one's 16-byte flag copy when its
+// event has completed; FINAL_WAIT waits for the true residual and the Krylov state.
+
+cudaError_t enqueue_replay(hz_problem* P) {
+  hz_problem::Run& R = P->run;
+  cudaStream_t s = P->stream;
+  cudaError_t e = cudaGraphLaunch(P->graph, s);
+  int slot = (int)(R.launched % PIPELINE);
+  const int B = P->plan.batch;
+  // the 16-byte flag block (it, first, done, half) of every instance
+  if (!e)
+    e = cudaMemcpy2DAsync(P->poll_host + 4 * B * slot, 4 * sizeof(int), &P->kv.st->it, sizeof(KState), 4 * sizeof(int),
+                          B, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaEventRecord(P->ev[slot], s);
+  if (!e) ++R.launched;
+  return e;
+}
+
+hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, int maxit) {
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
+  if (P->run.phase != hz_problem::Run::IDLE) return fail(P, HZ_EINVAL, "a solve is already in flight on this problem");
   if (!rhs || !x || !(tol > 0) || maxit < 1) return fail(P, HZ_EINVAL, "bad solve arguments");
   if ((const double*)rhs == x) return fail(P, HZ_EINVAL, "rhs and x may not alias");
   if (maxit > HIST_CAP / 2 - 1) maxit = HIST_CAP / 2 - 1;
@@ -411,75 +530,139 @@ hz_status solve_device(hz_problem* P, const double* rhs, double* x, double tol, 
     hz_status st = build_graph(P);
     if (st) return st;
   }
+  hz_problem::Run& R = P->run;
+  R = hz_problem::Run();
+  R.tol = tol;
+  R.maxit = maxit;
+  CK(launch_k_init(P->kv, tol, maxit, HIST_CAP, P->stream));
+  R.phase = hz_problem::Run::RUNNING;
+  while (R.launched < PIPELINE && R.launched < (long long)maxit + 2) CK(enqueue_replay(P));
+  return HZ_OK;
+}
+
+// Advance the solve; with block = false return as soon as the next step would wait.
+hz_status solve_advance(hz_problem* P, bool block, int* done) {
+  hz_problem::Run& R = P->run;
   cudaStream_t s = P->stream;
-  const KrylovVecs& k = P->kv;
-  CK(launch_k_init(k, tol, maxit, HIST_CAP, s));
-  int restarts = 0;
-  int state[4] = {0, 0, 0, 0};
+  *done = 0;
   for (;;) {
-    // Replay iterations, polling the flags of the iteration PIPELINE-1 steps back.
-    long long launched = 0, polled = 0;
-    bool done = false;
-    while (!done) {
-      if (launched < (long long)maxit + 2) {
-        CK(cudaGraphLaunch(P->graph, s));
-        int slot = (int)(launched % PIPELINE);
-        CK(cudaMemcpyAsync(P->poll_host + 4 * slot, &k.st->it, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaEventRecord(P->ev[slot], s));
-        ++launched;
-      }
-      if (launched - polled >= PIPELINE || launched >= (long long)maxit + 2) {
-        int slot = (int)(polled % PIPELINE);
-        CK(cudaEventSynchronize(P->ev[slot]));
-        std::memcpy(state, P->poll_host + 4 * slot, sizeof(state));
-        ++polled;
-        if (state[2] != 0) done = true;
-        else if (polled >= launched && launched >= (long long)maxit + 2) done = true;
-      }
+    if (R.phase == hz_problem::Run::IDLE) return fail(P, HZ_EINVAL, "no solve in flight");
+    if (R.phase == hz_problem::Run::DONE) {
+      *done = 1;
+      return HZ_OK;
     }
-    CK(cudaStreamSynchronize(s));
-    KState hs;
-    CK(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (hs.done == 1 && hs.bnorm2 > 0) {
-      CK(launch_k_true_residual(k, s));
-      double trr = 0;
-      CK(cudaMemcpyAsync(&trr, &k.st->trr, sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (!(trr <= hs.tol2) && restarts < 8 && hs.it < maxit) {
-        ++restarts;
-        CK(launch_k_restart(k, s));
+    if (R.phase == hz_problem::Run::RUNNING) {
+      int slot = (int)(R.polled % PIPELINE);
+      if (block) {
+        CK(cudaEventSynchronize(P->ev[slot]));
+      } else {
+        cudaError_t q = cudaEventQuery(P->ev[slot]);
+        if (q == cudaErrorNotReady) return HZ_OK;
+        if (q != cudaSuccess) return cuda_fail(P, q, "cudaEventQuery");
+      }
+      const int B = P->plan.batch;
+      const int* flags = P->poll_host + 4 * B * slot;  // per instance: it, first, done, half
+      ++R.polled;
+      bool all_done = true;
+      for (int b = 0; b < B; ++b) all_done = all_done && flags[4 * b + 2] != 0;
+      const long long cap = (long long)R.maxit + 2;
+      if (all_done || (R.polled >= R.launched && R.launched >= cap)) {
+        CK(launch_k_true_residual(P->kv, s));
+        CK(cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * B, cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(P->ev_final, s));
+        R.phase = hz_problem::Run::FINAL_WAIT;
         continue;
       }
-    } else if (hs.bnorm2 > 0) {
-      CK(launch_k_true_residual(k, s));
-      CK(cudaStreamSynchronize(s));
+      if (R.launched < cap) CK(enqueue_replay(P));
+      continue;
     }
-    CK(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    hz_status st = HZ_OK;
-    double iters = hs.iters_x2 * 0.5;
-    if (hs.done == 2) st = HZ_EBREAKDOWN;
-    else if (hs.done == 3) st = HZ_ENONFINITE;
-    else if (hs.done == 4 || hs.done == 0) { st = HZ_EMAXIT; iters = (double)maxit; }
-    int hl = std::min(hs.hist_len, HIST_CAP);
-    if (history && history_cap > 0 && hl > 0)
-    {
-      CK(cudaMemcpyAsync(history, k.hist, sizeof(double) * std::min(hl, history_cap), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+    // FINAL_WAIT
+    if (block) {
+      CK(cudaEventSynchronize(P->ev_final));
+    } else {
+      cudaError_t q = cudaEventQuery(P->ev_final);
+      if (q == cudaErrorNotReady) return HZ_OK;
+      if (q != cudaSuccess) return cuda_fail(P, q, "cudaEventQuery");
     }
-    if (info) {
-      info->iterations = iters;
-      info->relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.trr / hs.bnorm2) : 0.0;
-      info->history_len = std::min(hl, history_cap > 0 ? history_cap : 0);
-      info->status = st;
-      info->restarts = restarts;
+    bool restarted = false;
+    if (R.restarts < 8) {
+      for (int b = 0; b < P->plan.batch; ++b) {
+        const KState& hs = P->kstate_host[b];
+        if (hs.done == 1 && hs.bnorm2 > 0 && !(hs.trr <= hs.tol2) && hs.it < R.maxit) {
+          CK(launch_k_restart(instance_of(P->kv, b), s));
+          restarted = true;
+        }
+      }
     }
-    if (st == HZ_EBREAKDOWN) return fail(P, st, "Bi-CGSTAB breakdown");
-    if (st == HZ_ENONFINITE) return fail(P, st, "non-finite value in the Krylov scalars");
-    if (st == HZ_EMAXIT) return fail(P, st, "maximum iterations reached");
-    return HZ_OK;
+    if (restarted) {
+      ++R.restarts;
+      R.launched = R.polled = 0;
+      R.phase = hz_problem::Run::RUNNING;
+      while (R.launched < PIPELINE && R.launched < (long long)R.maxit + 2) CK(enqueue_replay(P));
+      continue;
+    }
+    R.phase = hz_problem::Run::DONE;
   }
+}
+
+hz_status instance_status(const KState& hs, int maxit, double* iters) {
+  *iters = hs.iters_x2 * 0.5;
+  if (hs.done == 2) return HZ_EBREAKDOWN;
+  if (hs.done == 3) return HZ_ENONFINITE;
+  if (hs.done == 4 || hs.done == 0) {
+    *iters = (double)maxit;
+    return HZ_EMAXIT;
+  }
+  return HZ_OK;
+}
+
+// Results of a finished solve: instance 0's history, `ninfo` infos (one per instance).
+hz_status solve_end(hz_problem* P, double* history, int history_cap, hz_solve_info* info, int ninfo = 1) {
+  hz_problem::Run& R = P->run;
+  if (R.phase != hz_problem::Run::DONE) return fail(P, HZ_EINVAL, "the solve has not finished");
+  R.phase = hz_problem::Run::IDLE;
+  const int B = P->plan.batch;
+  double iters0 = 0;
+  const hz_status st = instance_status(P->kstate_host[0], R.maxit, &iters0);
+  int hl = std::min(P->kstate_host[0].hist_len, HIST_CAP);
+  if (history && history_cap > 0 && hl > 0) {
+    CK(cudaMemcpyAsync(history, P->kv.hist, sizeof(double) * std::min(hl, history_cap), cudaMemcpyDeviceToHost,
+                       P->stream));
+  }
+  CK(cudaStreamSynchronize(P->stream));
+  hz_status worst = HZ_OK;
+  for (int b = 0; b < B; ++b) {
+    const KState& hs = P->kstate_host[b];
+    double it = 0;
+    hz_status sb = instance_status(hs, R.maxit, &it);
+    if (sb != HZ_OK && worst == HZ_OK) worst = sb;
+    if (info && b < ninfo) {
+      info[b].iterations = it;
+      info[b].relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.trr / hs.bnorm2) : 0.0;
+      info[b].history_len = b == 0 ? std::min(hl, history_cap > 0 ? history_cap : 0) : 0;
+      info[b].status = sb;
+      info[b].restarts = R.restarts;
+    }
+  }
+  const hz_status res = B == 1 ? st : worst;
+  if (res == HZ_EBREAKDOWN) return fail(P, res, "Bi-CGSTAB breakdown");
+  if (res == HZ_ENONFINITE) return fail(P, res, "non-finite value in the Krylov scalars");
+  if (res == HZ_EMAXIT) return fail(P, res, "maximum iterations reached");
+  return HZ_OK;
+}
+
+hz_status solve_device(hz_problem* P, const double* rhs, double* x, double tol, int maxit, double* history,
+                       int history_cap, hz_solve_info* info, int ninfo = 1) {
+  hz_status st = solve_begin(P, rhs, x, tol, maxit);
+  if (st) return st;
+  int done = 0;
+  st = solve_advance(P, true, &done);
+  if (st) {
+    P->run.phase = hz_problem::Run::IDLE;
+    cudaStreamSynchronize(P->stream);
+    return st;
+  }
+  return solve_end(P, history, history_cap, info, ninfo);
 }
 
 bool level_ok(const hz_problem* P, int level, bool allow_coarsest) {
@@ -492,6 +675,10 @@ bool level_ok(const hz_problem* P, int level, bool allow_coarsest) {
 // Level-l right-hand side in working form (h^2-scaled) from a physical FP64 array.
 cudaError_t import_rhs(hz_problem* P, int l, const double* f, Src* out) {
   double H = P->lv[l].H;
+  if (l == 0 && P->plan.fp32) {
+    *out = Src{P->kv.p32, P->n + 1, false};
+    return launch_import(true, P->kv.p32, P->n + 1, (const double2*)f, P->n + 1, P->n, H * H, P->stream);
+  }
   if (l == 0) {
     *out = Src{P->kv.tr, P->n + 1, true};
     return launch_import(false, P->kv.tr, P->n + 1, (const double2*)f, P->n + 1, P->n, H * H, P->stream);
@@ -539,7 +726,7 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
 
 bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
-           o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0);
+           o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024);
 }
 
 }  // namespace
@@ -557,6 +744,7 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->nu_kacz = 4;
   o->guard = 1;
   o->k_ref = 0.0;
+  o->batch = 1;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {
@@ -596,6 +784,9 @@ static void release(hz_problem* P) {
   for (auto& e : P->ev) if (e) { cudaEventDestroy(e); e = nullptr; }
   if (P->poll_host) { cudaFreeHost(P->poll_host); P->poll_host = nullptr; }
   if (P->ev_in) { cudaEventDestroy(P->ev_in); P->ev_in = nullptr; }
+  if (P->ev_final) { cudaEventDestroy(P->ev_final); P->ev_final = nullptr; }
+  if (P->kstate_host) { cudaFreeHost(P->kstate_host); P->kstate_host = nullptr; }
+  P->run = hz_problem::Run();
   if (P->ev_out) { cudaEventDestroy(P->ev_out); P->ev_out = nullptr; }
   if (P->stream) { cudaStreamSynchronize(P->stream); cudaStreamDestroy(P->stream); P->stream = nullptr; }
   if (P->own_arena && P->arena) cudaFree(P->arena);
@@ -632,10 +823,12 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaMallocHost(&P->poll_host, sizeof(int) * 4 * PIPELINE));
+  CK(cudaMallocHost(&P->poll_host, sizeof(int) * 4 * PIPELINE * pl.batch));
   CK(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_final, cudaEventDisableTiming));
+  CK(cudaMallocHost(&P->kstate_host, sizeof(KState) * pl.batch));
   StreamScope scope(P);
   for (auto& e : P->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   unsigned char* A = P->arena;
@@ -659,12 +852,26 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   }
   // Krylov vectors and scratch.
   KrylovVecs& k = P->kv;
-  double2* vb = (double2*)(A + pl.off_vec);
-  size_t stride_v = pl.vec_bytes / sizeof(double2);
-  double2** slots[] = {&k.r, &k.rhat, &k.p, &k.v, &k.s, &k.t, &k.y, &k.z, &k.tr, &P->b_int, &P->x_int};
-  for (int q = 0; q < pl.nvec; ++q) *slots[q] = vb + q * stride_v;
+  unsigned char* vb = A + pl.off_vec;
+  k.rhat = (double2*)vb;
+  vb += pl.rhat_bytes;
+  double2** slots[] = {&k.r, &k.p, &k.v, &k.s, &k.t, &k.y, &k.z, &k.tr, &P->b_int, &P->x_int};
+  for (int q = 0; q < pl.nvec - 1; ++q) *slots[q] = (double2*)(vb + q * pl.vec_bytes);
   k.x = nullptr;
   k.b = nullptr;
+  const long long Nn = (long long)(n + 1) * (n + 1);
+  k.batch = pl.batch;
+  k.sv = Nn;
+  k.part_stride = (long long)PARTIAL_SLOTS * MAX_G;
+  k.hist_stride = HIST_CAP;
+  if (fp32) {  // FP32 copies packed into the y and z slots (16 bytes per node hold two float2 arrays)
+    k.y32 = (float2*)k.y;
+    k.p32 = k.y32 + Nn * pl.batch;
+    k.z32 = (float2*)k.z;
+    k.s32 = k.z32 + Nn * pl.batch;
+  } else {
+    k.p32 = k.s32 = k.y32 = k.z32 = nullptr;
+  }
   k.kh = P->kh64;
   k.n = n;
   k.N = (long long)(n + 1) * (n + 1);
@@ -675,7 +882,7 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   long long want = (k.N + 255) / 256;
   k.G = (int)std::min<long long>(want, std::min(8LL * P->num_sms, (long long)MAX_G));
   if (k.G < 1) k.G = 1;
-  CK(cudaMemsetAsync(k.st, 0, sizeof(KState), s));
+  CK(cudaMemsetAsync(k.st, 0, sizeof(KState) * pl.batch, s));
   CK(launch_shadow(k.rhat, k.N, SHADOW_SEED, s));
   // Coarsest: dense inverse on the device.
   Level& C = P->lv.back();
@@ -734,14 +941,28 @@ hz_status hz_vcycle(hz_problem* P, const double* r, double* z) {
   if (!r || !z || (const double*)r == z) return fail(P, HZ_EINVAL, "bad vcycle arguments");
   StreamScope scope(P);
   double h = 1.0 / P->n;
-  CK(launch_import(false, P->kv.p, P->n + 1, (const double2*)r, P->n + 1, P->n, h * h, P->stream));
-  CK(run_vcycle(P, P->kv.p, (double2*)z, nullptr));
+  if (P->plan.fp32) {
+    CK(launch_import(true, P->kv.p32, P->n + 1, (const double2*)r, P->n + 1, P->n, h * h, P->stream));
+    CK(run_vcycle(P, P->kv.p32, P->kv.y32, nullptr));
+    CK(launch_export(true, (double2*)z, P->n + 1, P->kv.y32, P->n + 1, P->n, 1.0, nullptr, P->stream));
+  } else {
+    CK(launch_import(false, P->kv.p, P->n + 1, (const double2*)r, P->n + 1, P->n, h * h, P->stream));
+    CK(run_vcycle(P, P->kv.p, z, nullptr));
+  }
   return HZ_OK;
+}
+
+hz_status hz_solve_batch(hz_problem* P, const double* rhs, double* x, double tol, int maxit, hz_solve_info* infos) {
+  if (!P) return HZ_EINVAL;
+  if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
+  StreamScope scope(P);
+  return solve_device(P, rhs, x, tol, maxit, nullptr, 0, infos, P->plan.batch);
 }
 
 hz_status hz_solve(hz_problem* P, const double* rhs, double* x, double tol, int maxit, double* history,
                    int history_cap, hz_solve_info* info) {
   if (!P) return HZ_EINVAL;
+  if (P->setup && P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: use hz_solve_batch");
   StreamScope scope(P);
   return solve_device(P, rhs, x, tol, maxit, history, history_cap, info);
 }
@@ -751,6 +972,7 @@ hz_status hz_solve_host(hz_problem* P, const double* rhs_host, double* x_host, d
   if (!P) return HZ_EINVAL;
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
   if (!rhs_host || !x_host) return fail(P, HZ_EINVAL, "null host pointer");
+  if (P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: use hz_solve_batch");
   StreamScope scope(P);
   size_t bytes = sizeof(double2) * (size_t)(P->n + 1) * (P->n + 1);
   CK(cudaMemcpyAsync(P->b_int, rhs_host, bytes, cudaMemcpyHostToDevice, P->stream));
@@ -759,6 +981,36 @@ hz_status hz_solve_host(hz_problem* P, const double* rhs_host, double* x_host, d
   CK(cudaMemcpyAsync(x_host, P->x_int, bytes, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
   return st;
+}
+
+hz_status hz_solve_start(hz_problem* P, const double* rhs, double* x, double tol, int maxit) {
+  if (!P) return HZ_EINVAL;
+  if (P->setup && P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: use hz_solve_batch");
+  StreamScope scope(P);
+  return solve_begin(P, rhs, x, tol, maxit);
+}
+
+hz_status hz_solve_poll(hz_problem* P, int* done) {
+  if (!P || !done) return HZ_EINVAL;
+  hz_status st = solve_advance(P, false, done);
+  if (st && st != HZ_EINVAL) {
+    P->run.phase = hz_problem::Run::IDLE;
+    cudaStreamSynchronize(P->stream);
+  }
+  return st;
+}
+
+hz_status hz_solve_finish(hz_problem* P, double* history, int history_cap, hz_solve_info* info) {
+  if (!P) return HZ_EINVAL;
+  StreamScope scope(P);
+  int done = 0;
+  hz_status st = solve_advance(P, true, &done);
+  if (st) {
+    P->run.phase = hz_problem::Run::IDLE;
+    cudaStreamSynchronize(P->stream);
+    return st;
+  }
+  return solve_end(P, history, history_cap, info);
 }
 
 hz_status hz_apply(hz_problem* P, int op, const double* u, double* v) {
@@ -797,7 +1049,10 @@ hz_status hz_level_postsmooth(hz_problem* P, int level, const double* f, const d
   bool fp32 = P->plan.fp32;
   CK(launch_import(fp32, L.u, L.pitch, (const double2*)u_pre, L.n + 1, L.n, 1.0, P->stream));
   CK(launch_import(fp32, final_u(P, level + 1), C.pitch, (const double2*)ec, C.n + 1, C.n, 1.0, P->stream));
-  if (level == 0) {
+  if (level == 0 && fp32) {
+    CK(level_up(P, 0, src, P->kv.y32, P->n + 1, nullptr));
+    CK(launch_export(true, (double2*)u, P->n + 1, P->kv.y32, P->n + 1, P->n, 1.0, nullptr, P->stream));
+  } else if (level == 0) {
     CK(level_up(P, 0, src, P->kv.v, P->n + 1, nullptr));
     CK(cudaMemcpyAsync(u, P->kv.v, sizeof(double2) * (size_t)(P->n + 1) * (P->n + 1), cudaMemcpyDeviceToDevice,
                        P->stream));
@@ -869,10 +1124,219 @@ int hz_profile_iteration(hz_problem* P, const double* rhs, double* x, int iterat
   return count;
 }
 
+// ------------------------------------------------------------------ groups of problems
+
+struct hz_group {
+  std::vector<hz_problem*> probs;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t ev[PIPELINE]{};
+  int* flags = nullptr;  // pinned: PIPELINE slots x total instances x 4 ints
+  int total = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const double*> graph_b;
+  std::vector<double*> graph_x;
+  std::string err;
+};
+
+static void group_release(hz_group* g) {
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  for (auto& e : g->ev) if (e) cudaEventDestroy(e);
+  for (auto e : g->join) if (e) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->flags) cudaFreeHost(g->flags);
+  if (g->stream) cudaStreamDestroy(g->stream);
+}
+
+#define GK(call)                                                  \
+  do {                                                            \
+    cudaError_t e__ = (call);                                     \
+    if (e__ != cudaSuccess) {                                     \
+      g->err = std::string(#call) + ": " + cudaGetErrorString(e__); \
+      return HZ_ECUDA;                                            \
+    }                                                             \
+  } while (0)
+
+hz_status hz_group_create(hz_problem* const* probs, int count, hz_group** out) {
+  if (!out || !probs || count < 1) return HZ_EINVAL;
+  *out = nullptr;
+  hz_group* g = new hz_group();
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i] || !probs[i]->setup) { delete g; return HZ_EINVAL; }
+    g->probs.push_back(probs[i]);
+    g->total += probs[i]->plan.batch;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+  g->join.assign(count, nullptr);
+  for (int i = 0; i < count && !e; ++i) e = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming);
+  for (auto& ev : g->ev)
+    if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (!e) e = cudaMallocHost(&g->flags, sizeof(int) * 4 * PIPELINE * g->total);
+  if (e) {
+    group_release(g);
+    delete g;
+    return HZ_ECUDA;
+  }
+  *out = g;
+  return HZ_OK;
+}
+
+// One graph holding one iteration of every problem, each on its own branch.
+static hz_status group_graph(hz_group* g) {
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  GK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(g->fork, g->stream);
+  for (size_t i = 0; i < g->probs.size() && !e; ++i) {
+    hz_problem* P = g->probs[i];
+    e = cudaStreamWaitEvent(P->stream, g->fork, 0);
+    if (!e) e = enqueue_iteration(P);
+    if (!e) e = cudaEventRecord(g->join[i], P->stream);
+    if (!e) e = cudaStreamWaitEvent(g->stream, g->join[i], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+  if (e || e2) {
+    if (graph) cudaGraphDestroy(graph);
+    g->err = std::string("capture of the group iteration: ") + cudaGetErrorString(e ? e : e2);
+    return HZ_ECUDA;
+  }
+  e = cudaGraphInstantiate(&g->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e) {
+    g->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+    return HZ_ECUDA;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x, double tol, int maxit,
+                         hz_solve_info* infos) {
+  if (!g || !rhs || !x || !(tol > 0) || maxit < 1) return HZ_EINVAL;
+  if (maxit > HIST_CAP / 2 - 1) maxit = HIST_CAP / 2 - 1;
+  const size_t np = g->probs.size();
+  bool rebuild = !g->graph || g->graph_b.size() != np;
+  for (size_t i = 0; i < np; ++i) {
+    if (!rhs[i] || !x[i] || (const double*)x[i] == rhs[i]) return HZ_EINVAL;
+    hz_problem* P = g->probs[i];
+    if (P->run.phase != hz_problem::Run::IDLE) return HZ_EINVAL;
+    P->kv.b = (const double2*)rhs[i];
+    P->kv.x = (double2*)x[i];
+    if (!rebuild && (g->graph_b[i] != rhs[i] || g->graph_x[i] != x[i])) rebuild = true;
+  }
+  if (rebuild) {
+    hz_status st = group_graph(g);
+    if (st) return st;
+    g->graph_b.assign(rhs, rhs + np);
+    g->graph_x.assign(x, x + np);
+  }
+  // order after the callers' streams, then the start-up of every problem
+  for (size_t i = 0; i < np; ++i) {
+    hz_problem* P = g->probs[i];
+    GK(cudaEventRecord(P->ev_in, P->user_stream));
+    GK(cudaStreamWaitEvent(g->stream, P->ev_in, 0));
+  }
+  GK(cudaEventRecord(g->fork, g->stream));
+  for (size_t i = 0; i < np; ++i) {
+    hz_problem* P = g->probs[i];
+    GK(cudaStreamWaitEvent(P->stream, g->fork, 0));
+    GK(launch_k_init(P->kv, tol, maxit, HIST_CAP, P->stream));
+    GK(cudaEventRecord(g->join[i], P->stream));
+    GK(cudaStreamWaitEvent(g->stream, g->join[i], 0));
+  }
+  int restarts = 0;
+  for (;;) {
+    long long launched = 0, polled = 0;
+    const long long cap = (long long)maxit + 2;
+    bool done = false;
+    while (!done) {
+      if (launched < cap && launched - polled < PIPELINE) {
+        GK(cudaGraphLaunch(g->graph, g->stream));
+        int slot = (int)(launched % PIPELINE), off = 0;
+        for (size_t i = 0; i < np; ++i) {
+          hz_problem* P = g->probs[i];
+          GK(cudaMemcpy2DAsync(g->flags + 4 * (g->total * slot + off), 4 * sizeof(int), &P->kv.st->it, sizeof(KState),
+                               4 * sizeof(int), P->plan.batch, cudaMemcpyDeviceToHost, g->stream));
+          off += P->plan.batch;
+        }
+        GK(cudaEventRecord(g->ev[slot], g->stream));
+        ++launched;
+        continue;
+      }
+      int slot = (int)(polled % PIPELINE);
+      GK(cudaEventSynchronize(g->ev[slot]));
+      ++polled;
+      bool all = true;
+      for (int q = 0; q < g->total && all; ++q) all = g->flags[4 * (g->total * slot + q) + 2] != 0;
+      if (all || (polled >= launched && launched >= cap)) done = true;
+    }
+    // true residuals and final states
+    GK(cudaEventRecord(g->fork, g->stream));
+    for (size_t i = 0; i < np; ++i) {
+      hz_problem* P = g->probs[i];
+      GK(cudaStreamWaitEvent(P->stream, g->fork, 0));
+      GK(launch_k_true_residual(P->kv, P->stream));
+      GK(cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * P->plan.batch, cudaMemcpyDeviceToHost, P->stream));
+    }
+    for (size_t i = 0; i < np; ++i) GK(cudaStreamSynchronize(g->probs[i]->stream));
+    bool restarted = false;
+    if (restarts < 8) {
+      for (size_t i = 0; i < np; ++i) {
+        hz_problem* P = g->probs[i];
+        for (int b = 0; b < P->plan.batch; ++b) {
+          const KState& hs = P->kstate_host[b];
+          if (hs.done == 1 && hs.bnorm2 > 0 && !(hs.trr <= hs.tol2) && hs.it < maxit) {
+            GK(launch_k_restart(instance_of(P->kv, b), P->stream));
+            restarted = true;
+          }
+        }
+        GK(cudaEventRecord(g->join[i], P->stream));
+        GK(cudaStreamWaitEvent(g->stream, g->join[i], 0));
+      }
+    }
+    if (!restarted) break;
+    ++restarts;
+  }
+  hz_status worst = HZ_OK;
+  int q = 0;
+  for (size_t i = 0; i < np; ++i) {
+    hz_problem* P = g->probs[i];
+    for (int b = 0; b < P->plan.batch; ++b, ++q) {
+      const KState& hs = P->kstate_host[b];
+      double it = 0;
+      hz_status sb = instance_status(hs, maxit, &it);
+      if (sb != HZ_OK && worst == HZ_OK) worst = sb;
+      if (infos) {
+        infos[q].iterations = it;
+        infos[q].relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.trr / hs.bnorm2) : 0.0;
+        infos[q].history_len = 0;
+        infos[q].status = sb;
+        infos[q].restarts = restarts;
+      }
+    }
+  }
+  for (size_t i = 0; i < np; ++i) g->probs[i]->graph_b = nullptr;  // their own graphs hold other buffers
+  return worst;
+}
+
+const char* hz_group_last_error(const hz_group* g) { return g ? g->err.c_str() : "null group"; }
+
+void hz_group_destroy(hz_group* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  group_release(g);
+  delete g;
+}
+
 const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s", "k_x_half",
-                                "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth"};
+                                "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
+                                "kacz_sweep"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -29,11 +29,47 @@ __host__ __device__ __forceinline__ c2<T> mk(T re, T im) {
   return z;
 }
 
+// Conversions between binary64 and binary32 on the integer pipe. GB300 runs hardware float
+// conversions on its narrow FP64 pipe, which the FP32 V-cycle would otherwise saturate just
+// reading and writing the FP64 Krylov vectors. Written from the IEEE 754 formats: narrowing
+// rounds to nearest, ties to even, on the 29 dropped significand bits (a carry into the exponent
+// is the correct rounding); results below the binary32 normal range become signed zero;
+// overflow gives infinity; NaN stays NaN. Widening is exact for normal numbers and zero
+// (subnormal binary32 inputs become signed zero).
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0x7FF) return __int_as_float((int)(sign | 0x7F800000u | ((b & 0x000FFFFFFFFFFFFFull) ? 0x400000u : 0u)));
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return __int_as_float((int)sign);
+  const unsigned int m = (unsigned int)((b >> 29) & 0x7FFFFFu);
+  const unsigned int rem = (unsigned int)(b & 0x1FFFFFFFu);
+  unsigned int mag = ((unsigned int)ef << 23) | m;
+  mag += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  if (mag >= 0x7F800000u) mag = 0x7F800000u;
+  return __int_as_float((int)(sign | mag));
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int u = (unsigned int)__float_as_int(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned int e = (u >> 23) & 0xFF;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long eb = (e == 0xFF) ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (eb << 52) | m));
+}
+
 // Load a complex element stored as double2 or float2 and convert it to precision T.
 template <class T>
 __device__ __forceinline__ c2<T> ldc(const double2* p, long long i) {
   double2 v = p[i];
   return mk<T>((T)v.x, (T)v.y);
+}
+template <>
+__device__ __forceinline__ c2<float> ldc<float>(const double2* p, long long i) {
+  double2 v = p[i];
+  return mk<float>(f64_to_f32(v.x), f64_to_f32(v.y));
 }
 template <class T>
 __device__ __forceinline__ c2<T> ldc(const float2* p, long long i) {
@@ -43,6 +79,10 @@ __device__ __forceinline__ c2<T> ldc(const float2* p, long long i) {
 template <class T>
 __device__ __forceinline__ void stc(double2* p, long long i, c2<T> v) {
   p[i] = make_double2((double)v.x, (double)v.y);
+}
+template <>
+__device__ __forceinline__ void stc<float>(double2* p, long long i, c2<float> v) {
+  p[i] = make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
 }
 template <class T>
 __device__ __forceinline__ void stc(float2* p, long long i, c2<T> v) {
@@ -61,9 +101,13 @@ template <class T>
 __device__ __forceinline__ c2<T> cmulc(c2<T> a, c2<T> b) {
   return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// 1/x: IEEE division in FP64; the correctly rounded single-precision reciprocal in FP32.
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+
 template <class T>
 __device__ __forceinline__ c2<T> cdiv(c2<T> a, c2<T> b) {
-  T inv = (T)1 / (b.x * b.x + b.y * b.y);
+  T inv = rcp(b.x * b.x + b.y * b.y);
   return mk<T>((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
 }
 template <class T> __device__ __forceinline__ T cabs2(c2<T> a) { return a.x * a.x + a.y * a.y; }

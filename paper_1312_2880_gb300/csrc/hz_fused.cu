@@ -43,12 +43,148 @@ __device__ __forceinline__ c2<T> nb_sum(const c2<T>* s, int rw, int c, int r, in
                  cadd<T>(s[(b.js - gy) * rw + c], s[(b.jn - gy) * rw + c]));
 }
 
+// ---------------------------------------------------------------- interior tiles
+// Tiles whose region lies strictly inside the square (no boundary rows, no mirrors, every node
+// present) run these paths: a 32 x 8 thread layout walks rows and columns with fixed strides,
+// so there is no index division and no per-node bounds or boundary logic.
+
+constexpr int TXN = 32, TYN = 8;
+
+template <class T, class F2>
+__device__ __forceinline__ void smooth_restrict_inner(c2<T>* __restrict__ u, int pu, c2<T>* __restrict__ fc, int pc,
+                                                      const F2* __restrict__ f, int pf, const T* __restrict__ kh,
+                                                      int pk, T bA, T bB, c2<T>* su, c2<T>* sf, T* sk, int gx,
+                                                      int gy) {
+  constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
+  constexpr int RW = W + 5, RH = HH + 5;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < RH; r += TYN) {
+    const F2* fr = f + (long long)(gy + r) * pf + gx;
+    const T* kr = kh + (long long)(gy + r) * pk + gx;
+    for (int c = tx; c < RW; c += TXN) {
+      sf[r * RW + c] = ldc<T>(fr, c);
+      sk[r * RW + c] = kr[c];
+    }
+  }
+  __syncthreads();
+  // red nodes everywhere: u = f~ / d (zero guess)
+  for (int r = ty; r < RH; r += TYN) {
+    const int par = (0 - gx - gy - r) & 1;
+    for (int c = 2 * tx + par; c < RW; c += 2 * TXN) {
+      const int q = r * RW + c;
+      const T k = sk[q], k2 = k * k;
+      su[q] = cdiv<T>(sf[q], mk<T>(k2 - (T)4, bA * k2));
+    }
+  }
+  __syncthreads();
+  // black nodes one in from the edge
+  for (int r = 1 + ty; r < RH - 1; r += TYN) {
+    const int par = (1 - gx - gy - r) & 1;
+    for (int c = 2 * tx + par; c < RW - 1; c += 2 * TXN) {
+      if (c < 1) continue;
+      const int q = r * RW + c;
+      const T k = sk[q], k2 = k * k;
+      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
+      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+    }
+  }
+  __syncthreads();
+  // owned nodes out; residual f~ - B u two in from the edge, into sf
+  for (int r = 3 + ty; r < 3 + HH; r += TYN) {
+    c2<T>* ur = u + (long long)(gy + r) * pu + gx;
+    for (int c = 3 + tx; c < 3 + W; c += TXN) ur[c] = su[r * RW + c];
+  }
+  for (int r = 2 + ty; r < RH - 2; r += TYN) {
+    for (int c = 2 + tx; c < RW - 2; c += TXN) {
+      const int q = r * RW + c;
+      const T k = sk[q], k2 = k * k;
+      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
+      c2<T> au = cadd<T>(cmul<T>(mk<T>(k2 - (T)4, bB * k2), su[q]), nb);
+      sf[q] = csub<T>(sf[q], au);
+    }
+  }
+  __syncthreads();
+  // full weighting: one coarse node per (tx, row step)
+  const int I0 = (gx + 3) / 2, J0 = (gy + 3) / 2;
+  for (int Jl = ty; Jl < HH / 2; Jl += TYN) {
+    for (int Il = tx; Il < W / 2; Il += TXN) {
+      const int q = (2 * Jl + 3) * RW + (2 * Il + 3);
+      c2<T> top = cadd<T>(cadd<T>(sf[q - RW - 1], sf[q - RW + 1]), cscale<T>(sf[q - RW], (T)2));
+      c2<T> mid = cadd<T>(cadd<T>(sf[q - 1], sf[q + 1]), cscale<T>(sf[q], (T)2));
+      c2<T> bot = cadd<T>(cadd<T>(sf[q + RW - 1], sf[q + RW + 1]), cscale<T>(sf[q + RW], (T)2));
+      c2<T> acc = cadd<T>(cadd<T>(top, bot), cscale<T>(mid, (T)2));
+      fc[(long long)(J0 + Jl) * pc + I0 + Il] = cscale<T>(acc, (T)0.25);
+    }
+  }
+}
+
+template <class T, class F2, class O2>
+__device__ __forceinline__ void prolong_smooth_inner(O2* __restrict__ out, int po, const c2<T>* __restrict__ upre,
+                                                     int pu, const c2<T>* __restrict__ ec, int pc,
+                                                     const F2* __restrict__ f, int pf, const T* __restrict__ kh,
+                                                     int pk, T bA, c2<T>* su, c2<T>* sf, T* sk, int gx, int gy) {
+  constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
+  constexpr int RW = W + 4, RH = HH + 4;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < RH; r += TYN) {
+    const int j = gy + r, J = j >> 1, oj = j & 1;
+    const F2* fr = f + (long long)j * pf + gx;
+    const T* kr = kh + (long long)j * pk + gx;
+    const c2<T>* ur = upre + (long long)j * pu + gx;
+    const c2<T>* e0 = ec + (long long)J * pc;
+    const c2<T>* e1 = e0 + pc;
+    for (int c = tx; c < RW; c += TXN) {
+      const int i = gx + c, I = i >> 1, oi = i & 1;
+      c2<T> e = e0[I];
+      if (oi) e = cadd<T>(e, e0[I + 1]);
+      if (oj) {
+        e = cadd<T>(e, e1[I]);
+        if (oi) e = cadd<T>(e, e1[I + 1]);
+      }
+      const T wgt = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
+      su[r * RW + c] = cadd<T>(ur[c], cscale<T>(e, wgt));
+      sf[r * RW + c] = ldc<T>(fr, c);
+      sk[r * RW + c] = kr[c];
+    }
+  }
+  __syncthreads();
+  for (int r = 1 + ty; r < RH - 1; r += TYN) {  // black, one in from the edge
+    const int par = (1 - gx - gy - r) & 1;
+    for (int c = 2 * tx + par; c < RW - 1; c += 2 * TXN) {
+      if (c < 1) continue;
+      const int q = r * RW + c;
+      const T k = sk[q], k2 = k * k;
+      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
+      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+    }
+  }
+  __syncthreads();
+  for (int r = 2 + ty; r < 2 + HH; r += TYN) {  // red on the owned tile
+    const int par = (0 - gx - gy - r) & 1;
+    for (int c = 2 * tx + par; c < 2 + W; c += 2 * TXN) {
+      if (c < 2) continue;
+      const int q = r * RW + c;
+      const T k = sk[q], k2 = k * k;
+      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
+      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+    }
+  }
+  __syncthreads();
+  for (int r = 2 + ty; r < 2 + HH; r += TYN) {
+    O2* orow = out + (long long)(gy + r) * po + gx;
+    for (int c = 2 + tx; c < 2 + W; c += TXN) stc<T>(orow, c, su[r * RW + c]);
+  }
+}
+
 template <class T, class F2>
 __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__ u, int pu, c2<T>* __restrict__ fc,
                                                               int pc, const F2* __restrict__ f, int pf,
                                                               const T* __restrict__ kh, int pk, int n, T bA, T bB,
-                                                              const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                                              const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  fc += blockIdx.z * bi.sc;
+  f += blockIdx.z * bi.sf;
   constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
   constexpr int RW = W + 5, RH = HH + 5, RN = RW * RH, HW = (RW + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -57,7 +193,12 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   T* sk = reinterpret_cast<T*>(sf + RN);
   const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
   const int gx = x0 - 3, gy = y0 - 3;
-  for (int q = threadIdx.x; q < RN; q += FT) {
+  if (gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
+    smooth_restrict_inner<T, F2>(u, pu, fc, pc, f, pf, kh, pk, bA, bB, su, sf, sk, gx, gy);
+    return;
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (in_grid(i, j, n)) {
       sf[q] = ldc<T>(f, (long long)j * pf + i);
@@ -66,7 +207,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   }
   __syncthreads();
   // red nodes of the whole region: zero neighbours, u = f~ / d
-  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+  for (int q = tid; q < RH * HW; q += FT) {
     int r = q / HW, m = q - r * HW;
     int j = gy + r;
     int c = 2 * m + ((0 - gx - j) & 1);
@@ -78,7 +219,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   }
   __syncthreads();
   // black nodes one in from the region edge
-  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+  for (int q = tid; q < RH * HW; q += FT) {
     int r = q / HW, m = q - r * HW;
     int j = gy + r;
     int c = 2 * m + ((1 - gx - j) & 1);
@@ -91,13 +232,13 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   }
   __syncthreads();
   // write the owned nodes; residual f~ - B u two in from the edge (into sf)
-  for (int q = threadIdx.x; q < RN; q += FT) {
+  for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (!in_grid(i, j, n)) continue;
     if (r >= 3 && r < 3 + HH && c >= 3 && c < 3 + W) u[(long long)j * pu + i] = su[q];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < RN; q += FT) {
+  for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (r >= 2 && r <= RH - 3 && c >= 2 && c <= RW - 3 && in_grid(i, j, n)) {
       Nbr b = neighbours(i, j, n);
@@ -109,7 +250,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   __syncthreads();
   // full weighting onto the owned coarse nodes
   const int nc = n / 2;
-  for (int q = threadIdx.x; q < (W / 2) * (HH / 2); q += FT) {
+  for (int q = tid; q < (W / 2) * (HH / 2); q += FT) {
     int J = y0 / 2 + q / (W / 2), I = x0 / 2 + q % (W / 2);
     if (I > nc || J > nc) continue;
     c2<T> acc = mk<T>(0, 0);
@@ -133,8 +274,12 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
                                                              int pu, const c2<T>* __restrict__ ec, int pc,
                                                              const F2* __restrict__ f, int pf,
                                                              const T* __restrict__ kh, int pk, int n, T bA,
-                                                             const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                                             const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  out += blockIdx.z * bi.so;
+  upre += blockIdx.z * bi.su;
+  ec += blockIdx.z * bi.sc;
+  f += blockIdx.z * bi.sf;
   constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
   constexpr int RW = W + 4, RH = HH + 4, RN = RW * RH, HW = RW / 2;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -143,7 +288,12 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   T* sk = reinterpret_cast<T*>(sf + RN);
   const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
   const int gx = x0 - 2, gy = y0 - 2;
-  for (int q = threadIdx.x; q < RN; q += FT) {
+  if (gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
+    prolong_smooth_inner<T, F2, O2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, bA, su, sf, sk, gx, gy);
+    return;
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (in_grid(i, j, n)) {
       int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
@@ -161,7 +311,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   }
   __syncthreads();
   // black nodes one in from the region edge
-  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+  for (int q = tid; q < RH * HW; q += FT) {
     int r = q / HW, m = q - r * HW;
     int j = gy + r;
     int c = 2 * m + ((1 - gx - j) & 1);
@@ -174,7 +324,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   }
   __syncthreads();
   // red nodes of the owned tile
-  for (int q = threadIdx.x; q < RH * HW; q += FT) {
+  for (int q = tid; q < RH * HW; q += FT) {
     int r = q / HW, m = q - r * HW;
     int j = gy + r;
     int c = 2 * m + ((0 - gx - j) & 1);
@@ -186,7 +336,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
     }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < RN; q += FT) {
+  for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (r >= 2 && r < 2 + HH && c >= 2 && c < 2 + W && in_grid(i, j, n)) stc<T>(out, (long long)j * po + i, su[q]);
   }
@@ -203,7 +353,7 @@ constexpr size_t ps_smem() {
 
 template <class T, class F2>
 cudaError_t sr_t(void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh, int pk, int n, double bA,
-                 double bB, const int* stop, cudaStream_t s) {
+                 double bB, const int* stop, cudaStream_t s, const Inst& bi) {
   constexpr size_t sm = sr_smem<T>();
   static bool attr = false;
   if (!attr) {
@@ -213,15 +363,15 @@ cudaError_t sr_t(void* u, int pu, void* fc, int pc, const void* f, int pf, const
   }
   constexpr int CW = TileShape<T>::W / 2, CH = TileShape<T>::H / 2;
   int nc = n / 2;
-  dim3 grid((nc + CW) / CW, (nc + CH) / CH);
-  smooth_restrict_kernel<T, F2><<<grid, FT, sm, s>>>((c2<T>*)u, pu, (c2<T>*)fc, pc, (const F2*)f, pf, (const T*)kh, pk,
-                                                    n, (T)bA, (T)bB, stop);
+  dim3 grid((nc + CW) / CW, (nc + CH) / CH, bi.count);
+  smooth_restrict_kernel<T, F2><<<grid, dim3(TXN, TYN), sm, s>>>((c2<T>*)u, pu, (c2<T>*)fc, pc, (const F2*)f, pf,
+                                                                (const T*)kh, pk, n, (T)bA, (T)bB, stop, bi);
   return cudaGetLastError();
 }
 
 template <class T, class F2, class O2>
 cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, int pc, const void* f, int pf,
-                 const void* kh, int pk, int n, double bA, const int* stop, cudaStream_t s) {
+                 const void* kh, int pk, int n, double bA, const int* stop, cudaStream_t s, const Inst& bi) {
   constexpr size_t sm = ps_smem<T>();
   static bool attr = false;
   if (!attr) {
@@ -231,9 +381,10 @@ cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, in
     attr = true;
   }
   constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
-  dim3 grid((n + W) / W, (n + HH) / HH);
-  prolong_smooth_kernel<T, F2, O2><<<grid, FT, sm, s>>>((O2*)out, po, (const c2<T>*)upre, pu, (const c2<T>*)ec, pc,
-                                                        (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop);
+  dim3 grid((n + W) / W, (n + HH) / HH, bi.count);
+  prolong_smooth_kernel<T, F2, O2><<<grid, dim3(TXN, TYN), sm, s>>>((O2*)out, po, (const c2<T>*)upre, pu,
+                                                                    (const c2<T>*)ec, pc, (const F2*)f, pf,
+                                                                    (const T*)kh, pk, n, (T)bA, stop, bi);
   return cudaGetLastError();
 }
 
@@ -241,19 +392,18 @@ cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, in
 
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
-                                   cudaStream_t s) {
-  if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
-  if (f64_src) return sr_t<float, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
-  return sr_t<float, float2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s);
+                                   cudaStream_t s, const Inst& bi) {
+  if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
+  if (f64_src) return cudaErrorInvalidValue;  // the FP32 form's inputs are FP32
+  return sr_t<float, float2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
 }
 
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
-                                  const int* stop, cudaStream_t s) {
-  if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
-  if (f64_src && out_f64) return ps_t<float, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
-  if (!f64_src && !out_f64) return ps_t<float, float2, float2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s);
-  return cudaErrorInvalidValue;
+                                  const int* stop, cudaStream_t s, const Inst& bi) {
+  if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
+  if (f64_src || out_f64) return cudaErrorInvalidValue;  // the FP32 form's inputs and outputs are FP32
+  return ps_t<float, float2, float2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
 }
 
 }  // namespace hz

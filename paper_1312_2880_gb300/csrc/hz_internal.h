@@ -10,6 +10,17 @@
 
 namespace hz {
 
+// Instances of one launch (multi right-hand-side batches): blockIdx.z selects the instance and
+// every per-instance array advances by its stride in elements. su: the level's own arrays (u, u2,
+// and f below the finest grid); sf: the right-hand side f; sc: the coarse level's arrays (fc,
+// e_c); so: the output of the finest-grid post-sweep. The k h arrays and the coarsest inverse are
+// shared. stop_stride: ints between the instances' stop flags.
+struct Inst {
+  int count = 1;
+  long long su = 0, sf = 0, sc = 0, so = 0;
+  int stop_stride = 0;
+};
+
 // ---------------------------------------------------------------- V-cycle kernel launchers
 // `fp32` selects the working precision of the level arrays (float2/float instead of
 // double2/double). `f64_src` says the right-hand side f is a double2 array even when fp32 is
@@ -18,27 +29,39 @@ namespace hz {
 // turn the queued iterations after convergence into no-ops).
 
 cudaError_t launch_gs_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
-                             int pk, int n, int colour, double beta, const int* stop, cudaStream_t s);
+                             int pk, int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_gs_first(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                            int n, int colour, double beta, const int* stop, cudaStream_t s);
+                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_kacz_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
-                               int pk, int n, int colour, double beta, const int* stop, cudaStream_t s);
+                               int pk, int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_restrict_residual(bool fp32, void* fc, int pc, const void* u, int pu, const void* f, int pf,
                                      bool f64_src, const void* kh, int pk, int n, double beta, const int* stop,
-                                     cudaStream_t s);
+                                     cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_prolong_add(bool fp32, void* u, int pu, const void* ec, int pc, int n, const int* stop,
-                               cudaStream_t s);
+                               cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int pf, const void* ainvT, int nc,
-                                const int* stop, cudaStream_t s);
+                                const int* stop, cudaStream_t s, const Inst& bi = Inst());
 // Fused passes for a Gauss-Seidel level with one sweep each way (hz_fused.cu). smooth_restrict
 // writes u (pre-sweep from a zero guess) and fc (coarse right-hand side, h^2-scaled for the
 // coarse level); prolong_smooth writes out = post-sweep(upre + P ec), as double2 when out_f64.
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
-                                  const int* stop, cudaStream_t s);
+                                  const int* stop, cudaStream_t s, const Inst& bi = Inst());
+// Kaczmarz level kernels (hz_kaczmarz.cu). The whole-level pair keeps the level in one block's
+// shared memory (at most KACZ_LEVEL_MAX_SMEM bytes: 20 or 40 bytes per node); the tile kernel runs
+// one five-colour sweep per launch, out of place (uin may be null for a zero guess).
+constexpr int KACZ_LEVEL_MAX_SMEM = 200 * 1024;
+bool kacz_level_fits(bool fp32, int n);
+cudaError_t launch_kacz_level_pre(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
+                                  int pk, int n, double bA, double bB, int nu, const int* stop, cudaStream_t s, const Inst& bi = Inst());
+cudaError_t launch_kacz_level_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
+                                   const void* kh, int pk, int n, double bA, int nu, const int* stop, cudaStream_t s, const Inst& bi = Inst());
+cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
+                                   bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
+                                   cudaStream_t s, const Inst& bi = Inst());
 // dst (precision of fp32, pitch pd) = src (double2, pitch ps) * scale, on an (n+1)^2 grid.
 cudaError_t launch_import(bool fp32, void* dst, int pd, const double2* src, int ps, int n, double scale,
                           cudaStream_t s);
@@ -74,16 +97,30 @@ enum { KT_INIT = 0, KT_RV, KT_S, KT_XHALF, KT_TS, KT_XR, KT_TRUE, KT_RESTART };
 
 struct KrylovVecs {
   double2 *x, *r, *rhat, *p, *v, *s, *t, *y, *z, *tr;
+  // FP32 V-cycle form: the preconditioner reads p32/s32 (p and s rounded to FP32 by the FP64
+  // kernels that produce them) and writes y32 = K p, z32 = K s, which are computed in FP32 and
+  // so held exactly in FP32; the FP64 kernels widen them in registers. Null in the FP64 form.
+  float2 *p32, *s32, *y32, *z32;
   const double2* b;
   const double* kh;  // k h on the finest grid, pitch n+1
   int n;
   long long N;
   double scale_b;  // h^2: the solver works on the h^2-scaled system
-  KState* st;
-  double* partials;  // [8][G]
-  double* hist;
-  int G;  // reduction grid size
+  KState* st;        // [batch]
+  double* partials;  // [batch][part_stride]
+  double* hist;      // [batch][hist_stride]
+  int G;             // reduction grid size
+  // Batches of right-hand sides: instance b (blockIdx.z) uses every vector (b, x, r, p, v, s, t,
+  // y, z, tr and the FP32 copies) advanced by b * sv elements, its own state, partials and
+  // history; the shadow residual and k h are shared.
+  int batch = 1;
+  long long sv = 0;
+  long long part_stride = 0;
+  int hist_stride = 0;
 };
+
+// The vectors and state of instance b (host side, for launches that touch a single instance).
+KrylovVecs instance_of(const KrylovVecs& k, int b);
 
 cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s);
@@ -94,7 +131,7 @@ cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s);
-cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s);  // every instance of k (use instance_of for one)
 // v = A u (scaled by out_scale) on the finest grid in FP64; beta = 0 for L, the shift for M.
 cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, int n, double beta, double out_scale,
                               cudaStream_t s);

@@ -36,6 +36,15 @@ __device__ __forceinline__ double2 d2div(double2 a, double2 b) {
 __device__ __forceinline__ double2 d2mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// Preconditioned vectors: FP64, or FP32 widened exactly (integer pipe, see f32_to_f64).
+__device__ __forceinline__ double2 ldy(const double2* p, int e) { return p[e]; }
+__device__ __forceinline__ double2 ldy(const float2* p, int e) {
+  float2 v = p[e];
+  return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+}
+// FP64 value rounded to FP32 for the FP32 V-cycle (integer pipe, see f64_to_f32).
+__device__ __forceinline__ float2 narrow(double2 v) { return make_float2(f64_to_f32(v.x), f64_to_f32(v.y)); }
+
 __device__ __forceinline__ bool fin(double v) { return isfinite(v); }
 __device__ __forceinline__ bool fin2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
 
@@ -100,16 +109,45 @@ __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket
   return true;
 }
 
-// (h^2 A y)_e at flat index e of the finest grid (pitch n+1), A = L (beta = 0) or M.
-__device__ __forceinline__ double2 apply_at(const double2* __restrict__ y, const double* __restrict__ kh, int e,
-                                            int n, double beta) {
+// (h^2 A y) at node (i, j) = flat index e of the finest grid (pitch n+1), A = L (beta = 0) or M.
+// The FP64 pipe bounds these kernels, so interior nodes of L take the real-diagonal path:
+// d = (kh)^2 - 4 (one FMA) and v = nb + d y (two FMAs); boundary nodes and M use the complex row.
+template <class Y2>
+__device__ __forceinline__ double2 apply_at(const Y2* __restrict__ y, const double* __restrict__ kh, int e, int i,
+                                            int j, int n, double beta) {
   const int w = n + 1;
-  const int j = e / w, i = e - j * w;
   Nbr b = neighbours(i, j, n);
-  double2 nb = d2add(d2add(y[j * w + b.iw], y[j * w + b.ie]), d2add(y[b.js * w + i], y[b.jn * w + i]));
-  double2 d = row_diag<double>(kh[e], b.sides, beta);
-  return d2add(d2mul(d, y[e]), nb);
+  double2 nb = d2add(d2add(ldy(y, j * w + b.iw), ldy(y, j * w + b.ie)), d2add(ldy(y, b.js * w + i), ldy(y, b.jn * w + i)));
+  const double k = kh[e];
+  const double2 ye = ldy(y, e);
+  if (b.sides == 0 && beta == 0.0) {
+    const double dr = fma(k, k, -4.0);
+    return make_double2(fma(dr, ye.x, nb.x), fma(dr, ye.y, nb.y));
+  }
+  double2 d = row_diag<double>(k, b.sides, beta);
+  return d2add(d2mul(d, ye), nb);
 }
+
+// Grid-stride walk over the (n+1)^2 nodes that keeps (i, j) up to date without dividing per node.
+struct NodeWalk {
+  int e, i, j, di, dj, w, stride;
+  __device__ __forceinline__ NodeWalk(int n, int stride_) : w(n + 1), stride(stride_) {
+    e = blockIdx.x * blockDim.x + threadIdx.x;
+    j = e / w;
+    i = e - j * w;
+    dj = stride / w;
+    di = stride - dj * w;
+  }
+  __device__ __forceinline__ void next() {
+    e += stride;
+    i += di;
+    j += dj;
+    if (i >= w) {
+      i -= w;
+      ++j;
+    }
+  }
+};
 
 __device__ __forceinline__ void hist_push(KState* st, double* hist, double v) {
   if (st->hist_len < st->hist_cap) hist[st->hist_len] = v;
@@ -117,6 +155,20 @@ __device__ __forceinline__ void hist_push(KState* st, double* hist, double v) {
 }
 
 #define GRID_STRIDE(e, N) for (int e = blockIdx.x * KB + threadIdx.x; e < (N); e += gridDim.x * KB)
+
+__host__ __device__ __forceinline__ KrylovVecs offset_instance(KrylovVecs k, long long b) {
+  if (b) {
+    const long long o = b * k.sv;
+    k.x += o; k.r += o; k.p += o; k.v += o; k.s += o; k.t += o; k.y += o; k.z += o; k.tr += o; k.b += o;
+    if (k.p32) { k.p32 += o; k.s32 += o; k.y32 += o; k.z32 += o; }
+    k.st += b;
+    k.partials += b * k.part_stride;
+    k.hist += b * k.hist_stride;
+  }
+  return k;
+}
+// This block's instance (blockIdx.z).
+__device__ __forceinline__ KrylovVecs instance(const KrylovVecs& k) { return offset_instance(k, blockIdx.z); }
 
 __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long seed) {
   // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c + 1 of the generator
@@ -137,6 +189,7 @@ __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long see
 
 // x = 0, r = h^2 b, p = v = 0; |r|^2 and <r^, r> start the iteration.
 __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap) {
+  k = instance(k);
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
   GRID_STRIDE(e, N) {
@@ -179,6 +232,7 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
 
 // p = r (first step after a start or restart) or p = r + beta (p - omega v).
 __global__ void k_update_p_kernel(KrylovVecs k) {
+  k = instance(k);
   KState* st = k.st;
   if (st->done) return;
   if (st->it > st->maxit) {
@@ -190,23 +244,30 @@ __global__ void k_update_p_kernel(KrylovVecs k) {
   const double2 beta = st->beta, omega = st->omega;
   GRID_STRIDE(e, N) {
     double2 r = k.r[e];
+    double2 p;
     if (first) {
-      k.p[e] = r;
+      p = r;
     } else {
       double2 q = d2axmy(k.p[e], omega, k.v[e]);
-      k.p[e] = d2axpy(r, beta, q);
+      p = d2axpy(r, beta, q);
     }
+    k.p[e] = p;
+    if (k.p32) k.p32[e] = narrow(p);
   }
 }
 
 // v = A y with <r^, v>; alpha = rho / <r^, v>.
-__global__ void k_apply_rv_kernel(KrylovVecs k) {
+template <class Y2>
+__global__ void k_apply_rv_kernel(KrylovVecs k, const Y2* __restrict__ y) {
+  k = instance(k);
+  y += blockIdx.z * k.sv;
   KState* st = k.st;
   if (st->done) return;
   double acc[2] = {0.0, 0.0};
   const int N = (int)k.N;
-  GRID_STRIDE(e, N) {
-    double2 v = apply_at(k.y, k.kh, e, k.n, 0.0);
+  for (NodeWalk it(k.n, gridDim.x * KB); it.e < N; it.next()) {
+    const int e = it.e;
+    double2 v = apply_at(y, k.kh, e, it.i, it.j, k.n, 0.0);
     k.v[e] = v;
     double2 rh = k.rhat[e];
     acc[0] = fma(rh.x, v.x, fma(rh.y, v.y, acc[0]));
@@ -230,6 +291,7 @@ __global__ void k_apply_rv_kernel(KrylovVecs k) {
 
 // s = r - alpha v with |s|^2; stop after the half step when |s| <= tol |b|.
 __global__ void k_update_s_kernel(KrylovVecs k) {
+  k = instance(k);
   KState* st = k.st;
   if (st->done) return;
   double acc[1] = {0.0};
@@ -238,6 +300,7 @@ __global__ void k_update_s_kernel(KrylovVecs k) {
   GRID_STRIDE(e, N) {
     double2 s = d2axmy(k.r[e], alpha, k.v[e]);
     k.s[e] = s;
+    if (k.s32) k.s32[e] = narrow(s);
     acc[0] = fma(s.x, s.x, fma(s.y, s.y, acc[0]));
   }
   double tot[1];
@@ -256,12 +319,15 @@ __global__ void k_update_s_kernel(KrylovVecs k) {
 }
 
 // After a half-step stop: x += alpha y, once.
-__global__ void k_x_half_kernel(KrylovVecs k) {
+template <class Y2>
+__global__ void k_x_half_kernel(KrylovVecs k, const Y2* __restrict__ y) {
+  k = instance(k);
+  y += blockIdx.z * k.sv;
   KState* st = k.st;
   if (st->half != 1) return;
   const double2 alpha = st->alpha;
   const int N = (int)k.N;
-  GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, k.y[e]); }
+  GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, ldy(y, e)); }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -274,13 +340,17 @@ __global__ void k_x_half_kernel(KrylovVecs k) {
 }
 
 // t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>.
-__global__ void k_apply_ts_kernel(KrylovVecs k) {
+template <class Y2>
+__global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ z) {
+  k = instance(k);
+  z += blockIdx.z * k.sv;
   KState* st = k.st;
   if (st->done) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
-  GRID_STRIDE(e, N) {
-    double2 t = apply_at(k.z, k.kh, e, k.n, 0.0);
+  for (NodeWalk it(k.n, gridDim.x * KB); it.e < N; it.next()) {
+    const int e = it.e;
+    double2 t = apply_at(z, k.kh, e, it.i, it.j, k.n, 0.0);
     k.t[e] = t;
     double2 s = k.s[e];
     acc[0] = fma(t.x, s.x, fma(t.y, s.y, acc[0]));
@@ -304,14 +374,18 @@ __global__ void k_apply_ts_kernel(KrylovVecs k) {
 }
 
 // x += alpha y + omega z, r = s - omega t, with <r^, r> and |r|^2; the next beta.
-__global__ void k_update_xr_kernel(KrylovVecs k) {
+template <class Y2>
+__global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const Y2* __restrict__ z) {
+  k = instance(k);
+  y += blockIdx.z * k.sv;
+  z += blockIdx.z * k.sv;
   KState* st = k.st;
   if (st->done) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const double2 alpha = st->alpha, omega = st->omega;
   const int N = (int)k.N;
   GRID_STRIDE(e, N) {
-    double2 x = d2axpy(d2axpy(k.x[e], alpha, k.y[e]), omega, k.z[e]);
+    double2 x = d2axpy(d2axpy(k.x[e], alpha, ldy(y, e)), omega, ldy(z, e));
     k.x[e] = x;
     double2 r = d2axmy(k.s[e], omega, k.t[e]);
     k.r[e] = r;
@@ -350,11 +424,13 @@ __global__ void k_update_xr_kernel(KrylovVecs k) {
 
 // tr = h^2 b - A x and |tr|^2, to confirm a recurrence-converged iterate.
 __global__ void k_true_residual_kernel(KrylovVecs k) {
+  k = instance(k);
   KState* st = k.st;
   double acc[1] = {0.0};
   const int N = (int)k.N;
-  GRID_STRIDE(e, N) {
-    double2 ax = apply_at(k.x, k.kh, e, k.n, 0.0);
+  for (NodeWalk it(k.n, gridDim.x * KB); it.e < N; it.next()) {
+    const int e = it.e;
+    double2 ax = apply_at(k.x, k.kh, e, it.i, it.j, k.n, 0.0);
     double2 bv = k.b[e];
     double2 tr = make_double2(fma(bv.x, k.scale_b, -ax.x), fma(bv.y, k.scale_b, -ax.y));
     k.tr[e] = tr;
@@ -367,6 +443,7 @@ __global__ void k_true_residual_kernel(KrylovVecs k) {
 
 // Restart from the true residual: r = tr, rho = <r^, r>, next step p = r.
 __global__ void k_restart_kernel(KrylovVecs k) {
+  k = instance(k);
   KState* st = k.st;
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
@@ -397,30 +474,54 @@ __global__ void k_restart_kernel(KrylovVecs k) {
 __global__ void apply_fp64_kernel(double2* v, const double2* u, const double* kh, int n, double beta,
                                   double out_scale) {
   const int N = (n + 1) * (n + 1);
-  GRID_STRIDE(e, N) {
-    double2 a = apply_at(u, kh, e, n, beta);
+  for (NodeWalk it(n, gridDim.x * KB); it.e < N; it.next()) {
+    const int e = it.e;
+    double2 a = apply_at(u, kh, e, it.i, it.j, n, beta);
     v[e] = make_double2(a.x * out_scale, a.y * out_scale);
   }
 }
 
 }  // namespace
 
-#define KLAUNCH(name) name<<<k.G, KB, 0, s>>>(k); return cudaGetLastError();
+#define KGRID dim3(k.G, 1, k.batch)
+#define KLAUNCH(name) name<<<KGRID, KB, 0, s>>>(k); return cudaGetLastError();
+
+KrylovVecs instance_of(const KrylovVecs& k, int b) {
+  KrylovVecs r = offset_instance(k, b);
+  r.batch = 1;
+  return r;
+}
 
 cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s) {
   shadow_kernel<<<1024, 256, 0, s>>>(rhat, N, seed);
   return cudaGetLastError();
 }
 cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s) {
-  k_init_kernel<<<k.G, KB, 0, s>>>(k, tol, maxit, hist_cap);
+  k_init_kernel<<<KGRID, KB, 0, s>>>(k, tol, maxit, hist_cap);
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_p_kernel) }
-cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_apply_rv_kernel) }
+cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) {
+  if (k.y32) k_apply_rv_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32);
+  else k_apply_rv_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y);
+  return cudaGetLastError();
+}
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_s_kernel) }
-cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_x_half_kernel) }
-cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_apply_ts_kernel) }
-cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_xr_kernel) }
+cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s) {
+  if (k.y32) k_x_half_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32);
+  else k_x_half_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y);
+  return cudaGetLastError();
+}
+cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) {
+  if (k.z32) k_apply_ts_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.z32);
+  else k_apply_ts_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.z);
+  return cudaGetLastError();
+}
+cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) {
+  if (k.y32) k_update_xr_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32, k.z32);
+  else k_update_xr_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y, k.z);
+  return cudaGetLastError();
+}
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_true_residual_kernel) }
 cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_restart_kernel) }
 

@@ -26,8 +26,10 @@ inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1
 template <class T, class F2>
 __global__ void gs_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                  const T* __restrict__ kh, int pk, int n, int colour, T beta,
-                                 const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                 const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.sf;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (j > n) return;
@@ -46,8 +48,10 @@ __global__ void gs_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __rest
 template <class T, class F2>
 __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                 const T* __restrict__ kh, int pk, int n, int colour, T beta,
-                                const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.sf;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -68,8 +72,10 @@ __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restr
 template <class T, class F2>
 __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                    const T* __restrict__ kh, int pk, int n, int colour, T beta,
-                                   const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                   const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.sf;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (j > n) return;
@@ -84,7 +90,7 @@ __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __re
   c2<T> r = csub<T>(ldc<T>(f, (long long)j * pf + i), au);
   T cx = (i == 0 || i == n) ? (T)4 : (T)2;
   T cy = (j == 0 || j == n) ? (T)4 : (T)2;
-  c2<T> delta = cscale<T>(r, (T)1 / (cabs2<T>(d) + cx + cy));
+  c2<T> delta = cscale<T>(r, rcp(cabs2<T>(d) + cx + cy));
   u[p] = cadd<T>(up, cmulc<T>(d, delta));
   long long q;
   q = (long long)j * pu + b.iw; u[q] = cadd<T>(u[q], delta);
@@ -101,8 +107,11 @@ __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __re
 template <class T, class F2>
 __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c2<T>* __restrict__ u, int pu,
                                          const F2* __restrict__ f, int pf, const T* __restrict__ kh, int pk, int n,
-                                         T beta, const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                         T beta, const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  fc += blockIdx.z * bi.sc;
+  u += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.sf;
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   int nc = n / 2;
@@ -130,8 +139,10 @@ __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c
 // u += P e_c, bilinear interpolation from the (n/2+1)^2 grid.
 template <class T>
 __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* __restrict__ ec, int pc, int n,
-                                   const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                   const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  ec += blockIdx.z * bi.sc;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -152,8 +163,10 @@ __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* _
 // u = A_c^{-1} f~ with the dense inverse stored transposed (column c contiguous), one block.
 template <class T>
 __global__ void coarse_solve_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* __restrict__ f, int pf,
-                                    const c2<T>* __restrict__ ainvT, int nc, const int* __restrict__ stop) {
-  if (stop && *stop) return;
+                                    const c2<T>* __restrict__ ainvT, int nc, const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  u += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.su;
   extern __shared__ unsigned char smem_raw[];
   c2<T>* fs = reinterpret_cast<c2<T>*>(smem_raw);
   int w = nc + 1, m = w * w;
@@ -298,84 +311,94 @@ __global__ void inject_kh_kernel(T* __restrict__ kh, int pk, const double* __res
 
 template <class T, class F2>
 cudaError_t gs_colour_t(void* u, int pu, const void* f, int pf, const void* kh, int pk, int n, int colour, double beta,
-                        const int* stop, cudaStream_t s) {
-  gs_colour_kernel<T, F2><<<grid2((n + 2) / 2, n + 1), dim3(BX, BY), 0, s>>>(
-      (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour, (T)beta, stop);
+                        const int* stop, cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2((n + 2) / 2, n + 1);
+  g.z = bi.count;
+  gs_colour_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+                                                     (T)beta, stop, bi);
   return cudaGetLastError();
 }
 template <class T, class F2>
 cudaError_t gs_first_t(void* u, int pu, const void* f, int pf, const void* kh, int pk, int n, int colour, double beta,
-                       const int* stop, cudaStream_t s) {
-  gs_first_kernel<T, F2><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh,
-                                                                       pk, n, colour, (T)beta, stop);
+                       const int* stop, cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2(n + 1, n + 1);
+  g.z = bi.count;
+  gs_first_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+                                                    (T)beta, stop, bi);
   return cudaGetLastError();
 }
 template <class T, class F2>
 cudaError_t kacz_colour_t(void* u, int pu, const void* f, int pf, const void* kh, int pk, int n, int colour,
-                          double beta, const int* stop, cudaStream_t s) {
-  kacz_colour_kernel<T, F2><<<grid2((n + 5) / 5, n + 1), dim3(BX, BY), 0, s>>>(
-      (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour, (T)beta, stop);
+                          double beta, const int* stop, cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2((n + 5) / 5, n + 1);
+  g.z = bi.count;
+  kacz_colour_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+                                                       (T)beta, stop, bi);
   return cudaGetLastError();
 }
 template <class T, class F2>
 cudaError_t restrict_t(void* fc, int pc, const void* u, int pu, const void* f, int pf, const void* kh, int pk, int n,
-                       double beta, const int* stop, cudaStream_t s) {
-  restrict_residual_kernel<T, F2><<<grid2(n / 2 + 1, n / 2 + 1), dim3(BX, BY), 0, s>>>(
-      (c2<T>*)fc, pc, (const c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)beta, stop);
+                       double beta, const int* stop, cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2(n / 2 + 1, n / 2 + 1);
+  g.z = bi.count;
+  restrict_residual_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)fc, pc, (const c2<T>*)u, pu, (const F2*)f, pf,
+                                                             (const T*)kh, pk, n, (T)beta, stop, bi);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_gs_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                             int n, int colour, double beta, const int* stop, cudaStream_t s) {
-  if (!fp32) return gs_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  if (f64_src) return gs_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  return gs_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
+                             int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi) {
+  if (!fp32) return gs_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  if (f64_src) return gs_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  return gs_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
 }
 
 cudaError_t launch_gs_first(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                            int n, int colour, double beta, const int* stop, cudaStream_t s) {
-  if (!fp32) return gs_first_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  if (f64_src) return gs_first_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  return gs_first_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
+                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi) {
+  if (!fp32) return gs_first_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  if (f64_src) return gs_first_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  return gs_first_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
 }
 
 cudaError_t launch_kacz_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                               int n, int colour, double beta, const int* stop, cudaStream_t s) {
-  if (!fp32) return kacz_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  if (f64_src) return kacz_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
-  return kacz_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s);
+                               int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi) {
+  if (!fp32) return kacz_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  if (f64_src) return kacz_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+  return kacz_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
 }
 
 cudaError_t launch_restrict_residual(bool fp32, void* fc, int pc, const void* u, int pu, const void* f, int pf,
                                      bool f64_src, const void* kh, int pk, int n, double beta, const int* stop,
-                                     cudaStream_t s) {
-  if (!fp32) return restrict_t<double, double2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s);
-  if (f64_src) return restrict_t<float, double2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s);
-  return restrict_t<float, float2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s);
+                                     cudaStream_t s, const Inst& bi) {
+  if (!fp32) return restrict_t<double, double2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s, bi);
+  if (f64_src) return restrict_t<float, double2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s, bi);
+  return restrict_t<float, float2>(fc, pc, u, pu, f, pf, kh, pk, n, beta, stop, s, bi);
 }
 
 cudaError_t launch_prolong_add(bool fp32, void* u, int pu, const void* ec, int pc, int n, const int* stop,
-                               cudaStream_t s) {
+                               cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2(n + 1, n + 1);
+  g.z = bi.count;
   if (fp32)
-    prolong_add_kernel<float><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>((float2*)u, pu, (const float2*)ec, pc, n, stop);
+    prolong_add_kernel<float><<<g, dim3(BX, BY), 0, s>>>((float2*)u, pu, (const float2*)ec, pc, n, stop, bi);
   else
-    prolong_add_kernel<double><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>((double2*)u, pu, (const double2*)ec, pc, n,
-                                                                            stop);
+    prolong_add_kernel<double><<<g, dim3(BX, BY), 0, s>>>((double2*)u, pu, (const double2*)ec, pc, n, stop, bi);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int pf, const void* ainvT, int nc,
-                                const int* stop, cudaStream_t s) {
+                                const int* stop, cudaStream_t s, const Inst& bi) {
   int m = (nc + 1) * (nc + 1);
   int threads = m < 256 ? ((m + 31) / 32) * 32 : 256;
+  dim3 g(1, 1, bi.count);
   if (fp32)
-    coarse_solve_kernel<float><<<1, threads, m * sizeof(float2), s>>>((float2*)u, pu, (const float2*)f, pf,
-                                                                       (const float2*)ainvT, nc, stop);
+    coarse_solve_kernel<float><<<g, threads, m * sizeof(float2), s>>>((float2*)u, pu, (const float2*)f, pf,
+                                                                       (const float2*)ainvT, nc, stop, bi);
   else
-    coarse_solve_kernel<double><<<1, threads, m * sizeof(double2), s>>>((double2*)u, pu, (const double2*)f, pf,
-                                                                         (const double2*)ainvT, nc, stop);
+    coarse_solve_kernel<double><<<g, threads, m * sizeof(double2), s>>>((double2*)u, pu, (const double2*)f, pf,
+                                                                         (const double2*)ainvT, nc, stop, bi);
   return cudaGetLastError();
 }
 

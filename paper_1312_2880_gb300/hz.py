@@ -32,7 +32,7 @@ class HzError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
-                ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double)]
+                ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -81,6 +81,10 @@ def lib() -> ctypes.CDLL:
         "hz_vcycle": (c_int, [P, c_void_p, c_void_p]),
         "hz_solve": (c_int, [P, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
         "hz_solve_host": (c_int, [P, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
+        "hz_solve_batch": (c_int, [P, c_void_p, c_void_p, c_double, c_int, POINTER(SolveInfo)]),
+        "hz_solve_start": (c_int, [P, c_void_p, c_void_p, c_double, c_int]),
+        "hz_solve_poll": (c_int, [P, POINTER(c_int)]),
+        "hz_solve_finish": (c_int, [P, dp, c_int, POINTER(SolveInfo)]),
         "hz_apply": (c_int, [P, c_int, c_void_p, c_void_p]),
         "hz_level_presmooth": (c_int, [P, c_int, c_void_p, c_void_p, c_void_p]),
         "hz_level_postsmooth": (c_int, [P, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -92,6 +96,10 @@ def lib() -> ctypes.CDLL:
         "hz_status_string": (ctypes.c_char_p, [c_int]),
         "hz_destroy": (None, [P]),
         "hz_apply_dot_noalloc": (c_int, [c_int, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "hz_group_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+        "hz_group_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_double, c_int, POINTER(SolveInfo)]),
+        "hz_group_last_error": (ctypes.c_char_p, [c_void_p]),
+        "hz_group_destroy": (None, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -109,11 +117,11 @@ def _ptr(t) -> c_void_p:
     return c_void_p(t.data_ptr())
 
 
-def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0) -> Opts:
+def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1) -> Opts:
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
-    o.nu_gs, o.nu_kacz, o.guard, o.k_ref = nu_gs, nu_kacz, int(bool(guard)), float(k_ref)
+    o.nu_gs, o.nu_kacz, o.guard, o.k_ref, o.batch = nu_gs, nu_kacz, int(bool(guard)), float(k_ref), int(batch)
     return o
 
 
@@ -154,7 +162,7 @@ class Problem:
     """
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
-                 nu_kacz=4, guard=True, k_ref=0.0, arena=None):
+                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None):
         import torch
 
         L = lib()
@@ -167,7 +175,8 @@ class Problem:
         if st != HZ_OK:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
-        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref)
+        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch)
+        self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
         if self.bytes == 0:
@@ -233,6 +242,48 @@ class Problem:
              "restarts": info.restarts}
         return x, d, hist[: info.history_len].copy()
 
+    def solve_batch(self, rhs, tol: float = 1e-6, maxit: int = 1000, x=None, allow_fail: bool = False):
+        """All `batch` right-hand sides at once: rhs is a (batch, n+1, n+1) complex128 CUDA tensor.
+        Returns (x, list of info dicts)."""
+        import torch
+
+        self._stream()
+        m = self.n + 1
+        assert tuple(rhs.shape) == (self.batch, m, m)
+        x = torch.empty_like(rhs) if x is None else x
+        infos = (SolveInfo * self.batch)()
+        st = lib().hz_solve_batch(self._h, _ptr(rhs), _ptr(x), tol, maxit, infos)
+        ok = (HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN, HZ_ENONFINITE) if allow_fail else (HZ_OK,)
+        self._check(st, ok)
+        return x, [{"iterations": i.iterations, "relres_true": i.relres_true, "status": i.status,
+                    "restarts": i.restarts} for i in infos]
+
+    # ---- non-blocking solve (serving)
+    def solve_start(self, rhs, x, tol: float = 1e-6, maxit: int = 1000):
+        """Queue a solve and return at once; keep `rhs` and `x` alive until :meth:`solve_finish`."""
+        self._stream()
+        self._pending = (rhs, x)
+        self._check(lib().hz_solve_start(self._h, _ptr(rhs), _ptr(x), tol, maxit))
+
+    def solve_poll(self) -> bool:
+        """True once the solve in flight has stopped; never waits."""
+        done = c_int(0)
+        self._check(lib().hz_solve_poll(self._h, byref(done)))
+        return bool(done.value)
+
+    def solve_finish(self, history_cap: int = 4096, allow_fail: bool = False):
+        """Wait for the solve in flight; returns (x, info dict, history)."""
+        self._stream()
+        hist = np.zeros(max(1, history_cap), dtype=np.float64)
+        info = SolveInfo()
+        st = lib().hz_solve_finish(self._h, hist.ctypes.data_as(POINTER(c_double)), history_cap, byref(info))
+        ok = (HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN, HZ_ENONFINITE) if allow_fail else (HZ_OK,)
+        self._check(st, ok)
+        x = self._pending[1]
+        self._pending = None
+        return x, {"iterations": info.iterations, "relres_true": info.relres_true, "status": st,
+                   "restarts": info.restarts}, hist[: info.history_len].copy()
+
     def solve_host(self, rhs: np.ndarray, tol: float = 1e-6, maxit: int = 1000, history_cap: int = 4096,
                    out: np.ndarray | None = None):
         """As :meth:`solve` with host (numpy complex128) input and output."""
@@ -293,3 +344,45 @@ class Problem:
         u = self._empty(self.num_levels - 1)
         self._check(lib().hz_coarse_solve(self._h, _ptr(f), _ptr(u)))
         return u
+
+
+class Group:
+    """Several set-up (batched) problems solved together: one CUDA graph per iteration of all."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = c_void_p()
+        st = lib().hz_group_create(arr, len(self.problems), byref(h))
+        if st != HZ_OK:
+            raise HzError(st, "hz_group_create failed")
+        self._h = h
+
+    def solve(self, rhs_list, tol: float = 1e-6, maxit: int = 1000, allow_fail: bool = False):
+        """rhs_list[i]: (batch_i, n_i+1, n_i+1) complex128 CUDA tensor. Returns (x list, infos)."""
+        import torch
+
+        for p in self.problems:
+            p._stream()
+        xs = [torch.empty_like(r) for r in rhs_list]
+        rp = (c_void_p * len(xs))(*[_ptr(r).value for r in rhs_list])
+        xp = (c_void_p * len(xs))(*[_ptr(x).value for x in xs])
+        total = sum(p.batch for p in self.problems)
+        infos = (SolveInfo * total)()
+        st = lib().hz_group_solve(self._h, rp, xp, tol, maxit, infos)
+        ok = (HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN, HZ_ENONFINITE) if allow_fail else (HZ_OK,)
+        if st not in ok:
+            raise HzError(st, lib().hz_group_last_error(self._h).decode())
+        torch.cuda.synchronize()
+        return xs, [{"iterations": i.iterations, "relres_true": i.relres_true, "status": i.status} for i in infos]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hz_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

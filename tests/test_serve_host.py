@@ -1,0 +1,75 @@
+"""Host logic of the serving scheduler (admission by memory, reuse of resident problems, eviction,
+latency accounting) against a fake backend: no GPU needed."""
+import pytest
+
+from paper_1312_2880_gb300 import serve
+
+
+class FakeProblem:
+    built = 0
+
+    def __init__(self, n, kfield, beta, **kw):
+        FakeProblem.built += 1
+        self.n = n
+        self.polls = 0
+        self.closed = False
+
+    def solve_start(self, rhs, x, tol, maxit):
+        self.polls = 3 + self.n // 64  # finishes after a few polls
+
+    def solve_poll(self):
+        self.polls -= 1
+        return self.polls <= 0
+
+    def solve_finish(self, history_cap=0, allow_fail=False):
+        return None, {"status": 0, "iterations": 10.0, "relres_true": 1e-7, "restarts": 0}, []
+
+    def close(self):
+        self.closed = True
+
+
+class FakeHz:
+    Problem = FakeProblem
+
+    @staticmethod
+    def footprint_bytes(n, **kw):
+        return 1000 * n
+
+
+@pytest.fixture
+def server():
+    def make(budget, max_active=4):
+        return serve.Server(hbm_budget=budget, max_active=max_active, backend=FakeHz,
+                            make_io=lambda n, src: (None, None))
+
+    return make
+
+
+def _job(rid, n, key, arrival=0.0):
+    return serve.Job(rid, n, key, lambda: None, 1.0, (1, 1), arrival=arrival)
+
+
+def test_resident_problems_are_reused(server):
+    FakeProblem.built = 0
+    s = server(budget=10**9, max_active=1)
+    out = s.run([_job(r, 64, ("a",)) for r in range(5)], realtime=False)
+    assert out["completed"] == 5 and FakeProblem.built == 1
+
+
+def test_memory_budget_bounds_admission_and_evicts_idle(server):
+    FakeProblem.built = 0
+    foot = 1000 * 64 + 2 * 16 * 65 ** 2
+    s = server(budget=2 * foot, max_active=8)
+    jobs = [_job(r, 64, (r % 4,)) for r in range(8)]
+    out = s.run(jobs, realtime=False)
+    assert out["completed"] == 8
+    assert out["peak_hbm_bytes"] <= 2 * foot
+    assert out["evictions"] >= 2 and FakeProblem.built >= 4
+
+
+def test_latency_counts_from_arrival(server):
+    s = server(budget=10**9)
+    out = s.run([_job(0, 64, ("a",), arrival=0.0), _job(1, 64, ("b",), arrival=0.05)], realtime=True)
+    assert out["completed"] == 2 and out["p50_ms"] is not None
+    for j in s.done:
+        assert j.end >= j.arrival and j.start >= j.arrival
