@@ -4,10 +4,11 @@ Timed workload (default ``wedge512``): n = 512 (513^2 nodes), k = 100, seeded th
 k * {1.0, 1.5, 0.75}, 8 seeded point sources of 1/h^2, hybrid (HYB-V) hierarchy of 8 levels,
 Bi-CGSTAB to relres 1e-6. A step is one complete solve (every kernel of the hot path) with the
 inputs resident in HBM. Between solves the library rewrites every Krylov vector from the
-right-hand side, so no state carries over; the whole problem (~60 MB) fits in L2, so its
-kernels run from L2 and the HBM roofline is measured on the n = 4096 grid instead
-(``--roofline-workload``, two profiled iterations, no solve): per-kernel device times from
-CUDA events on the library's stream.
+right-hand side, so no state carries over, and L2 is flushed (a 512 MB write, untimed) before
+each timed solve. The problem (~60 MB) fits in L2, so within a solve its kernels run mostly from
+L2; the HBM roofline is therefore measured on the n = 4096 grid (``--roofline-workload``, two
+profiled iterations launched kernel by kernel, no solve): per-kernel device times from CUDA
+events on the library's stream.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead: one full oracle
 solve gives its iteration count, then each step times a bounded sample of whole iterations,
@@ -171,9 +172,19 @@ def barrier_max(value: float, world: int) -> float:
     return float(t.item())
 
 
-def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
+def l2_flush_buffer():
+    """A device buffer larger than L2 (129 MB); writing it evicts every line of the solve."""
     import torch
 
+    return torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+
+
+def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
+    """Each step: flush L2 (untimed), then one solve bracketed by CUDA events on the caller's
+    stream. Returns per-step ms, their sum and the solve infos."""
+    import torch
+
+    flush = l2_flush_buffer()
     for _ in range(warmup):
         P.solve(rhs, tol=tol, maxit=5000)
     torch.cuda.synchronize()
@@ -182,17 +193,19 @@ def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
 
         dist.barrier()
     stream = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     infos = []
-    ev[0].record(stream)
     for s in range(steps):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
         _, info, _ = P.solve(rhs, tol=tol, maxit=5000)
-        ev[s + 1].record(stream)
+        ev[s][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
-    per = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
-    total = ev[0].elapsed_time(ev[steps])
-    return per, total, infos
+    if world > 1:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in ev]
+    return per, sum(per), infos
 
 
 def time_e2e(P, rhs_host, steps: int, tol: float):
@@ -408,7 +421,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "medium": wl.meta.get("medium", ""),
                    "levels": wl.levels, "variant": wl.variant, "tol": tol, "rhs": wl.meta.get("rhs", ""),
-                   "l2": "problem fits in L2; HBM rates measured on the roofline workload, larger than L2",
+                   "l2": "flushed before every timed solve (512 MB write); HBM rates measured on the roofline workload, larger than L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iterations": it32,
         "relres_true": results["fp32"]["relres_true"],
