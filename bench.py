@@ -267,6 +267,44 @@ def sweep_rates(per, fp32: bool, hbm_peak: float, n: int):
     return out
 
 
+def pass_forms(P):
+    """Fused-pass forms the tile autotuner picked: {"L<l> n=<n_l>": [pre, post]} per fused level."""
+    return {f"L{l} n={d['n']}": [d["pass_down"], d["pass_up"]] for l, d in enumerate(P.schedule())
+            if d["pass_down"] >= 0}
+
+
+def source_digest():
+    """SHA-256 of the CUDA sources and headers the kernels are built from."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1312_2880_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, level: int, workload_name: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `level` from a committed ncu summary
+    under profiles/ (lines "traffic: <kernel>@L<level> <workload> <bytes> sources=<digest>"), or
+    None when no summary covers it or the kernel sources have changed since it was taken."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    digest = source_digest()
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            parts = line.strip().strip("`").split()
+            if len(parts) == 5 and parts[0] == "traffic:" and parts[1] == f"{kernel}@L{level}" \
+                    and parts[2] == workload_name and parts[4] == f"sources={digest}":
+                return int(parts[3])
+    return None
+
+
 def shares(per):
     total = sum(sum(v) for v in per.values())
     top = sorted(per.items(), key=lambda kv: -sum(kv[1]))[:10]
@@ -379,7 +417,8 @@ def run_ours(args):
         ms = barrier_max(total / steps, world)
         _, info_chk, _ = P.solve(rhs, tol=tol, maxit=5000)
         results[prec] = {"ms": ms, "per_step_ms": [round(x, 3) for x in per], "iterations": infos[-1]["iterations"],
-                         "relres_true": infos[-1]["relres_true"], "clocks": clk.summary(), "P": P}
+                         "relres_true": infos[-1]["relres_true"], "clocks": clk.summary(), "P": P,
+                         "forms": pass_forms(P)}
     P32 = results["fp32"]["P"]
     per_small = profile(P32, rhs, 2)
     launches_per_iter = sum(len(v) for k, v in per_small.items() if k[0] != "zero") // 2
@@ -402,6 +441,8 @@ def run_ours(args):
     per_big = profile(Pr, rrhs, 2)
     roof = roofline(per_big, True, hbm_peak, peak_kind, rw.n)
     roof["workload"] = rw.name
+    roof["traffic"] = profiled_traffic(roof["kernel"], roof["level"], rw.name)
+    roof_forms = pass_forms(Pr)
     sweeps = sweep_rates(per_big, True, hbm_peak, rw.n)
     big_iter_ms = sum(sum(v) for v in per_big.values()) / 2
     Pr.close()
@@ -437,6 +478,8 @@ def run_ours(args):
                       "kernel_share": shares(per_big)},
         "kernel_share": shares(per_small),
         "gpu_launches": gpu_launches,
+        "tile_autotuner": {wl.name: results["fp32"]["forms"], rw.name: roof_forms,
+                           "forms": "0 = shared-memory tiles; v = 1..5: register streaming, 2^(v+3) rows per warp"},
         "clocks": results["fp32"]["clocks"],
         "clocks_fp64_form": results["fp64"]["clocks"],
     }

@@ -73,6 +73,10 @@ typedef struct {
   double k_ref;  /* wavenumber that sets each level's scale c = k_ref H; 0 = mean of k(x) */
   int batch;     /* right-hand sides solved together by hz_solve_batch (1..1024, default 1); every
                     kernel launch then covers all of them and finished ones retire individually */
+  int pass_variant; /* kernel form of the two fused passes of each Gauss-Seidel level in the FP32 form
+                       (the FP64 form always uses 0): -1 (default) = chosen per level at setup by
+                       timing every form on the level's arrays (tile autotuner); 0 = shared-memory
+                       tiles; 1..5 = register streaming with 2^(v+3) rows per warp */
 } hz_hierarchy_opts;
 
 typedef struct {
@@ -82,6 +86,9 @@ typedef struct {
   int smoother; /* hz_smoother */
   int resid_op; /* hz_op used for the residual, role (B) of Sec. 5 */
   int nu;       /* sweeps before and after the coarse-grid correction */
+  int pass_down; /* form of the fused pre-smoothing pass (see pass_variant); -1 = not a fused level
+                    or not yet set up */
+  int pass_up;   /* form of the fused post-smoothing pass; -1 likewise */
 } hz_level_info;
 
 typedef struct {

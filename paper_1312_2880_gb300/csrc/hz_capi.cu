@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hz_internal.h"
@@ -40,6 +43,7 @@ struct Level {
   void* u = nullptr;  // working precision complex
   void* f = nullptr;  // working precision complex (levels >= 1)
   void* u2 = nullptr; // result of the fused post-smoothing pass (levels >= 1)
+  int var_down = 0, var_up = 0;  // fused-pass variants (FP32 form; picked by the tile autotuner)
 };
 
 struct Plan {
@@ -336,7 +340,8 @@ cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop, bool all = 
   int pu = L.pitch;
   cudaError_t e;
   if (fused(P, l))
-    return mark(P, launch_smooth_restrict(fp32, u, pu, C.f, C.pitch, f.f, f.pf, f.f64, kh, pk, L.n, bA, bB, stop, s, bi),
+    return mark(P, launch_smooth_restrict(fp32, u, pu, C.f, C.pitch, f.f, f.pf, f.f64, kh, pk, L.n, bA, bB, stop, s, bi,
+                                          L.var_down),
                 HZ_K_SMOOTH_RESTRICT, l);
   KaczPath kp = kacz_path(P, l);
   if (kp == KACZ_LEVEL)
@@ -406,7 +411,7 @@ cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* 
     int pk;
     const void* kh = kh_of(P, l, &pk);
     return mark(P, launch_prolong_smooth(fp32, out, po, false, L.u, L.pitch, ec, C.pitch, f.f, f.pf, f.f64, kh, pk,
-                                         L.n, op_beta(P, L.relax_op), stop, P->stream, bi),
+                                         L.n, op_beta(P, L.relax_op), stop, P->stream, bi, L.var_up),
                 HZ_K_PROLONG_SMOOTH, l);
   }
   KaczPath kp = kacz_path(P, l);
@@ -726,7 +731,104 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
 
 bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
-           o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024);
+           o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024 ||
+           o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS);
+}
+
+// ------------------------------------------------------------------ tile autotuner
+// Every fused Gauss-Seidel level of the FP32 form runs each candidate variant of its two passes
+// (shared-memory tiles, or register streaming with 16 .. 256 rows per warp) on its own arrays,
+// with all right-hand sides of the batch: one untimed launch, then the best of three timings of
+// five back-to-back launches with CUDA events on the library stream. The fastest is kept, and cached per
+// (n_l, batch, pass, finest level or not) for later problems of the same shape.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+
+// Candidates for a level of n_l intervals: streaming needs n_l >= 4; segments longer than the
+// level add nothing over the one that covers it.
+std::vector<int> tune_candidates(int nl) {
+  std::vector<int> c{0};
+  if (nl < 4) return c;
+  for (int v = 1; v < FUSED_VARIANTS; ++v) {
+    c.push_back(v);
+    if (stream_rows(v) >= nl + 1) break;
+  }
+  return c;
+}
+
+// Best of three timings of five back-to-back launches (after one untimed launch), in ms per launch.
+cudaError_t time_pass(hz_problem* P, int l, bool up, float* best_ms) {
+  cudaEvent_t a, b;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a))) return e;
+  if ((e = cudaEventCreate(&b))) { cudaEventDestroy(a); return e; }
+  const void* f0 = P->plan.fp32 ? (const void*)P->kv.p32 : (const void*)P->kv.p;
+  void* out0 = P->plan.fp32 ? (void*)P->kv.y32 : (void*)P->kv.y;
+  auto launch = [&]() -> cudaError_t {
+    if (up) {
+      void* out = l == 0 ? out0 : final_u(P, l);
+      int po = l == 0 ? P->n + 1 : P->lv[l].pitch;
+      return level_up(P, l, level_src(P, l, f0), out, po, nullptr, true);
+    }
+    return level_down(P, l, level_src(P, l, f0), nullptr, true);
+  };
+  constexpr int REPS = 5;
+  *best_ms = 1e30f;
+  e = launch();
+  for (int rep = 0; rep < 3 && !e; ++rep) {
+    e = cudaEventRecord(a, P->stream);
+    for (int q = 0; q < REPS && !e; ++q) e = launch();
+    if (!e) e = cudaEventRecord(b, P->stream);
+    if (!e) e = cudaEventSynchronize(b);
+    float ms = 0;
+    if (!e) e = cudaEventElapsedTime(&ms, a, b);
+    if (!e) *best_ms = std::min(*best_ms, ms / REPS);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
+}
+
+cudaError_t autotune(hz_problem* P) {
+  const int B = P->plan.batch;
+  for (int l = 0; l < P->plan.levels - 1; ++l) {
+    Level& L = P->lv[l];
+    if (!fused(P, l)) continue;
+    if (!P->plan.fp32) {
+      L.var_down = L.var_up = 0;
+      continue;
+    }
+    if (P->opts.pass_variant >= 0) {
+      const bool ok = P->opts.pass_variant == 0 || L.n >= 4;
+      L.var_down = L.var_up = ok ? P->opts.pass_variant : 0;
+      continue;
+    }
+    for (int up = 0; up < 2; ++up) {
+      int& var = up ? L.var_up : L.var_down;
+      const auto key = std::make_tuple(L.n, B, up, l == 0 ? 1 : 0);
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+          var = it->second;
+          continue;
+        }
+      }
+      int best = 0;
+      float best_ms = 1e30f;
+      for (int v : tune_candidates(L.n)) {
+        var = v;
+        float ms;
+        cudaError_t e = time_pass(P, l, up, &ms);
+        if (e) return e;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+      }
+      var = best;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[key] = best;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -745,6 +847,7 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->guard = 1;
   o->k_ref = 0.0;
   o->batch = 1;
+  o->pass_variant = -1;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {
@@ -894,6 +997,8 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   CK(cudaMemcpyAsync(&status, P->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (status != 0) return fail(P, HZ_EINVAL, "coarsest operator is singular");
+  CK(autotune(P));
+  CK(cudaStreamSynchronize(s));
   P->setup = true;
   return HZ_OK;
 }
@@ -915,6 +1020,7 @@ int hz_describe_hierarchy(const hz_problem* P, const hz_hierarchy_opts* opts, hz
     out[l].smoother = lv[l].smoother;
     out[l].resid_op = lv[l].resid_op;
     out[l].nu = lv[l].nu;
+    out[l].pass_down = out[l].pass_up = -1;  // chosen at setup
   }
   return pl.levels;
 }
@@ -932,6 +1038,9 @@ hz_status hz_get_level_info(const hz_problem* P, int level, hz_level_info* info)
   info->smoother = L.smoother;
   info->resid_op = L.resid_op;
   info->nu = L.nu;
+  const bool fz = level < P->plan.levels - 1 && fused(P, level);
+  info->pass_down = fz ? L.var_down : -1;
+  info->pass_up = fz ? L.var_up : -1;
   return HZ_OK;
 }
 

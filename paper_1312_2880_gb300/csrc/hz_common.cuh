@@ -139,4 +139,56 @@ __device__ __forceinline__ int reflect(int i, int n) {
   return i > n ? 2 * n - i : i;
 }
 
+// Fixed-rounding complex arithmetic for the fused Gauss-Seidel passes. Every operation is an
+// explicit round-to-nearest add, multiply or fused multiply-add, so the compiler cannot contract
+// or reorder it differently from one kernel to another: the tile and streaming forms of a pass,
+// which share these helpers and take the same operations in the same order on every node, give
+// bit-identical results, and the choice between them never changes a solution.
+namespace xr {
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+
+template <class T> __device__ __forceinline__ c2<T> cadd(c2<T> a, c2<T> b) { return mk<T>(add(a.x, b.x), add(a.y, b.y)); }
+template <class T> __device__ __forceinline__ c2<T> csub(c2<T> a, c2<T> b) { return mk<T>(sub(a.x, b.x), sub(a.y, b.y)); }
+template <class T> __device__ __forceinline__ c2<T> cscale(c2<T> a, T s) { return mk<T>(mul(a.x, s), mul(a.y, s)); }
+template <class T>
+__device__ __forceinline__ c2<T> cmul(c2<T> a, c2<T> b) {
+  return mk<T>(fma(a.x, b.x, -mul(a.y, b.y)), fma(a.x, b.y, mul(a.y, b.x)));
+}
+template <class T>
+__device__ __forceinline__ c2<T> cdiv(c2<T> a, c2<T> d) {
+  const T inv = rcp(fma(d.x, d.x, mul(d.y, d.y)));
+  return mk<T>(mul(fma(a.x, d.x, mul(a.y, d.y)), inv), mul(fma(a.y, d.x, -mul(a.x, d.y)), inv));
+}
+// Scaled-row diagonal (k H)^2 - 4 + i (beta (k H)^2 + 2 sides k H).
+template <class T>
+__device__ __forceinline__ c2<T> diag(T kh, int sides, T beta) {
+  const T k2 = mul(kh, kh);
+  return mk<T>(sub(k2, (T)4), fma((T)(2 * sides), kh, mul(beta, k2)));
+}
+// Sum of a node's four neighbours in the order (W + E) + (S + N).
+template <class T>
+__device__ __forceinline__ c2<T> nb4(c2<T> w, c2<T> e, c2<T> s, c2<T> n) {
+  return cadd<T>(cadd<T>(w, e), cadd<T>(s, n));
+}
+// Gauss-Seidel point update (f - nb) / d and residual f - (d u + nb).
+template <class T>
+__device__ __forceinline__ c2<T> gs(c2<T> f, c2<T> nb, c2<T> d) { return cdiv<T>(csub<T>(f, nb), d); }
+template <class T>
+__device__ __forceinline__ c2<T> resid(c2<T> f, c2<T> u, c2<T> nb, c2<T> d) {
+  return csub<T>(f, cadd<T>(cmul<T>(d, u), nb));
+}
+// One row of full weighting: (w + e) + 2 c.
+template <class T>
+__device__ __forceinline__ c2<T> fw3(c2<T> w, c2<T> c, c2<T> e) { return cadd<T>(cadd<T>(w, e), cscale<T>(c, (T)2)); }
+}  // namespace xr
+
 }  // namespace hz

@@ -39,8 +39,19 @@ __device__ __forceinline__ bool in_grid(int i, int j, int n) { return (unsigned)
 template <class T>
 __device__ __forceinline__ c2<T> nb_sum(const c2<T>* s, int rw, int c, int r, int i, int j, int n, int gx, int gy) {
   Nbr b = neighbours(i, j, n);
-  return cadd<T>(cadd<T>(s[r * rw + (b.iw - gx)], s[r * rw + (b.ie - gx)]),
-                 cadd<T>(s[(b.js - gy) * rw + c], s[(b.jn - gy) * rw + c]));
+  return xr::nb4<T>(s[r * rw + (b.iw - gx)], s[r * rw + (b.ie - gx)], s[(b.js - gy) * rw + c],
+                    s[(b.jn - gy) * rw + c]);
+}
+
+// Bilinear interpolation of the coarse correction at fine node (2I + oi, 2J + oj) from coarse rows
+// e0 (J) and e1 (J + 1): coincident nodes copy, edge midpoints average two, centres four, in the
+// order ((e00 + e10) + (e01 + e11)) / 4 that the streaming form also takes.
+template <class T>
+__device__ __forceinline__ c2<T> bilinear(const c2<T>* e0, const c2<T>* e1, int I, int oi, int oj) {
+  if (oi && oj) return xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e0[I], e1[I]), xr::cadd<T>(e0[I + 1], e1[I + 1])), (T)0.25);
+  if (oi) return xr::cscale<T>(xr::cadd<T>(e0[I], e0[I + 1]), (T)0.5);
+  if (oj) return xr::cscale<T>(xr::cadd<T>(e0[I], e1[I]), (T)0.5);
+  return e0[I];
 }
 
 // ---------------------------------------------------------------- interior tiles
@@ -72,8 +83,7 @@ __device__ __forceinline__ void smooth_restrict_inner(c2<T>* __restrict__ u, int
     const int par = (0 - gx - gy - r) & 1;
     for (int c = 2 * tx + par; c < RW; c += 2 * TXN) {
       const int q = r * RW + c;
-      const T k = sk[q], k2 = k * k;
-      su[q] = cdiv<T>(sf[q], mk<T>(k2 - (T)4, bA * k2));
+      su[q] = xr::cdiv<T>(sf[q], xr::diag<T>(sk[q], 0, bA));
     }
   }
   __syncthreads();
@@ -83,9 +93,8 @@ __device__ __forceinline__ void smooth_restrict_inner(c2<T>* __restrict__ u, int
     for (int c = 2 * tx + par; c < RW - 1; c += 2 * TXN) {
       if (c < 1) continue;
       const int q = r * RW + c;
-      const T k = sk[q], k2 = k * k;
-      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
-      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+      const c2<T> nb = xr::nb4<T>(su[q - 1], su[q + 1], su[q - RW], su[q + RW]);
+      su[q] = xr::gs<T>(sf[q], nb, xr::diag<T>(sk[q], 0, bA));
     }
   }
   __syncthreads();
@@ -97,10 +106,8 @@ __device__ __forceinline__ void smooth_restrict_inner(c2<T>* __restrict__ u, int
   for (int r = 2 + ty; r < RH - 2; r += TYN) {
     for (int c = 2 + tx; c < RW - 2; c += TXN) {
       const int q = r * RW + c;
-      const T k = sk[q], k2 = k * k;
-      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
-      c2<T> au = cadd<T>(cmul<T>(mk<T>(k2 - (T)4, bB * k2), su[q]), nb);
-      sf[q] = csub<T>(sf[q], au);
+      const c2<T> nb = xr::nb4<T>(su[q - 1], su[q + 1], su[q - RW], su[q + RW]);
+      sf[q] = xr::resid<T>(sf[q], su[q], nb, xr::diag<T>(sk[q], 0, bB));
     }
   }
   __syncthreads();
@@ -109,11 +116,10 @@ __device__ __forceinline__ void smooth_restrict_inner(c2<T>* __restrict__ u, int
   for (int Jl = ty; Jl < HH / 2; Jl += TYN) {
     for (int Il = tx; Il < W / 2; Il += TXN) {
       const int q = (2 * Jl + 3) * RW + (2 * Il + 3);
-      c2<T> top = cadd<T>(cadd<T>(sf[q - RW - 1], sf[q - RW + 1]), cscale<T>(sf[q - RW], (T)2));
-      c2<T> mid = cadd<T>(cadd<T>(sf[q - 1], sf[q + 1]), cscale<T>(sf[q], (T)2));
-      c2<T> bot = cadd<T>(cadd<T>(sf[q + RW - 1], sf[q + RW + 1]), cscale<T>(sf[q + RW], (T)2));
-      c2<T> acc = cadd<T>(cadd<T>(top, bot), cscale<T>(mid, (T)2));
-      fc[(long long)(J0 + Jl) * pc + I0 + Il] = cscale<T>(acc, (T)0.25);
+      const c2<T> top = xr::fw3<T>(sf[q - RW - 1], sf[q - RW], sf[q - RW + 1]);
+      const c2<T> mid = xr::fw3<T>(sf[q - 1], sf[q], sf[q + 1]);
+      const c2<T> bot = xr::fw3<T>(sf[q + RW - 1], sf[q + RW], sf[q + RW + 1]);
+      fc[(long long)(J0 + Jl) * pc + I0 + Il] = xr::cscale<T>(xr::fw3<T>(top, mid, bot), (T)0.25);
     }
   }
 }
@@ -135,14 +141,7 @@ __device__ __forceinline__ void prolong_smooth_inner(O2* __restrict__ out, int p
     const c2<T>* e1 = e0 + pc;
     for (int c = tx; c < RW; c += TXN) {
       const int i = gx + c, I = i >> 1, oi = i & 1;
-      c2<T> e = e0[I];
-      if (oi) e = cadd<T>(e, e0[I + 1]);
-      if (oj) {
-        e = cadd<T>(e, e1[I]);
-        if (oi) e = cadd<T>(e, e1[I + 1]);
-      }
-      const T wgt = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
-      su[r * RW + c] = cadd<T>(ur[c], cscale<T>(e, wgt));
+      su[r * RW + c] = xr::cadd<T>(ur[c], bilinear<T>(e0, e1, I, oi, oj));
       sf[r * RW + c] = ldc<T>(fr, c);
       sk[r * RW + c] = kr[c];
     }
@@ -153,9 +152,8 @@ __device__ __forceinline__ void prolong_smooth_inner(O2* __restrict__ out, int p
     for (int c = 2 * tx + par; c < RW - 1; c += 2 * TXN) {
       if (c < 1) continue;
       const int q = r * RW + c;
-      const T k = sk[q], k2 = k * k;
-      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
-      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+      const c2<T> nb = xr::nb4<T>(su[q - 1], su[q + 1], su[q - RW], su[q + RW]);
+      su[q] = xr::gs<T>(sf[q], nb, xr::diag<T>(sk[q], 0, bA));
     }
   }
   __syncthreads();
@@ -164,9 +162,8 @@ __device__ __forceinline__ void prolong_smooth_inner(O2* __restrict__ out, int p
     for (int c = 2 * tx + par; c < 2 + W; c += 2 * TXN) {
       if (c < 2) continue;
       const int q = r * RW + c;
-      const T k = sk[q], k2 = k * k;
-      c2<T> nb = cadd<T>(cadd<T>(su[q - 1], su[q + 1]), cadd<T>(su[q - RW], su[q + RW]));
-      su[q] = cdiv<T>(csub<T>(sf[q], nb), mk<T>(k2 - (T)4, bA * k2));
+      const c2<T> nb = xr::nb4<T>(su[q - 1], su[q + 1], su[q - RW], su[q + RW]);
+      su[q] = xr::gs<T>(sf[q], nb, xr::diag<T>(sk[q], 0, bA));
     }
   }
   __syncthreads();
@@ -214,7 +211,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
     int i = gx + c;
     if (c < RW && in_grid(i, j, n)) {
       int sides = (i == 0) + (i == n) + (j == 0) + (j == n);
-      su[r * RW + c] = cdiv<T>(sf[r * RW + c], row_diag<T>(sk[r * RW + c], sides, bA));
+      su[r * RW + c] = xr::cdiv<T>(sf[r * RW + c], xr::diag<T>(sk[r * RW + c], sides, bA));
     }
   }
   __syncthreads();
@@ -227,7 +224,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
     if (r >= 1 && r <= RH - 2 && c >= 1 && c <= RW - 2 && in_grid(i, j, n)) {
       Nbr b = neighbours(i, j, n);
       c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
-      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+      su[r * RW + c] = xr::gs<T>(sf[r * RW + c], s, xr::diag<T>(sk[r * RW + c], b.sides, bA));
     }
   }
   __syncthreads();
@@ -243,8 +240,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
     if (r >= 2 && r <= RH - 3 && c >= 2 && c <= RW - 3 && in_grid(i, j, n)) {
       Nbr b = neighbours(i, j, n);
       c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
-      c2<T> au = cadd<T>(cmul<T>(row_diag<T>(sk[q], b.sides, bB), su[q]), s);
-      sf[q] = csub<T>(sf[q], au);
+      sf[q] = xr::resid<T>(sf[q], su[q], s, xr::diag<T>(sk[q], b.sides, bB));
     }
   }
   __syncthreads();
@@ -253,19 +249,13 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   for (int q = tid; q < (W / 2) * (HH / 2); q += FT) {
     int J = y0 / 2 + q / (W / 2), I = x0 / 2 + q % (W / 2);
     if (I > nc || J > nc) continue;
-    c2<T> acc = mk<T>(0, 0);
+    c2<T> row[3];
 #pragma unroll
-    for (int bj = -1; bj <= 1; ++bj) {
-      int rr = reflect(2 * J + bj, n) - gy;
-      c2<T> row = mk<T>(0, 0);
-#pragma unroll
-      for (int ai = -1; ai <= 1; ++ai) {
-        c2<T> v = sf[rr * RW + reflect(2 * I + ai, n) - gx];
-        row = cadd<T>(row, ai == 0 ? cscale<T>(v, (T)2) : v);
-      }
-      acc = cadd<T>(acc, bj == 0 ? cscale<T>(row, (T)2) : row);
+    for (int bj = 0; bj < 3; ++bj) {
+      const c2<T>* sr = sf + (reflect(2 * J + bj - 1, n) - gy) * RW - gx;
+      row[bj] = xr::fw3<T>(sr[reflect(2 * I - 1, n)], sr[2 * I], sr[reflect(2 * I + 1, n)]);
     }
-    fc[(long long)J * pc + I] = cscale<T>(acc, (T)0.25);
+    fc[(long long)J * pc + I] = xr::cscale<T>(xr::fw3<T>(row[0], row[1], row[2]), (T)0.25);
   }
 }
 
@@ -296,15 +286,9 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (in_grid(i, j, n)) {
-      int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
-      c2<T> e = ec[(long long)J * pc + I];
-      if (oi) e = cadd<T>(e, ec[(long long)J * pc + I + 1]);
-      if (oj) {
-        e = cadd<T>(e, ec[(long long)(J + 1) * pc + I]);
-        if (oi) e = cadd<T>(e, ec[(long long)(J + 1) * pc + I + 1]);
-      }
-      T w = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
-      su[q] = cadd<T>(upre[(long long)j * pu + i], cscale<T>(e, w));
+      const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
+      const c2<T>* e0 = ec + (long long)J * pc;
+      su[q] = xr::cadd<T>(upre[(long long)j * pu + i], bilinear<T>(e0, e0 + pc, I, oi, oj));
       sf[q] = ldc<T>(f, (long long)j * pf + i);
       sk[q] = kh[(long long)j * pk + i];
     }
@@ -319,7 +303,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
     if (r >= 1 && r <= RH - 2 && c >= 1 && c <= RW - 2 && in_grid(i, j, n)) {
       Nbr b = neighbours(i, j, n);
       c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
-      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+      su[r * RW + c] = xr::gs<T>(sf[r * RW + c], s, xr::diag<T>(sk[r * RW + c], b.sides, bA));
     }
   }
   __syncthreads();
@@ -332,7 +316,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
     if (r >= 2 && r < 2 + HH && c >= 2 && c < 2 + W && in_grid(i, j, n)) {
       Nbr b = neighbours(i, j, n);
       c2<T> s = nb_sum<T>(su, RW, c, r, i, j, n, gx, gy);
-      su[r * RW + c] = cdiv<T>(csub<T>(sf[r * RW + c], s), row_diag<T>(sk[r * RW + c], b.sides, bA));
+      su[r * RW + c] = xr::gs<T>(sf[r * RW + c], s, xr::diag<T>(sk[r * RW + c], b.sides, bA));
     }
   }
   __syncthreads();
@@ -392,17 +376,22 @@ cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, in
 
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
-                                   cudaStream_t s, const Inst& bi) {
+                                   cudaStream_t s, const Inst& bi, int variant) {
   if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
   if (f64_src) return cudaErrorInvalidValue;  // the FP32 form's inputs are FP32
+  if (variant >= 1 && variant < FUSED_VARIANTS)
+    return launch_smooth_restrict_stream(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stream_rows(variant), stop, s, bi);
   return sr_t<float, float2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
 }
 
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
-                                  const int* stop, cudaStream_t s, const Inst& bi) {
+                                  const int* stop, cudaStream_t s, const Inst& bi, int variant) {
   if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
   if (f64_src || out_f64) return cudaErrorInvalidValue;  // the FP32 form's inputs and outputs are FP32
+  if (variant >= 1 && variant < FUSED_VARIANTS)
+    return launch_prolong_smooth_stream(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stream_rows(variant), stop, s,
+                                        bi);
   return ps_t<float, float2, float2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
 }
 

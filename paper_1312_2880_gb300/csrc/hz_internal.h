@@ -44,12 +44,23 @@ cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int p
 // Fused passes for a Gauss-Seidel level with one sweep each way (hz_fused.cu). smooth_restrict
 // writes u (pre-sweep from a zero guess) and fc (coarse right-hand side, h^2-scaled for the
 // coarse level); prolong_smooth writes out = post-sweep(upre + P ec), as double2 when out_f64.
+// variant (FP32 form only): 0 = shared-memory tiles; 1 .. FUSED_VARIANTS-1 = register streaming
+// (hz_stream.cu) with stream_rows(variant) rows per warp. The FP64 form always uses tiles.
+constexpr int FUSED_VARIANTS = 6;
+inline int stream_rows(int variant) { return 8 << variant; }
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
-                                   cudaStream_t s, const Inst& bi = Inst());
+                                   cudaStream_t s, const Inst& bi = Inst(), int variant = 0);
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
-                                  const int* stop, cudaStream_t s, const Inst& bi = Inst());
+                                  const int* stop, cudaStream_t s, const Inst& bi = Inst(), int variant = 0);
+// Register-streaming forms (FP32; n >= 4; u / upre and kh rows 16-byte aligned).
+cudaError_t launch_smooth_restrict_stream(void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
+                                          int pk, int n, double bA, double bB, int seg_rows, const int* stop,
+                                          cudaStream_t s, const Inst& bi);
+cudaError_t launch_prolong_smooth_stream(void* out, int po, const void* upre, int pu, const void* ec, int pc,
+                                         const void* f, int pf, const void* kh, int pk, int n, double bA, int seg_rows,
+                                         const int* stop, cudaStream_t s, const Inst& bi);
 // Kaczmarz level kernels (hz_kaczmarz.cu). The whole-level pair keeps the level in one block's
 // shared memory (at most KACZ_LEVEL_MAX_SMEM bytes: 20 or 40 bytes per node); the tile kernel runs
 // one five-colour sweep per launch, out of place (uin may be null for a zero guess).

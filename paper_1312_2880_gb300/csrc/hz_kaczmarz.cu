@@ -67,18 +67,20 @@ __device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, con
 
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
 
-// All rows of `colour` on the whole (n+1)^2 level, shared pitch n+1: one warp per grid row.
+// All rows of `colour` on the whole (n+1)^2 level, shared pitch n+1. Grid row j holds the colour
+// at i = i0(j) + 5m, m < M = ceil((n+1)/5); thread t takes (j, m) = (t / M, t % M), so on levels up
+// to n = 64 every row action of a colour runs at once (one per thread) between two barriers.
 template <class T>
 __device__ __forceinline__ void level_colour(c2<T>* su, const c2<T>* sf, const T* sk, int n, int colour, T beta) {
-  const int w = n + 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int j = warp; j < w; j += nwarp) {
-    const int i0 = mod5(colour - 2 * j);
-    const bool edge_row = (j == 0 || j == n);
-    for (int i = i0 + 5 * lane; i <= n; i += 5 * 32) {
-      if (edge_row || i == 0 || i == n) row_action<T>(su, sf, sk, w, 0, 0, i, j, n, beta);
-      else row_action_inner<T>(su, sf, sk, w, j * w + i, beta);
-    }
+  const int w = n + 1, M = (w + 4) / 5;
+  for (int t = threadIdx.x; t < w * M; t += blockDim.x) {
+    const int j = t / M, m = t - j * M;
+    const int i = mod5(colour - 2 * j) + 5 * m;
+    if (i > n) continue;
+    if (j == 0 || j == n || i == 0 || i == n)
+      row_action<T>(su, sf, sk, w, 0, 0, i, j, n, beta);
+    else
+      row_action_inner<T>(su, sf, sk, w, j * w + i, beta);
   }
 }
 

@@ -32,12 +32,13 @@ class HzError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
-                ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int)]
+                ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int),
+                ("pass_variant", c_int)]
 
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", c_int), ("H", c_double), ("relax_op", c_int), ("smoother", c_int), ("resid_op", c_int),
-                ("nu", c_int)]
+                ("nu", c_int), ("pass_down", c_int), ("pass_up", c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -117,11 +118,15 @@ def _ptr(t) -> c_void_p:
     return c_void_p(t.data_ptr())
 
 
-def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1) -> Opts:
+def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
+              pass_variant=-1) -> Opts:
+    """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
+    memory tiles; 1..5 = register streaming with 2**(v+3) rows per warp (FP32 form)."""
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
     o.nu_gs, o.nu_kacz, o.guard, o.k_ref, o.batch = nu_gs, nu_kacz, int(bool(guard)), float(k_ref), int(batch)
+    o.pass_variant = int(pass_variant)
     return o
 
 
@@ -132,7 +137,7 @@ def footprint_bytes(n: int, **opts) -> int:
 def _level_dict(li: LevelInfo) -> dict:
     inv = {v: k for k, v in OPS.items()}
     return {"n": li.n, "H": li.H, "relax_op": inv[li.relax_op], "smoother": SMOOTHERS[li.smoother],
-            "resid_op": inv[li.resid_op], "nu": li.nu}
+            "resid_op": inv[li.resid_op], "nu": li.nu, "pass_down": li.pass_down, "pass_up": li.pass_up}
 
 
 def describe_hierarchy(n: int, kfield, beta: float = 0.5, **opts) -> list:
@@ -162,7 +167,7 @@ class Problem:
     """
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
-                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None):
+                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1):
         import torch
 
         L = lib()
@@ -175,7 +180,7 @@ class Problem:
         if st != HZ_OK:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
-        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch)
+        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant)
         self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
