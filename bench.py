@@ -543,7 +543,7 @@ def run_profile_case(args):
     build.build()
     rw = workload(args.profile_case)
     P = hz.Problem(rw.n, rw.kfield, 0.5, variant=rw.variant, precision=args.profile_precision, levels=rw.levels,
-                   k_ref=rw.k_ref)
+                   k_ref=rw.k_ref, pass_variant=args.pass_variant)
     recs = P.profile_iteration(torch.from_numpy(rw.rhs).cuda(), iterations=1)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": rw.name, "launches": len(recs)}))
@@ -566,6 +566,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=150)
     ap.add_argument("--serve-rate", type=float, default=15.0)
     ap.add_argument("--profile-precision", default="fp32")
+    ap.add_argument("--pass-variant", type=int, default=-1,
+                    help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..5: streaming)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
