@@ -153,7 +153,13 @@ __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+// FP32: the hardware reciprocal approximation (rcp.approx, about 1 ulp); the divisors here are
+// |d|^2 of a Helmholtz diagonal, never denormal. FP64: the correctly rounded reciprocal.
+__device__ __forceinline__ float rcp(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
 
 template <class T> __device__ __forceinline__ c2<T> cadd(c2<T> a, c2<T> b) { return mk<T>(add(a.x, b.x), add(a.y, b.y)); }
@@ -168,12 +174,14 @@ __device__ __forceinline__ c2<T> cdiv(c2<T> a, c2<T> d) {
   const T inv = rcp(fma(d.x, d.x, mul(d.y, d.y)));
   return mk<T>(mul(fma(a.x, d.x, mul(a.y, d.y)), inv), mul(fma(a.y, d.x, -mul(a.x, d.y)), inv));
 }
-// Scaled-row diagonal (k H)^2 - 4 + i (beta (k H)^2 + 2 sides k H).
+// Scaled-row diagonal (k H)^2 - 4 + i (beta (k H)^2 + 2 sides k H); two_sides = 2 sides.
 template <class T>
-__device__ __forceinline__ c2<T> diag(T kh, int sides, T beta) {
+__device__ __forceinline__ c2<T> diag2(T kh, T two_sides, T beta) {
   const T k2 = mul(kh, kh);
-  return mk<T>(sub(k2, (T)4), fma((T)(2 * sides), kh, mul(beta, k2)));
+  return mk<T>(sub(k2, (T)4), fma(two_sides, kh, mul(beta, k2)));
 }
+template <class T>
+__device__ __forceinline__ c2<T> diag(T kh, int sides, T beta) { return diag2<T>(kh, (T)(2 * sides), beta); }
 // Sum of a node's four neighbours in the order (W + E) + (S + N).
 template <class T>
 __device__ __forceinline__ c2<T> nb4(c2<T> w, c2<T> e, c2<T> s, c2<T> n) {

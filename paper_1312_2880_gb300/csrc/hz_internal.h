@@ -62,7 +62,7 @@ cudaError_t launch_prolong_smooth_stream(void* out, int po, const void* upre, in
                                          const void* f, int pf, const void* kh, int pk, int n, double bA, int seg_rows,
                                          const int* stop, cudaStream_t s, const Inst& bi);
 // Kaczmarz level kernels (hz_kaczmarz.cu). The whole-level pair keeps the level in one block's
-// shared memory (at most KACZ_LEVEL_MAX_SMEM bytes: 20 or 40 bytes per node); the tile kernel runs
+// shared memory (at most KACZ_LEVEL_MAX_SMEM bytes: 28 or 56 bytes per node); the tile kernel runs
 // one five-colour sweep per launch, out of place (uin may be null for a zero guess).
 constexpr int KACZ_LEVEL_MAX_SMEM = 200 * 1024;
 bool kacz_level_fits(bool fp32, int n);

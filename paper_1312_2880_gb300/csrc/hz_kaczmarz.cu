@@ -5,9 +5,10 @@
 // conj(a_pq) (f~_p - a_p u) / |a_p|^2 to it; rows of one colour (i + 2j) mod 5 have disjoint
 // supports, so a colour is a set of independent updates equal to the sequential sweep over it.
 //
-// kacz_level_*: the whole level lives in one block's shared memory (small levels). Pre mode:
-//   zero guess, nu sweeps (colours 0..4), then the residual with the (B) operator and full
-//   weighting onto the coarse level. Post mode: u_pre + P e_c, then nu sweeps (colours 4..0).
+// kacz_level_*: the whole level lives in one block's shared memory (small levels), with each row's
+//   diagonal and 1/|a_p|^2 computed once per launch. Pre mode: zero guess, nu sweeps (colours
+//   0..4), then the residual with the (B) operator and full weighting onto the coarse level. Post
+//   mode: u_pre + P e_c, then nu sweeps (colours 4..0).
 // kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a 10-node halo:
 //   a colour phase moves information two nodes (a row reads and writes its neighbours), so after
 //   five phases the tile interior holds exactly the sequential sweep's values. Out of place.
@@ -67,22 +68,108 @@ __device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, con
 
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
 
-// All rows of `colour` on the whole (n+1)^2 level, shared pitch n+1. Grid row j holds the colour
-// at i = i0(j) + 5m, m < M = ceil((n+1)/5); thread t takes (j, m) = (t / M, t % M), so on levels up
-// to n = 64 every row action of a colour runs at once (one per thread) between two barriers.
+// ------------------------------------------------------------------ whole level in one block
+// Row constants of a level: the diagonal d_p of the relaxation operator and 1 / |a_p|^2 (|d_p|^2
+// plus the squared off-diagonal coefficients: 1 each, 2 for a mirror neighbour, so 4 on an edge).
 template <class T>
-__device__ __forceinline__ void level_colour(c2<T>* su, const c2<T>* sf, const T* sk, int n, int colour, T beta) {
+__device__ __forceinline__ void row_consts(T kh, int i, int j, int n, T beta, c2<T>* d, T* inv) {
+  const int sides = (i == 0) + (i == n) + (j == 0) + (j == n);
+  *d = row_diag<T>(kh, sides, beta);
+  const T cx = (i == 0 || i == n) ? (T)4 : (T)2, cy = (j == 0 || j == n) ? (T)4 : (T)2;
+  *inv = rcp(cabs2<T>(*d) + cx + cy);
+}
+
+// Row action with precomputed constants, node strictly inside the square: the five values are
+// read once and written once.
+template <class T>
+__device__ __forceinline__ void act_inner(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int p) {
+  const c2<T> d = sd[p];
+  const c2<T> up = su[p], uw = su[p - 1], ue = su[p + 1], us = su[p - w], un = su[p + w];
+  const c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(uw, ue), cadd<T>(us, un)));
+  const c2<T> delta = cscale<T>(csub<T>(sf[p], au), sinv[p]);
+  su[p] = cadd<T>(up, cmulc<T>(d, delta));
+  su[p - 1] = cadd<T>(uw, delta);
+  su[p + 1] = cadd<T>(ue, delta);
+  su[p - w] = cadd<T>(us, delta);
+  su[p + w] = cadd<T>(un, delta);
+}
+// Boundary row: mirror neighbours may coincide (coefficient 2), so each update re-reads.
+template <class T>
+__device__ __forceinline__ void act_edge(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int i,
+                                         int j, int n) {
+  const Nbr b = neighbours(i, j, n);
+  const int p = j * w + i, qw = j * w + b.iw, qe = j * w + b.ie, qs = b.js * w + i, qn = b.jn * w + i;
+  const c2<T> d = sd[p], up = su[p];
+  const c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(su[qw], su[qe]), cadd<T>(su[qs], su[qn])));
+  const c2<T> delta = cscale<T>(csub<T>(sf[p], au), sinv[p]);
+  su[p] = cadd<T>(up, cmulc<T>(d, delta));
+  su[qw] = cadd<T>(su[qw], delta);
+  su[qe] = cadd<T>(su[qe], delta);
+  su[qs] = cadd<T>(su[qs], delta);
+  su[qn] = cadd<T>(su[qn], delta);
+}
+
+// Thread -> row of a colour: grid row j holds the colour at i = i0(j) + 5m, m < M = ceil((n+1)/5),
+// i0 = (colour + 3j) mod 5; thread t takes (j, m) = (t / M, t % M). On levels up to n = 64 the
+// whole colour is one row action per thread between two barriers.
+struct ColourSlot {
+  int j, m, b;  // b = 3j mod 5
+};
+__device__ __forceinline__ ColourSlot colour_slot(int t, int M) {
+  ColourSlot c;
+  c.j = t / M;
+  c.m = t - c.j * M;
+  c.b = (3 * c.j) % 5;
+  return c;
+}
+template <class T>
+__device__ __forceinline__ void act_slot(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n,
+                                         int colour, const ColourSlot& cs) {
+  int i0 = colour + cs.b;
+  i0 = i0 >= 5 ? i0 - 5 : i0;
+  const int i = i0 + 5 * cs.m, w = n + 1;
+  if (i > n || cs.j > n) return;
+  if (cs.j == 0 || cs.j == n || i == 0 || i == n)
+    act_edge<T>(su, sf, sd, sinv, w, i, cs.j, n);
+  else
+    act_inner<T>(su, sf, sd, sinv, w, cs.j * w + i);
+}
+
+// nu sweeps over the colours in the given order (0..4, or 4..0 when `post`).
+template <class T>
+__device__ __forceinline__ void level_sweeps(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n,
+                                             int nu, bool post) {
   const int w = n + 1, M = (w + 4) / 5;
-  for (int t = threadIdx.x; t < w * M; t += blockDim.x) {
-    const int j = t / M, m = t - j * M;
-    const int i = mod5(colour - 2 * j) + 5 * m;
-    if (i > n) continue;
-    if (j == 0 || j == n || i == 0 || i == n)
-      row_action<T>(su, sf, sk, w, 0, 0, i, j, n, beta);
-    else
-      row_action_inner<T>(su, sf, sk, w, j * w + i, beta);
+  if (w * M <= (int)blockDim.x) {
+    const ColourSlot cs = colour_slot(threadIdx.x, M);
+    for (int s = 0; s < nu; ++s)
+      for (int k = 0; k < 5; ++k) {
+        act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, cs);
+        __syncthreads();
+      }
+  } else {
+    for (int s = 0; s < nu; ++s)
+      for (int k = 0; k < 5; ++k) {
+        for (int t = threadIdx.x; t < w * M; t += blockDim.x) act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, colour_slot(t, M));
+        __syncthreads();
+      }
   }
 }
+
+// Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node.
+template <class T>
+struct LevelSmem {
+  c2<T>* su;
+  c2<T>* sf;
+  c2<T>* sd;
+  T* sinv;
+  __device__ LevelSmem(unsigned char* smem, int N) {
+    su = reinterpret_cast<c2<T>*>(smem);
+    sf = su + N;
+    sd = sf + N;
+    sinv = reinterpret_cast<T*>(sd + N);
+  }
+};
 
 template <class T>
 __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ u, int pu, c2<T>* __restrict__ fc,
@@ -95,46 +182,40 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = n + 1, N = w * w;
-  c2<T>* su = reinterpret_cast<c2<T>*>(smem);
-  c2<T>* sf = su + N;
-  T* sk = reinterpret_cast<T*>(sf + N);
+  LevelSmem<T> S(smem, N);
   for (int q = threadIdx.x; q < N; q += LB) {
-    int j = q / w, i = q - j * w;
-    su[q] = mk<T>(0, 0);
-    sf[q] = f[(long long)j * pf + i];
-    sk[q] = kh[(long long)j * pk + i];
+    const int j = q / w, i = q - j * w;
+    S.su[q] = mk<T>(0, 0);
+    S.sf[q] = f[(long long)j * pf + i];
+    row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
   }
   __syncthreads();
-  for (int s = 0; s < nu; ++s)
-    for (int c = 0; c < 5; ++c) {
-      level_colour<T>(su, sf, sk, n, c, bA);
-      __syncthreads();
-    }
+  level_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
+  // u out; residual f~ - B u into sf (the B diagonal from d: same real part, beta_B k^2 imaginary)
   for (int q = threadIdx.x; q < N; q += LB) {
-    int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = su[q];
+    const int j = q / w, i = q - j * w;
+    u[(long long)j * pu + i] = S.su[q];
   }
-  __syncthreads();
-  // residual f~ - B u into sf
   for (int q = threadIdx.x; q < N; q += LB) {
-    int j = q / w, i = q - j * w;
-    Nbr b = neighbours(i, j, n);
-    c2<T> au = cadd<T>(cmul<T>(row_diag<T>(sk[q], b.sides, bB), su[q]),
-                       cadd<T>(cadd<T>(su[j * w + b.iw], su[j * w + b.ie]), cadd<T>(su[b.js * w + i], su[b.jn * w + i])));
-    sf[q] = csub<T>(sf[q], au);
+    const int j = q / w, i = q - j * w;
+    const Nbr b = neighbours(i, j, n);
+    const c2<T> au = cadd<T>(cmul<T>(row_diag<T>(kh[(long long)j * pk + i], b.sides, bB), S.su[q]),
+                             cadd<T>(cadd<T>(S.su[j * w + b.iw], S.su[j * w + b.ie]),
+                                     cadd<T>(S.su[b.js * w + i], S.su[b.jn * w + i])));
+    S.sd[q] = csub<T>(S.sf[q], au);  // sd now holds the residual
   }
   __syncthreads();
   const int nc = n / 2, wc = nc + 1;
   for (int q = threadIdx.x; q < wc * wc; q += LB) {
-    int J = q / wc, I = q - J * wc;
+    const int J = q / wc, I = q - J * wc;
     c2<T> acc = mk<T>(0, 0);
 #pragma unroll
     for (int bj = -1; bj <= 1; ++bj) {
-      int jj = reflect(2 * J + bj, n);
+      const int jj = reflect(2 * J + bj, n);
       c2<T> row = mk<T>(0, 0);
 #pragma unroll
       for (int ai = -1; ai <= 1; ++ai) {
-        c2<T> v = sf[jj * w + reflect(2 * I + ai, n)];
+        const c2<T> v = S.sd[jj * w + reflect(2 * I + ai, n)];
         row = cadd<T>(row, ai == 0 ? cscale<T>(v, (T)2) : v);
       }
       acc = cadd<T>(acc, bj == 0 ? cscale<T>(row, (T)2) : row);
@@ -155,32 +236,26 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = n + 1, N = w * w;
-  c2<T>* su = reinterpret_cast<c2<T>*>(smem);
-  c2<T>* sf = su + N;
-  T* sk = reinterpret_cast<T*>(sf + N);
+  LevelSmem<T> S(smem, N);
   for (int q = threadIdx.x; q < N; q += LB) {
-    int j = q / w, i = q - j * w;
-    int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
+    const int j = q / w, i = q - j * w;
+    const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
     c2<T> e = ec[(long long)J * pc + I];
     if (oi) e = cadd<T>(e, ec[(long long)J * pc + I + 1]);
     if (oj) {
       e = cadd<T>(e, ec[(long long)(J + 1) * pc + I]);
       if (oi) e = cadd<T>(e, ec[(long long)(J + 1) * pc + I + 1]);
     }
-    T wt = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
-    su[q] = cadd<T>(u[(long long)j * pu + i], cscale<T>(e, wt));
-    sf[q] = f[(long long)j * pf + i];
-    sk[q] = kh[(long long)j * pk + i];
+    const T wt = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
+    S.su[q] = cadd<T>(u[(long long)j * pu + i], cscale<T>(e, wt));
+    S.sf[q] = f[(long long)j * pf + i];
+    row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
   }
   __syncthreads();
-  for (int s = 0; s < nu; ++s)
-    for (int c = 4; c >= 0; --c) {
-      level_colour<T>(su, sf, sk, n, c, bA);
-      __syncthreads();
-    }
+  level_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
   for (int q = threadIdx.x; q < N; q += LB) {
-    int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = su[q];
+    const int j = q / w, i = q - j * w;
+    u[(long long)j * pu + i] = S.su[q];
   }
 }
 
@@ -250,7 +325,7 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
 
 template <class T>
 size_t level_smem(int n) {
-  return (size_t)(n + 1) * (n + 1) * (2 * sizeof(c2<T>) + sizeof(T));
+  return (size_t)(n + 1) * (n + 1) * (3 * sizeof(c2<T>) + sizeof(T));
 }
 
 template <class T>

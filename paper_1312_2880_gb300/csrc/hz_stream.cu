@@ -43,8 +43,8 @@ __device__ __forceinline__ int mirror_index(int i, int n) {
   i = i > n ? 2 * n - i : i;
   return i < 0 ? 0 : i;  // beyond one reflection: any node (such lanes never feed an output)
 }
-// Boundary sides of row (or column) j, mirror images included (j in [-n, 2n]).
-__device__ __forceinline__ int sides_of(int j, int n) { return (j == 0) + (j == n); }
+// Twice the boundary sides of row (or column) j, mirror images included (j in [-n, 2n]; n >= 1).
+__device__ __forceinline__ float sides2(int j, int n) { return (j == 0 || j == n) ? 2.0f : 0.0f; }
 
 __device__ __forceinline__ float2 shfl_up2(float2 v) {
   return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
@@ -54,7 +54,7 @@ __device__ __forceinline__ float2 shfl_down2(float2 v) {
 }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return xr::cadd<float>(a, b); }
 __device__ __forceinline__ float2 scl2(float2 a, float s) { return xr::cscale<float>(a, s); }
-__device__ __forceinline__ float2 diag(float k, int sides, float beta) { return xr::diag<float>(k, sides, beta); }
+__device__ __forceinline__ float2 diag(float k, float two_sides, float beta) { return xr::diag2<float>(k, two_sides, beta); }
 
 // ------------------------------------------------------------------ per-lane async copies
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -114,15 +114,16 @@ __device__ __forceinline__ void store_pair(float2* __restrict__ row, int c0, int
 }
 
 struct Lane {  // per-lane constants of a strip
-  int c0, m0, m1, sc0, sc1;
+  int c0, m0, m1;
+  float sc0, sc1;  // twice the boundary sides of the two columns
 };
 __device__ __forceinline__ Lane lane_of(int gx, int n) {
   Lane q;
   q.c0 = gx + 2 * (int)threadIdx.x;
   q.m0 = mirror_index(q.c0, n);
   q.m1 = mirror_index(q.c0 + 1, n);
-  q.sc0 = sides_of(q.c0, n);
-  q.sc1 = sides_of(q.c0 + 1, n);
+  q.sc0 = sides2(q.c0, n);
+  q.sc1 = sides2(q.c0 + 1, n);
   return q;
 }
 
@@ -182,7 +183,7 @@ __device__ __forceinline__ void sr_stage(SRState& S, unsigned char* ring, const 
   const int j0 = y0 - 3 + t;
   {  // red at row t (zero guess)
     L2c& U = S.U[Q];
-    const int rs = sides_of(j0, A.n);
+    const float rs = sides2(j0, A.n);
     if (er == 0)
       U.a = xr::cdiv<float>(S.F[Q].a, diag(S.K[Q].x, q.sc0 + rs, A.bA));
     else
@@ -190,7 +191,7 @@ __device__ __forceinline__ void sr_stage(SRState& S, unsigned char* ring, const 
   }
   if (t >= 1) {  // black at row t-1, column er
     constexpr int q1 = (Q + 3) & 3, q2 = (Q + 2) & 3;
-    const int rs = sides_of(j0 - 1, A.n);
+    const float rs = sides2(j0 - 1, A.n);
     L2c& U = S.U[q1];
     if (er == 1) {
       const float2 nb = xr::nb4<float>(U.a, shfl_down2(U.a), S.U[q2].b, S.U[Q].b);
@@ -204,7 +205,7 @@ __device__ __forceinline__ void sr_stage(SRState& S, unsigned char* ring, const 
   }
   if (t >= 2) {  // residual f - B u at row t-2 and its full-weighting row sum
     constexpr int q1 = (Q + 3) & 3, q2 = (Q + 2) & 3, q3 = (Q + 1) & 3;
-    const int rs = sides_of(j0 - 2, A.n);
+    const float rs = sides2(j0 - 2, A.n);
     const L2c& U = S.U[q2];
     L2c R;
     R.a = xr::resid<float>(S.F[q2].a, U.a, xr::nb4<float>(shfl_up2(U.b), U.b, S.U[q3].a, S.U[q1].a),
@@ -348,7 +349,7 @@ __device__ __forceinline__ void ps_stage(PSState& S, unsigned char* ring, const 
   }
   if (t >= 1) {  // black at row t-1, column er (its vertical neighbours are red v nodes)
     constexpr int q1 = (Q + 3) & 3, q2 = (Q + 2) & 3;
-    const int rs = sides_of(j0 - 1, A.n);
+    const float rs = sides2(j0 - 1, A.n);
     L2c& U = S.U[q1];
     if (er == 1) {
       const float2 nb = xr::nb4<float>(U.a, shfl_down2(U.a), S.U[q2].b, S.U[Q].b);
@@ -360,7 +361,7 @@ __device__ __forceinline__ void ps_stage(PSState& S, unsigned char* ring, const 
   }
   if (t >= 2) {  // red at row t-2, column er (its neighbours are updated black nodes)
     constexpr int q1 = (Q + 3) & 3, q2 = (Q + 2) & 3, q3 = (Q + 1) & 3;
-    const int rs = sides_of(j0 - 2, A.n);
+    const float rs = sides2(j0 - 2, A.n);
     L2c& U = S.U[q2];
     if (er == 0) {
       const float2 nb = xr::nb4<float>(shfl_up2(U.b), U.b, S.U[q3].a, S.U[q1].a);
