@@ -223,9 +223,11 @@ def time_e2e(P, rhs_host, steps: int, tol: float):
 
 
 def profile(P, rhs, iterations: int = 2):
-    """{(kernel, level): [ms per launch]} over `iterations` profiled Bi-CGSTAB iterations."""
+    """{(kernel, level): [ms per launch]} over `iterations` Bi-CGSTAB iterations captured in one
+    CUDA graph with an event node after every kernel (hz_profile_graph): each kernel as it runs
+    inside a solve's graph replay, timed with CUDA events on the library's stream."""
     per = {}
-    for name, level, ms in P.profile_iteration(rhs, iterations=iterations):
+    for name, level, ms in P.profile_iteration(rhs, iterations=iterations, graph=True):
         per.setdefault((name, level), []).append(ms)
     return per
 

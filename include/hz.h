@@ -77,6 +77,10 @@ typedef struct {
                        (the FP64 form always uses 0): -1 (default) = chosen per level at setup by
                        timing every form on the level's arrays (tile autotuner); 0 = shared-memory
                        tiles; 1..5 = register streaming with 2^(v+3) rows per warp */
+  int coarse_tail;  /* 1 (default): the smallest levels, from the first whose whole V-cycle below it
+                       fits one block's shared memory down to the coarsest, run as one launch (same
+                       operations, same results as the per-level kernels for one-sweep Gauss-Seidel
+                       and FP32 Kaczmarz levels); 0: one or more launches per level */
 } hz_hierarchy_opts;
 
 typedef struct {
@@ -89,6 +93,7 @@ typedef struct {
   int pass_down; /* form of the fused pre-smoothing pass (see pass_variant); -1 = not a fused level
                     or not yet set up */
   int pass_up;   /* form of the fused post-smoothing pass; -1 likewise */
+  int in_tail;   /* 1 if the level runs inside the one-block coarse tail (see coarse_tail) */
 } hz_level_info;
 
 typedef struct {
@@ -235,6 +240,7 @@ typedef enum {
   HZ_K_PROLONG_SMOOTH, /* fused: bilinear correction and GS post-sweep */
   HZ_K_KACZ_LEVEL,     /* whole Kaczmarz level in one block (pre: sweeps + residual + FW; post: correction + sweeps) */
   HZ_K_KACZ_SWEEP,     /* one five-colour Kaczmarz sweep over halo tiles */
+  HZ_K_TAIL,           /* coarse tail: every level from hz_level_info.in_tail down, in one block */
   HZ_K_COUNT
 } hz_kernel;
 
@@ -250,6 +256,12 @@ typedef struct {
  * CUDA graph; the arithmetic is the same as hz_solve's first iterations. Writes up to cap
  * records to out (host) and returns the number of launches, or -1 on error. Synchronises. */
 int hz_profile_iteration(hz_problem* p, const double* rhs, double* x, int iterations, hz_kernel_time* out, int cap);
+
+/* The same records for `iterations` iterations captured as one CUDA graph with an event node
+ * after every kernel and replayed once: each record is the time from the previous event node to
+ * the kernel's own, i.e. the kernel as it runs inside the solve's graph replay (back to back,
+ * with the graph's launch gaps). Synchronises. */
+int hz_profile_graph(hz_problem* p, const double* rhs, double* x, int iterations, hz_kernel_time* out, int cap);
 
 /* Name of an hz_kernel. */
 const char* hz_kernel_name(int kernel);

@@ -171,6 +171,9 @@ struct hz_problem {
   const double2* graph_b = nullptr;
   double2* graph_x = nullptr;
   int num_sms = 0;
+  int tail_start = -1;  // first level run by the one-block coarse tail (-1: none)
+  TailArgs tail{};
+  size_t tail_smem = 0;
   std::string err;
   // Solve in flight (see solve_begin/solve_advance/solve_end).
   struct Run {
@@ -186,6 +189,7 @@ struct hz_problem {
   // Measurement: when set, every launch is followed by an event on `stream` (hz_profile_iteration).
   struct ProfRec { int kernel, level; cudaEvent_t ev; };
   std::vector<ProfRec>* prof = nullptr;
+  bool prof_capture = false;  // prof events are recorded into a graph being captured
 };
 
 namespace {
@@ -232,7 +236,10 @@ cudaError_t mark(hz_problem* P, cudaError_t e, int kernel, int level) {
   if (e == cudaSuccess && P->prof) {
     cudaEvent_t ev;
     e = cudaEventCreate(&ev);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, P->stream);
+    // inside a stream capture the record becomes an event node of the graph
+    if (e == cudaSuccess)
+      e = P->prof_capture ? cudaEventRecordWithFlags(ev, P->stream, cudaEventRecordExternal)
+                          : cudaEventRecord(ev, P->stream);
     if (e == cudaSuccess) P->prof->push_back({kernel, level, ev});
   }
   return e;
@@ -453,12 +460,18 @@ Src level_src(const hz_problem* P, int l, const void* f0) {
 // z = V-cycle(f0) with f0 already h^2-scaled; f0 and z (pitch n+1) are double2 in the FP64 form
 // and float2 in the FP32 form.
 cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, bool all = false) {
-  int L = P->plan.levels;
+  const int L = P->plan.levels, lt = P->tail_start;
   cudaError_t e;
-  for (int l = 0; l < L - 1; ++l)
+  const int down_end = lt > 0 ? lt : L - 1;
+  for (int l = 0; l < down_end; ++l)
     if ((e = level_down(P, l, level_src(P, l, f0), stop, all))) return e;
-  if ((e = coarse(P, stop, all))) return e;
-  for (int l = L - 2; l >= 0; --l) {
+  if (lt > 0) {
+    const Inst bi = inst_for(P, lt, all);
+    if ((e = mark(P, launch_tail(P->plan.fp32, P->tail, P->tail_smem, stop, P->stream, bi), HZ_K_TAIL, lt))) return e;
+  } else if ((e = coarse(P, stop, all))) {
+    return e;
+  }
+  for (int l = down_end - 1; l >= 0; --l) {
     void* out = l == 0 ? (void*)z : final_u(P, l);
     int po = l == 0 ? P->n + 1 : P->lv[l].pitch;
     if ((e = level_up(P, l, level_src(P, l, f0), out, po, stop, all))) return e;
@@ -732,7 +745,53 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
 bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
            o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024 ||
-           o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS);
+           o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1);
+}
+
+// ------------------------------------------------------------------ coarse tail
+// The largest tail that fits TAIL_MAX_SMEM: levels lt .. L-1 (lt >= 1), each a one-sweep
+// Gauss-Seidel level or a Kaczmarz level, the last the coarsest.
+void plan_tail(hz_problem* P) {
+  P->tail_start = -1;
+  const int L = P->plan.levels;
+  if (!P->opts.coarse_tail || L < 3) return;
+  const bool fp32 = P->plan.fp32;
+  for (int lt = 1; lt <= L - 2; ++lt) {
+    if (L - lt > TAIL_MAX_LEVELS) continue;
+    bool ok = true;
+    TailArgs A{};
+    A.count = L - lt;
+    for (int l = lt; l < L && ok; ++l) {
+      const Level& V = P->lv[l];
+      TailLevel& T = A.lv[l - lt];
+      T.n = V.n;
+      T.nu = V.nu;
+      T.bA = op_beta(P, V.relax_op);
+      T.bB = op_beta(P, V.resid_op);
+      T.kh = V.kh;
+      T.pk = V.pk;
+      if (l == L - 1)
+        T.kind = TAIL_COARSE;
+      else if (fused(P, l))
+        T.kind = TAIL_GS;
+      else if (V.smoother == HZ_SMOOTH_KACZMARZ)
+        T.kind = TAIL_KACZ;
+      else
+        ok = false;
+    }
+    if (!ok) continue;
+    const size_t smem = tail_layout(fp32, &A);
+    if (smem > (size_t)TAIL_MAX_SMEM) continue;
+    A.ainvT = P->ainvT;
+    A.f_in = P->lv[lt].f;
+    A.pf = P->lv[lt].pitch;
+    A.u_out = final_u(P, lt);
+    A.po = P->lv[lt].pitch;
+    P->tail = A;
+    P->tail_smem = smem;
+    P->tail_start = lt;
+    return;
+  }
 }
 
 // ------------------------------------------------------------------ tile autotuner
@@ -793,7 +852,7 @@ cudaError_t autotune(hz_problem* P) {
   const int B = P->plan.batch;
   for (int l = 0; l < P->plan.levels - 1; ++l) {
     Level& L = P->lv[l];
-    if (!fused(P, l)) continue;
+    if (!fused(P, l) || (P->tail_start > 0 && l >= P->tail_start)) continue;  // tail levels run in hz_tail.cu
     if (!P->plan.fp32) {
       L.var_down = L.var_up = 0;
       continue;
@@ -848,6 +907,7 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->k_ref = 0.0;
   o->batch = 1;
   o->pass_variant = -1;
+  o->coarse_tail = 1;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {
@@ -997,6 +1057,7 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   CK(cudaMemcpyAsync(&status, P->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (status != 0) return fail(P, HZ_EINVAL, "coarsest operator is singular");
+  plan_tail(P);
   CK(autotune(P));
   CK(cudaStreamSynchronize(s));
   P->setup = true;
@@ -1021,6 +1082,7 @@ int hz_describe_hierarchy(const hz_problem* P, const hz_hierarchy_opts* opts, hz
     out[l].resid_op = lv[l].resid_op;
     out[l].nu = lv[l].nu;
     out[l].pass_down = out[l].pass_up = -1;  // chosen at setup
+    out[l].in_tail = 0;
   }
   return pl.levels;
 }
@@ -1038,9 +1100,10 @@ hz_status hz_get_level_info(const hz_problem* P, int level, hz_level_info* info)
   info->smoother = L.smoother;
   info->resid_op = L.resid_op;
   info->nu = L.nu;
-  const bool fz = level < P->plan.levels - 1 && fused(P, level);
+  const bool fz = level < P->plan.levels - 1 && fused(P, level) && !(P->tail_start > 0 && level >= P->tail_start);
   info->pass_down = fz ? L.var_down : -1;
   info->pass_up = fz ? L.var_up : -1;
+  info->in_tail = (P->tail_start > 0 && level >= P->tail_start) ? 1 : 0;
   return HZ_OK;
 }
 
@@ -1230,6 +1293,52 @@ int hz_profile_iteration(hz_problem* P, const double* rhs, double* x, int iterat
   for (auto& r : recs) cudaEventDestroy(r.ev);
   cudaEventDestroy(start);
   P->graph_b = nullptr;  // the captured graph still refers to the previous buffers only by value
+  return count;
+}
+
+int hz_profile_graph(hz_problem* P, const double* rhs, double* x, int iterations, hz_kernel_time* out, int cap) {
+  if (!P || !P->setup || !rhs || !x || iterations < 1 || (cap > 0 && !out)) return -1;
+  StreamScope scope(P);
+  std::vector<hz_problem::ProfRec> recs;
+  cudaEvent_t start;
+  if (cudaEventCreate(&start) != cudaSuccess) return -1;
+  P->kv.b = (const double2*)rhs;
+  P->kv.x = (double2*)x;
+  int count = -1;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = launch_k_init(P->kv, 1e-300, iterations + 1, HIST_CAP, P->stream);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t ec = cudaEventRecordWithFlags(start, P->stream, cudaEventRecordExternal);
+    P->prof = &recs;
+    P->prof_capture = true;
+    for (int it = 0; it < iterations && ec == cudaSuccess; ++it) ec = enqueue_iteration(P);
+    P->prof = nullptr;
+    P->prof_capture = false;
+    e = cudaStreamEndCapture(P->stream, &g);
+    if (ec) e = ec;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e == cudaSuccess) {
+    cudaEvent_t prev = start;
+    count = (int)recs.size();
+    for (int q = 0; q < count; ++q) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, prev, recs[q].ev);
+      if (q < cap) out[q] = hz_kernel_time{recs[q].kernel, recs[q].level, ms};
+      prev = recs[q].ev;
+    }
+  } else {
+    cuda_fail(P, e, "hz_profile_graph");
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (g) cudaGraphDestroy(g);
+  for (auto& r : recs) cudaEventDestroy(r.ev);
+  cudaEventDestroy(start);
+  P->graph_b = nullptr;
   return count;
 }
 
@@ -1445,7 +1554,7 @@ const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s", "k_x_half",
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
-                                "kacz_sweep"};
+                                "kacz_sweep", "coarse_tail"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -169,6 +169,12 @@ template <class T>
 __device__ __forceinline__ c2<T> cmul(c2<T> a, c2<T> b) {
   return mk<T>(fma(a.x, b.x, -mul(a.y, b.y)), fma(a.x, b.y, mul(a.y, b.x)));
 }
+// conj(a) * b
+template <class T>
+__device__ __forceinline__ c2<T> cmulc(c2<T> a, c2<T> b) {
+  return mk<T>(fma(a.x, b.x, mul(a.y, b.y)), fma(a.x, b.y, -mul(a.y, b.x)));
+}
+template <class T> __device__ __forceinline__ T cabs2(c2<T> a) { return fma(a.x, a.x, mul(a.y, a.y)); }
 template <class T>
 __device__ __forceinline__ c2<T> cdiv(c2<T> a, c2<T> d) {
   const T inv = rcp(fma(d.x, d.x, mul(d.y, d.y)));
@@ -197,6 +203,29 @@ __device__ __forceinline__ c2<T> resid(c2<T> f, c2<T> u, c2<T> nb, c2<T> d) {
 // One row of full weighting: (w + e) + 2 c.
 template <class T>
 __device__ __forceinline__ c2<T> fw3(c2<T> w, c2<T> c, c2<T> e) { return cadd<T>(cadd<T>(w, e), cscale<T>(c, (T)2)); }
+// Full weighting at coarse node (I, J) of a fine array r (row pitch pr, n intervals), fine nodes
+// outside the square mirrored: rows (w + e) + 2 c, then across rows the same, times 4/16 (the
+// restricted residual is scaled by (2h)^2 / h^2 = 4 for the coarse level's h^2-scaled rows).
+template <class T>
+__device__ __forceinline__ c2<T> fw_node(const c2<T>* r, int pr, int n, int I, int J) {
+  c2<T> row[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const c2<T>* rr = r + (long long)reflect(2 * J + b - 1, n) * pr;
+    row[b] = fw3<T>(rr[reflect(2 * I - 1, n)], rr[2 * I], rr[reflect(2 * I + 1, n)]);
+  }
+  return cscale<T>(fw3<T>(row[0], row[1], row[2]), (T)0.25);
+}
+// Bilinear interpolation of the coarse correction at fine node (2I + oi, 2J + oj) from coarse rows
+// e0 (J) and e1 (J + 1): coincident nodes copy, edge midpoints average two, centres four, in the
+// order ((e00 + e10) + (e01 + e11)) / 4.
+template <class T>
+__device__ __forceinline__ c2<T> bilinear(const c2<T>* e0, const c2<T>* e1, int I, int oi, int oj) {
+  if (oi && oj) return cscale<T>(cadd<T>(cadd<T>(e0[I], e1[I]), cadd<T>(e0[I + 1], e1[I + 1])), (T)0.25);
+  if (oi) return cscale<T>(cadd<T>(e0[I], e0[I + 1]), (T)0.5);
+  if (oj) return cscale<T>(cadd<T>(e0[I], e1[I]), (T)0.5);
+  return e0[I];
+}
 }  // namespace xr
 
 }  // namespace hz

@@ -43,17 +43,6 @@ __device__ __forceinline__ c2<T> nb_sum(const c2<T>* s, int rw, int c, int r, in
                     s[(b.jn - gy) * rw + c]);
 }
 
-// Bilinear interpolation of the coarse correction at fine node (2I + oi, 2J + oj) from coarse rows
-// e0 (J) and e1 (J + 1): coincident nodes copy, edge midpoints average two, centres four, in the
-// order ((e00 + e10) + (e01 + e11)) / 4 that the streaming form also takes.
-template <class T>
-__device__ __forceinline__ c2<T> bilinear(const c2<T>* e0, const c2<T>* e1, int I, int oi, int oj) {
-  if (oi && oj) return xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e0[I], e1[I]), xr::cadd<T>(e0[I + 1], e1[I + 1])), (T)0.25);
-  if (oi) return xr::cscale<T>(xr::cadd<T>(e0[I], e0[I + 1]), (T)0.5);
-  if (oj) return xr::cscale<T>(xr::cadd<T>(e0[I], e1[I]), (T)0.5);
-  return e0[I];
-}
-
 // ---------------------------------------------------------------- interior tiles
 // Tiles whose region lies strictly inside the square (no boundary rows, no mirrors, every node
 // present) run these paths: a 32 x 8 thread layout walks rows and columns with fixed strides,
@@ -141,7 +130,7 @@ __device__ __forceinline__ void prolong_smooth_inner(O2* __restrict__ out, int p
     const c2<T>* e1 = e0 + pc;
     for (int c = tx; c < RW; c += TXN) {
       const int i = gx + c, I = i >> 1, oi = i & 1;
-      su[r * RW + c] = xr::cadd<T>(ur[c], bilinear<T>(e0, e1, I, oi, oj));
+      su[r * RW + c] = xr::cadd<T>(ur[c], xr::bilinear<T>(e0, e1, I, oi, oj));
       sf[r * RW + c] = ldc<T>(fr, c);
       sk[r * RW + c] = kr[c];
     }
@@ -249,13 +238,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   for (int q = tid; q < (W / 2) * (HH / 2); q += FT) {
     int J = y0 / 2 + q / (W / 2), I = x0 / 2 + q % (W / 2);
     if (I > nc || J > nc) continue;
-    c2<T> row[3];
-#pragma unroll
-    for (int bj = 0; bj < 3; ++bj) {
-      const c2<T>* sr = sf + (reflect(2 * J + bj - 1, n) - gy) * RW - gx;
-      row[bj] = xr::fw3<T>(sr[reflect(2 * I - 1, n)], sr[2 * I], sr[reflect(2 * I + 1, n)]);
-    }
-    fc[(long long)J * pc + I] = xr::cscale<T>(xr::fw3<T>(row[0], row[1], row[2]), (T)0.25);
+    fc[(long long)J * pc + I] = xr::fw_node<T>(sf - gy * RW - gx, RW, n, I, J);
   }
 }
 
@@ -288,7 +271,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
     if (in_grid(i, j, n)) {
       const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
       const c2<T>* e0 = ec + (long long)J * pc;
-      su[q] = xr::cadd<T>(upre[(long long)j * pu + i], bilinear<T>(e0, e0 + pc, I, oi, oj));
+      su[q] = xr::cadd<T>(upre[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, I, oi, oj));
       sf[q] = ldc<T>(f, (long long)j * pf + i);
       sk[q] = kh[(long long)j * pk + i];
     }

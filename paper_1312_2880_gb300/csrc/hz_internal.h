@@ -73,6 +73,31 @@ cudaError_t launch_kacz_level_post(bool fp32, void* u, int pu, const void* ec, i
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
                                    bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
                                    cudaStream_t s, const Inst& bi = Inst());
+// Coarse tail (hz_tail.cu): levels lt .. L-1 of the V-cycle in one block's shared memory.
+constexpr int TAIL_MAX_LEVELS = 12;
+constexpr int TAIL_MAX_SMEM = 200 * 1024;
+enum { TAIL_GS = 0, TAIL_KACZ = 1, TAIL_COARSE = 2 };
+struct TailLevel {
+  int n, kind, nu;   // n_l; TAIL_*; sweeps (Kaczmarz)
+  double bA, bB;     // shift of the relaxation (A) and residual (B) operators
+  const void* kh;    // k H of the level (device, working precision, pitch pk)
+  int pk;
+  unsigned off_u, off_f, off_k, off_d, off_inv;  // shared-memory byte offsets (tail_layout)
+};
+struct TailArgs {
+  int count;  // levels in the tail, the last the coarsest
+  TailLevel lv[TAIL_MAX_LEVELS];
+  unsigned off_r;    // residual scratch
+  const void* ainvT; // coarsest inverse (transposed)
+  const void* f_in;  // right-hand side of the first tail level (pitch pf)
+  int pf;
+  void* u_out;       // its final u (pitch po)
+  int po;
+};
+// Fills the offsets; returns the shared memory the tail needs.
+size_t tail_layout(bool fp32, TailArgs* A);
+cudaError_t launch_tail(bool fp32, const TailArgs& A, size_t smem, const int* stop, cudaStream_t s,
+                        const Inst& bi = Inst());
 // dst (precision of fp32, pitch pd) = src (double2, pitch ps) * scale, on an (n+1)^2 grid.
 cudaError_t launch_import(bool fp32, void* dst, int pd, const double2* src, int ps, int n, double scale,
                           cudaStream_t s);

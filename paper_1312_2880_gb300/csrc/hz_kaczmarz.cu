@@ -6,7 +6,7 @@
 // supports, so a colour is a set of independent updates equal to the sequential sweep over it.
 //
 // kacz_level_*: the whole level lives in one block's shared memory (small levels), with each row's
-//   diagonal and 1/|a_p|^2 computed once per launch. Pre mode: zero guess, nu sweeps (colours
+//   diagonal and 1/|a_p|^2 computed once per launch (operations in hz_level.cuh). Pre mode: zero guess, nu sweeps (colours
 //   0..4), then the residual with the (B) operator and full weighting onto the coarse level. Post
 //   mode: u_pre + P e_c, then nu sweeps (colours 4..0).
 // kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a 10-node halo:
@@ -16,6 +16,7 @@
 
 #include "hz_common.cuh"
 #include "hz_internal.h"
+#include "hz_level.cuh"
 
 namespace hz {
 
@@ -69,93 +70,6 @@ __device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, con
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
 
 // ------------------------------------------------------------------ whole level in one block
-// Row constants of a level: the diagonal d_p of the relaxation operator and 1 / |a_p|^2 (|d_p|^2
-// plus the squared off-diagonal coefficients: 1 each, 2 for a mirror neighbour, so 4 on an edge).
-template <class T>
-__device__ __forceinline__ void row_consts(T kh, int i, int j, int n, T beta, c2<T>* d, T* inv) {
-  const int sides = (i == 0) + (i == n) + (j == 0) + (j == n);
-  *d = row_diag<T>(kh, sides, beta);
-  const T cx = (i == 0 || i == n) ? (T)4 : (T)2, cy = (j == 0 || j == n) ? (T)4 : (T)2;
-  *inv = rcp(cabs2<T>(*d) + cx + cy);
-}
-
-// Row action with precomputed constants, node strictly inside the square: the five values are
-// read once and written once.
-template <class T>
-__device__ __forceinline__ void act_inner(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int p) {
-  const c2<T> d = sd[p];
-  const c2<T> up = su[p], uw = su[p - 1], ue = su[p + 1], us = su[p - w], un = su[p + w];
-  const c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(uw, ue), cadd<T>(us, un)));
-  const c2<T> delta = cscale<T>(csub<T>(sf[p], au), sinv[p]);
-  su[p] = cadd<T>(up, cmulc<T>(d, delta));
-  su[p - 1] = cadd<T>(uw, delta);
-  su[p + 1] = cadd<T>(ue, delta);
-  su[p - w] = cadd<T>(us, delta);
-  su[p + w] = cadd<T>(un, delta);
-}
-// Boundary row: mirror neighbours may coincide (coefficient 2), so each update re-reads.
-template <class T>
-__device__ __forceinline__ void act_edge(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int i,
-                                         int j, int n) {
-  const Nbr b = neighbours(i, j, n);
-  const int p = j * w + i, qw = j * w + b.iw, qe = j * w + b.ie, qs = b.js * w + i, qn = b.jn * w + i;
-  const c2<T> d = sd[p], up = su[p];
-  const c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(su[qw], su[qe]), cadd<T>(su[qs], su[qn])));
-  const c2<T> delta = cscale<T>(csub<T>(sf[p], au), sinv[p]);
-  su[p] = cadd<T>(up, cmulc<T>(d, delta));
-  su[qw] = cadd<T>(su[qw], delta);
-  su[qe] = cadd<T>(su[qe], delta);
-  su[qs] = cadd<T>(su[qs], delta);
-  su[qn] = cadd<T>(su[qn], delta);
-}
-
-// Thread -> row of a colour: grid row j holds the colour at i = i0(j) + 5m, m < M = ceil((n+1)/5),
-// i0 = (colour + 3j) mod 5; thread t takes (j, m) = (t / M, t % M). On levels up to n = 64 the
-// whole colour is one row action per thread between two barriers.
-struct ColourSlot {
-  int j, m, b;  // b = 3j mod 5
-};
-__device__ __forceinline__ ColourSlot colour_slot(int t, int M) {
-  ColourSlot c;
-  c.j = t / M;
-  c.m = t - c.j * M;
-  c.b = (3 * c.j) % 5;
-  return c;
-}
-template <class T>
-__device__ __forceinline__ void act_slot(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n,
-                                         int colour, const ColourSlot& cs) {
-  int i0 = colour + cs.b;
-  i0 = i0 >= 5 ? i0 - 5 : i0;
-  const int i = i0 + 5 * cs.m, w = n + 1;
-  if (i > n || cs.j > n) return;
-  if (cs.j == 0 || cs.j == n || i == 0 || i == n)
-    act_edge<T>(su, sf, sd, sinv, w, i, cs.j, n);
-  else
-    act_inner<T>(su, sf, sd, sinv, w, cs.j * w + i);
-}
-
-// nu sweeps over the colours in the given order (0..4, or 4..0 when `post`).
-template <class T>
-__device__ __forceinline__ void level_sweeps(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n,
-                                             int nu, bool post) {
-  const int w = n + 1, M = (w + 4) / 5;
-  if (w * M <= (int)blockDim.x) {
-    const ColourSlot cs = colour_slot(threadIdx.x, M);
-    for (int s = 0; s < nu; ++s)
-      for (int k = 0; k < 5; ++k) {
-        act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, cs);
-        __syncthreads();
-      }
-  } else {
-    for (int s = 0; s < nu; ++s)
-      for (int k = 0; k < 5; ++k) {
-        for (int t = threadIdx.x; t < w * M; t += blockDim.x) act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, colour_slot(t, M));
-        __syncthreads();
-      }
-  }
-}
-
 // Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node.
 template <class T>
 struct LevelSmem {
@@ -187,41 +101,14 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
     const int j = q / w, i = q - j * w;
     S.su[q] = mk<T>(0, 0);
     S.sf[q] = f[(long long)j * pf + i];
-    row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
   }
   __syncthreads();
-  level_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
-  // u out; residual f~ - B u into sf (the B diagonal from d: same real part, beta_B k^2 imaginary)
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = S.su[q];
-  }
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    const Nbr b = neighbours(i, j, n);
-    const c2<T> au = cadd<T>(cmul<T>(row_diag<T>(kh[(long long)j * pk + i], b.sides, bB), S.su[q]),
-                             cadd<T>(cadd<T>(S.su[j * w + b.iw], S.su[j * w + b.ie]),
-                                     cadd<T>(S.su[b.js * w + i], S.su[b.jn * w + i])));
-    S.sd[q] = csub<T>(S.sf[q], au);  // sd now holds the residual
-  }
+  lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
+  for (int q = threadIdx.x; q < N; q += LB) u[(long long)(q / w) * pu + q % w] = S.su[q];
+  lvl::residual<T>(S.sd, S.su, S.sf, kh, pk, n, bB);  // the residual replaces the diagonals
   __syncthreads();
-  const int nc = n / 2, wc = nc + 1;
-  for (int q = threadIdx.x; q < wc * wc; q += LB) {
-    const int J = q / wc, I = q - J * wc;
-    c2<T> acc = mk<T>(0, 0);
-#pragma unroll
-    for (int bj = -1; bj <= 1; ++bj) {
-      const int jj = reflect(2 * J + bj, n);
-      c2<T> row = mk<T>(0, 0);
-#pragma unroll
-      for (int ai = -1; ai <= 1; ++ai) {
-        const c2<T> v = S.sd[jj * w + reflect(2 * I + ai, n)];
-        row = cadd<T>(row, ai == 0 ? cscale<T>(v, (T)2) : v);
-      }
-      acc = cadd<T>(acc, bj == 0 ? cscale<T>(row, (T)2) : row);
-    }
-    fc[(long long)J * pc + I] = cscale<T>(acc, (T)0.25);
-  }
+  lvl::restrict_fw<T>(fc, pc, S.sd, n);
 }
 
 template <class T>
@@ -239,24 +126,14 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   LevelSmem<T> S(smem, N);
   for (int q = threadIdx.x; q < N; q += LB) {
     const int j = q / w, i = q - j * w;
-    const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
-    c2<T> e = ec[(long long)J * pc + I];
-    if (oi) e = cadd<T>(e, ec[(long long)J * pc + I + 1]);
-    if (oj) {
-      e = cadd<T>(e, ec[(long long)(J + 1) * pc + I]);
-      if (oi) e = cadd<T>(e, ec[(long long)(J + 1) * pc + I + 1]);
-    }
-    const T wt = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
-    S.su[q] = cadd<T>(u[(long long)j * pu + i], cscale<T>(e, wt));
+    const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
+    S.su[q] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
     S.sf[q] = f[(long long)j * pf + i];
-    row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
   }
   __syncthreads();
-  level_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = S.su[q];
-  }
+  lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
+  for (int q = threadIdx.x; q < N; q += LB) u[(long long)(q / w) * pu + q % w] = S.su[q];
 }
 
 template <class T, class F2>

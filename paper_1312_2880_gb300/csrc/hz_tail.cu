@@ -1,0 +1,139 @@
+// The coarse tail of the V-cycle (Sec. 5) in one block: every level from the first one that fits
+// down to the coarsest is held in shared memory, and one launch runs its pre-relaxation and
+// restriction on the way down, the dense coarsest solve, and the correction and post-relaxation
+// on the way up. Below a few thousand nodes a level's kernels are bound by launch and ramp
+// latency, not by work, so this replaces 2 (L - lt) - 1 launches by one. Each level's operations
+// are the ones the per-level kernels perform (hz_level.cuh, fixed-rounding arithmetic), so the
+// result is bitwise the same as without the tail wherever those kernels use the same forms
+// (one-sweep Gauss-Seidel levels, whole-level Kaczmarz in FP32).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hz_common.cuh"
+#include "hz_internal.h"
+#include "hz_level.cuh"
+
+namespace hz {
+
+namespace {
+
+constexpr int TAIL_THREADS = 1024;
+
+template <class T>
+__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, const int* __restrict__ stop, Inst bi) {
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const c2<T>* fin = reinterpret_cast<const c2<T>*>(A.f_in) + blockIdx.z * bi.sf;
+  c2<T>* uout = reinterpret_cast<c2<T>*>(A.u_out) + blockIdx.z * bi.so;
+  auto U = [&](int l) { return reinterpret_cast<c2<T>*>(smem + A.lv[l].off_u); };
+  auto F = [&](int l) { return reinterpret_cast<c2<T>*>(smem + A.lv[l].off_f); };
+  auto K = [&](int l) { return reinterpret_cast<T*>(smem + A.lv[l].off_k); };
+  auto D = [&](int l) { return reinterpret_cast<c2<T>*>(smem + A.lv[l].off_d); };
+  auto V = [&](int l) { return reinterpret_cast<T*>(smem + A.lv[l].off_inv); };
+  c2<T>* R = reinterpret_cast<c2<T>*>(smem + A.off_r);
+  const int last = A.count - 1;
+
+  // right-hand side of the first level; k H (Gauss-Seidel) or row constants (Kaczmarz) of every
+  // relaxation level; zero guess of the Kaczmarz levels
+  for (int l = 0; l < last; ++l) {
+    const TailLevel& L = A.lv[l];
+    const int w = L.n + 1, N = w * w;
+    const T* kh = reinterpret_cast<const T*>(L.kh);
+    for (int q = threadIdx.x; q < N; q += TAIL_THREADS) {
+      const int j = q / w, i = q - j * w;
+      if (l == 0) F(0)[q] = fin[(long long)j * A.pf + i];
+      if (L.kind == TAIL_GS) {
+        K(l)[q] = kh[(long long)j * L.pk + i];
+      } else {
+        lvl::row_consts<T>(kh[(long long)j * L.pk + i], i, j, L.n, (T)L.bA, &D(l)[q], &V(l)[q]);
+        U(l)[q] = mk<T>(0, 0);
+      }
+    }
+  }
+  __syncthreads();
+
+  // down: relax from a zero guess, residual with the (B) operator, full weighting
+  for (int l = 0; l < last; ++l) {
+    const TailLevel& L = A.lv[l];
+    if (L.kind == TAIL_GS) {
+      lvl::gs_pre<T>(U(l), F(l), K(l), L.n, (T)L.bA);
+      lvl::residual<T>(R, U(l), F(l), K(l), L.n + 1, L.n, (T)L.bB);
+    } else {
+      lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, false);
+      lvl::residual<T>(R, U(l), F(l), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
+    }
+    __syncthreads();
+    lvl::restrict_fw<T>(F(l + 1), A.lv[l + 1].n + 1, R, L.n);
+    __syncthreads();
+  }
+
+  // coarsest: u = A^-1 f
+  {
+    const int m = (A.lv[last].n + 1) * (A.lv[last].n + 1);
+    const c2<T>* ainvT = reinterpret_cast<const c2<T>*>(A.ainvT);
+    for (int r = threadIdx.x; r < m; r += TAIL_THREADS) U(last)[r] = lvl::coarse_row<T>(ainvT, F(last), m, r);
+    __syncthreads();
+  }
+
+  // up: bilinear correction, relaxation in the reverse order
+  for (int l = last - 1; l >= 0; --l) {
+    const TailLevel& L = A.lv[l];
+    lvl::prolong_add<T>(U(l), U(l + 1), A.lv[l + 1].n + 1, L.n);
+    __syncthreads();
+    if (L.kind == TAIL_GS)
+      lvl::gs_post<T>(U(l), F(l), K(l), L.n, (T)L.bA);
+    else
+      lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, true);
+  }
+
+  const int w = A.lv[0].n + 1;
+  for (int q = threadIdx.x; q < w * w; q += TAIL_THREADS) uout[(long long)(q / w) * A.po + q % w] = U(0)[q];
+}
+
+}  // namespace
+
+size_t tail_layout(bool fp32, TailArgs* A) {
+  const size_t c = fp32 ? sizeof(float2) : sizeof(double2), r = fp32 ? sizeof(float) : sizeof(double);
+  size_t off = 0, rmax = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 15) & ~(size_t)15;
+    return (unsigned)o;
+  };
+  for (int l = 0; l < A->count; ++l) {
+    TailLevel& L = A->lv[l];
+    const size_t N = (size_t)(L.n + 1) * (L.n + 1);
+    L.off_u = take(N * c);
+    L.off_f = take(N * c);
+    L.off_k = L.off_d = L.off_inv = 0;
+    if (L.kind == TAIL_GS) L.off_k = take(N * r);
+    if (L.kind == TAIL_KACZ) {
+      L.off_d = take(N * c);
+      L.off_inv = take(N * r);
+    }
+    if (L.kind != TAIL_COARSE) rmax = std::max(rmax, N);
+  }
+  A->off_r = take(rmax * c);
+  return off;
+}
+
+cudaError_t launch_tail(bool fp32, const TailArgs& A, size_t smem, const int* stop, cudaStream_t s, const Inst& bi) {
+  if (A.count < 2 || A.count > TAIL_MAX_LEVELS || smem > (size_t)TAIL_MAX_SMEM) return cudaErrorInvalidValue;
+  static bool ready[2] = {false, false};
+  cudaError_t e;
+  if (!ready[fp32]) {
+    e = fp32 ? cudaFuncSetAttribute(tail_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM)
+             : cudaFuncSetAttribute(tail_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM);
+    if (e) return e;
+    ready[fp32] = true;
+  }
+  dim3 grid(1, 1, bi.count);
+  if (fp32)
+    tail_kernel<float><<<grid, TAIL_THREADS, smem, s>>>(A, stop, bi);
+  else
+    tail_kernel<double><<<grid, TAIL_THREADS, smem, s>>>(A, stop, bi);
+  return cudaGetLastError();
+}
+
+}  // namespace hz

@@ -10,6 +10,7 @@
 
 #include "hz_common.cuh"
 #include "hz_internal.h"
+#include "hz_level.cuh"
 
 namespace hz {
 
@@ -172,11 +173,7 @@ __global__ void coarse_solve_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* 
   int w = nc + 1, m = w * w;
   for (int q = threadIdx.x; q < m; q += blockDim.x) fs[q] = f[(long long)(q / w) * pf + q % w];
   __syncthreads();
-  for (int r = threadIdx.x; r < m; r += blockDim.x) {
-    c2<T> acc = mk<T>(0, 0);
-    for (int c = 0; c < m; ++c) acc = cadd<T>(acc, cmul<T>(ainvT[(long long)c * m + r], fs[c]));
-    u[(long long)(r / w) * pu + r % w] = acc;
-  }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) u[(long long)(r / w) * pu + r % w] = lvl::coarse_row<T>(ainvT, fs, m, r);
 }
 
 // Dense scaled operator of the coarsest level (row-major, m x m) next to the identity, then

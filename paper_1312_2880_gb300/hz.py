@@ -33,12 +33,12 @@ class HzError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
                 ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int),
-                ("pass_variant", c_int)]
+                ("pass_variant", c_int), ("coarse_tail", c_int)]
 
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", c_int), ("H", c_double), ("relax_op", c_int), ("smoother", c_int), ("resid_op", c_int),
-                ("nu", c_int), ("pass_down", c_int), ("pass_up", c_int)]
+                ("nu", c_int), ("pass_down", c_int), ("pass_up", c_int), ("in_tail", c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "hz_level_sweeps": (c_int, [P, c_int, c_void_p, c_void_p, c_int, c_int]),
         "hz_coarse_solve": (c_int, [P, c_void_p, c_void_p]),
         "hz_profile_iteration": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
+        "hz_profile_graph": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
         "hz_kernel_name": (ctypes.c_char_p, [c_int]),
         "hz_last_error": (ctypes.c_char_p, [P]),
         "hz_status_string": (ctypes.c_char_p, [c_int]),
@@ -119,7 +120,7 @@ def _ptr(t) -> c_void_p:
 
 
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
-              pass_variant=-1) -> Opts:
+              pass_variant=-1, coarse_tail=True) -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
     memory tiles; 1..5 = register streaming with 2**(v+3) rows per warp (FP32 form)."""
     o = Opts()
@@ -127,6 +128,7 @@ def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, gua
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
     o.nu_gs, o.nu_kacz, o.guard, o.k_ref, o.batch = nu_gs, nu_kacz, int(bool(guard)), float(k_ref), int(batch)
     o.pass_variant = int(pass_variant)
+    o.coarse_tail = int(bool(coarse_tail))
     return o
 
 
@@ -137,7 +139,8 @@ def footprint_bytes(n: int, **opts) -> int:
 def _level_dict(li: LevelInfo) -> dict:
     inv = {v: k for k, v in OPS.items()}
     return {"n": li.n, "H": li.H, "relax_op": inv[li.relax_op], "smoother": SMOOTHERS[li.smoother],
-            "resid_op": inv[li.resid_op], "nu": li.nu, "pass_down": li.pass_down, "pass_up": li.pass_up}
+            "resid_op": inv[li.resid_op], "nu": li.nu, "pass_down": li.pass_down, "pass_up": li.pass_up,
+            "in_tail": bool(li.in_tail)}
 
 
 def describe_hierarchy(n: int, kfield, beta: float = 0.5, **opts) -> list:
@@ -167,7 +170,7 @@ class Problem:
     """
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
-                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1):
+                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1, coarse_tail=True):
         import torch
 
         L = lib()
@@ -180,7 +183,8 @@ class Problem:
         if st != HZ_OK:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
-        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant)
+        self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant,
+                              coarse_tail)
         self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
@@ -303,13 +307,15 @@ class Problem:
         return x, {"iterations": info.iterations, "relres_true": info.relres_true, "status": st,
                    "restarts": info.restarts}, hist[: info.history_len].copy()
 
-    def profile_iteration(self, rhs, iterations: int = 1, x=None) -> list:
-        """Per-launch device times (ms) of `iterations` Bi-CGSTAB iterations: [(kernel, level, ms)]."""
+    def profile_iteration(self, rhs, iterations: int = 1, x=None, graph: bool = False) -> list:
+        """Per-launch device times (ms) of `iterations` Bi-CGSTAB iterations: [(kernel, level, ms)].
+        graph=True: measured inside one CUDA graph replay (hz_profile_graph), as in a solve."""
         self._stream()
         x = self._empty() if x is None else x
         cap = 4096
         out = (KernelTime * cap)()
-        cnt = lib().hz_profile_iteration(self._h, _ptr(rhs), _ptr(x), iterations, out, cap)
+        fn = lib().hz_profile_graph if graph else lib().hz_profile_iteration
+        cnt = fn(self._h, _ptr(rhs), _ptr(x), iterations, out, cap)
         if cnt < 0:
             raise HzError(HZ_ECUDA, lib().hz_last_error(self._h).decode())
         return [(lib().hz_kernel_name(out[q].kernel).decode(), out[q].level, float(out[q].ms)) for q in range(min(cnt, cap))]
