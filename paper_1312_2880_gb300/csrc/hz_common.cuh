@@ -16,6 +16,16 @@
 
 namespace hz {
 
+// Programmatic dependent launch: every kernel is launched allowed to start while its predecessor
+// in the stream (or graph) is still running. It first waits until the predecessor has completed
+// and its writes are visible (griddepcontrol.wait; nothing is read before), then allows its own
+// successor to begin launching, so launch latency overlaps execution. Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 template <class T> struct cplx_of;
 template <> struct cplx_of<double> { using type = double2; };
 template <> struct cplx_of<float> { using type = float2; };

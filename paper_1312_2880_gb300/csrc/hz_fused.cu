@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
                                                               int pc, const F2* __restrict__ f, int pf,
                                                               const T* __restrict__ kh, int pk, int n, T bA, T bB,
                                                               const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   fc += blockIdx.z * bi.sc;
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
                                                              const F2* __restrict__ f, int pf,
                                                              const T* __restrict__ kh, int pk, int n, T bA,
                                                              const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   out += blockIdx.z * bi.so;
   upre += blockIdx.z * bi.su;
@@ -331,7 +333,7 @@ cudaError_t sr_t(void* u, int pu, void* fc, int pc, const void* f, int pf, const
   constexpr int CW = TileShape<T>::W / 2, CH = TileShape<T>::H / 2;
   int nc = n / 2;
   dim3 grid((nc + CW) / CW, (nc + CH) / CH, bi.count);
-  smooth_restrict_kernel<T, F2><<<grid, dim3(TXN, TYN), sm, s>>>((c2<T>*)u, pu, (c2<T>*)fc, pc, (const F2*)f, pf,
+  pdl_launch(smooth_restrict_kernel<T, F2>, grid, dim3(TXN, TYN), sm, s, (c2<T>*)u, pu, (c2<T>*)fc, pc, (const F2*)f, pf,
                                                                 (const T*)kh, pk, n, (T)bA, (T)bB, stop, bi);
   return cudaGetLastError();
 }
@@ -349,7 +351,7 @@ cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, in
   }
   constexpr int W = TileShape<T>::W, HH = TileShape<T>::H;
   dim3 grid((n + W) / W, (n + HH) / HH, bi.count);
-  prolong_smooth_kernel<T, F2, O2><<<grid, dim3(TXN, TYN), sm, s>>>((O2*)out, po, (const c2<T>*)upre, pu,
+  pdl_launch(prolong_smooth_kernel<T, F2, O2>, grid, dim3(TXN, TYN), sm, s, (O2*)out, po, (const c2<T>*)upre, pu,
                                                                     (const c2<T>*)ec, pc, (const F2*)f, pf,
                                                                     (const T*)kh, pk, n, (T)bA, stop, bi);
   return cudaGetLastError();

@@ -10,6 +10,25 @@
 
 namespace hz {
 
+// Launches `kernel` with programmatic stream serialization: it may begin launching while the
+// previous kernel in the stream (or captured graph) is still running, and waits for it inside
+// (every kernel of the library starts with pdl_enter()).
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // Instances of one launch (multi right-hand-side batches): blockIdx.z selects the instance and
 // every per-instance array advances by its stride in elements. su: the level's own arrays (u, u2,
 // and f below the finest grid); sf: the right-hand side f; sc: the coarse level's arrays (fc,

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
                                                              int pc, const c2<T>* __restrict__ f, int pf,
                                                              const T* __restrict__ kh, int pk, int n, T bA, T bB,
                                                              int nu, const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   fc += blockIdx.z * bi.sc;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
                                                               const c2<T>* __restrict__ f, int pf,
                                                               const T* __restrict__ kh, int pk, int n, T bA, int nu,
                                                               const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   ec += blockIdx.z * bi.sc;
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
                                                               const F2* __restrict__ f, int pf,
                                                               const T* __restrict__ kh, int pk, int n, T bA, int post,
                                                               const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   uout += blockIdx.z * bi.su;
   if (uin) uin += blockIdx.z * bi.su;
@@ -229,12 +232,12 @@ cudaError_t launch_kacz_level_pre(bool fp32, void* u, int pu, void* fc, int pc, 
   cudaError_t e;
   if (fp32) {
     if ((e = set_level_attr<float>())) return e;
-    kacz_level_pre_kernel<float><<<dim3(1, 1, bi.count), LB, level_smem<float>(n), s>>>((float2*)u, pu, (float2*)fc, pc, (const float2*)f,
+    pdl_launch(kacz_level_pre_kernel<float>, dim3(1, 1, bi.count), LB, level_smem<float>(n), s, (float2*)u, pu, (float2*)fc, pc, (const float2*)f,
                                                                      pf, (const float*)kh, pk, n, (float)bA, (float)bB,
                                                                      nu, stop, bi);
   } else {
     if ((e = set_level_attr<double>())) return e;
-    kacz_level_pre_kernel<double><<<dim3(1, 1, bi.count), LB, level_smem<double>(n), s>>>((double2*)u, pu, (double2*)fc, pc,
+    pdl_launch(kacz_level_pre_kernel<double>, dim3(1, 1, bi.count), LB, level_smem<double>(n), s, (double2*)u, pu, (double2*)fc, pc,
                                                                        (const double2*)f, pf, (const double*)kh, pk, n,
                                                                        bA, bB, nu, stop, bi);
   }
@@ -247,12 +250,12 @@ cudaError_t launch_kacz_level_post(bool fp32, void* u, int pu, const void* ec, i
   cudaError_t e;
   if (fp32) {
     if ((e = set_level_attr<float>())) return e;
-    kacz_level_post_kernel<float><<<dim3(1, 1, bi.count), LB, level_smem<float>(n), s>>>((float2*)u, pu, (const float2*)ec, pc,
+    pdl_launch(kacz_level_post_kernel<float>, dim3(1, 1, bi.count), LB, level_smem<float>(n), s, (float2*)u, pu, (const float2*)ec, pc,
                                                                       (const float2*)f, pf, (const float*)kh, pk, n,
                                                                       (float)bA, nu, stop, bi);
   } else {
     if ((e = set_level_attr<double>())) return e;
-    kacz_level_post_kernel<double><<<dim3(1, 1, bi.count), LB, level_smem<double>(n), s>>>((double2*)u, pu, (const double2*)ec, pc,
+    pdl_launch(kacz_level_post_kernel<double>, dim3(1, 1, bi.count), LB, level_smem<double>(n), s, (double2*)u, pu, (const double2*)ec, pc,
                                                                         (const double2*)f, pf, (const double*)kh, pk, n,
                                                                         bA, nu, stop, bi);
   }
@@ -283,15 +286,15 @@ cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* ui
     return e;
   }
   if (!fp32)
-    kacz_sweep_tile_kernel<double, double2><<<grid, TB, sm64, s>>>((double2*)uout, po, (const double2*)uin, pu,
+    pdl_launch(kacz_sweep_tile_kernel<double, double2>, grid, TB, sm64, s, (double2*)uout, po, (const double2*)uin, pu,
                                                                 (const double2*)f, pf, (const double*)kh, pk, n, bA,
                                                                 post, stop, bi);
   else if (f64_src)
-    kacz_sweep_tile_kernel<float, double2><<<grid, TB, sm32, s>>>((float2*)uout, po, (const float2*)uin, pu,
+    pdl_launch(kacz_sweep_tile_kernel<float, double2>, grid, TB, sm32, s, (float2*)uout, po, (const float2*)uin, pu,
                                                                (const double2*)f, pf, (const float*)kh, pk, n,
                                                                (float)bA, post, stop, bi);
   else
-    kacz_sweep_tile_kernel<float, float2><<<grid, TB, sm32, s>>>((float2*)uout, po, (const float2*)uin, pu,
+    pdl_launch(kacz_sweep_tile_kernel<float, float2>, grid, TB, sm32, s, (float2*)uout, po, (const float2*)uin, pu,
                                                               (const float2*)f, pf, (const float*)kh, pk, n, (float)bA,
                                                               post, stop, bi);
   return cudaGetLastError();

@@ -171,6 +171,7 @@ __host__ __device__ __forceinline__ KrylovVecs offset_instance(KrylovVecs k, lon
 __device__ __forceinline__ KrylovVecs instance(const KrylovVecs& k) { return offset_instance(k, blockIdx.z); }
 
 __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long seed) {
+  pdl_enter();
   // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c + 1 of the generator
   // started from `seed`, top 53 bits mapped to [0, 1); r^_p = (u_2p - 1/2) + i (u_2p+1 - 1/2).
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
@@ -189,6 +190,7 @@ __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long see
 
 // x = 0, r = h^2 b, p = v = 0; |r|^2 and <r^, r> start the iteration.
 __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap) {
+  pdl_enter();
   k = instance(k);
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
@@ -232,6 +234,7 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
 
 // p = r (first step after a start or restart) or p = r + beta (p - omega v).
 __global__ void k_update_p_kernel(KrylovVecs k) {
+  pdl_enter();
   k = instance(k);
   KState* st = k.st;
   if (st->done) return;
@@ -259,6 +262,7 @@ __global__ void k_update_p_kernel(KrylovVecs k) {
 // v = A y with <r^, v>; alpha = rho / <r^, v>.
 template <class Y2>
 __global__ void k_apply_rv_kernel(KrylovVecs k, const Y2* __restrict__ y) {
+  pdl_enter();
   k = instance(k);
   y += blockIdx.z * k.sv;
   KState* st = k.st;
@@ -291,6 +295,7 @@ __global__ void k_apply_rv_kernel(KrylovVecs k, const Y2* __restrict__ y) {
 
 // s = r - alpha v with |s|^2; stop after the half step when |s| <= tol |b|.
 __global__ void k_update_s_kernel(KrylovVecs k) {
+  pdl_enter();
   k = instance(k);
   KState* st = k.st;
   if (st->done) return;
@@ -321,6 +326,7 @@ __global__ void k_update_s_kernel(KrylovVecs k) {
 // After a half-step stop: x += alpha y, once.
 template <class Y2>
 __global__ void k_x_half_kernel(KrylovVecs k, const Y2* __restrict__ y) {
+  pdl_enter();
   k = instance(k);
   y += blockIdx.z * k.sv;
   KState* st = k.st;
@@ -342,6 +348,7 @@ __global__ void k_x_half_kernel(KrylovVecs k, const Y2* __restrict__ y) {
 // t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>.
 template <class Y2>
 __global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ z) {
+  pdl_enter();
   k = instance(k);
   z += blockIdx.z * k.sv;
   KState* st = k.st;
@@ -376,6 +383,7 @@ __global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ z) {
 // x += alpha y + omega z, r = s - omega t, with <r^, r> and |r|^2; the next beta.
 template <class Y2>
 __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const Y2* __restrict__ z) {
+  pdl_enter();
   k = instance(k);
   y += blockIdx.z * k.sv;
   z += blockIdx.z * k.sv;
@@ -424,6 +432,7 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
 
 // tr = h^2 b - A x and |tr|^2, to confirm a recurrence-converged iterate.
 __global__ void k_true_residual_kernel(KrylovVecs k) {
+  pdl_enter();
   k = instance(k);
   KState* st = k.st;
   double acc[1] = {0.0};
@@ -443,6 +452,7 @@ __global__ void k_true_residual_kernel(KrylovVecs k) {
 
 // Restart from the true residual: r = tr, rho = <r^, r>, next step p = r.
 __global__ void k_restart_kernel(KrylovVecs k) {
+  pdl_enter();
   k = instance(k);
   KState* st = k.st;
   double acc[3] = {0.0, 0.0, 0.0};
@@ -473,6 +483,7 @@ __global__ void k_restart_kernel(KrylovVecs k) {
 
 __global__ void apply_fp64_kernel(double2* v, const double2* u, const double* kh, int n, double beta,
                                   double out_scale) {
+  pdl_enter();
   const int N = (n + 1) * (n + 1);
   for (NodeWalk it(n, gridDim.x * KB); it.e < N; it.next()) {
     const int e = it.e;
@@ -484,7 +495,7 @@ __global__ void apply_fp64_kernel(double2* v, const double2* u, const double* kh
 }  // namespace
 
 #define KGRID dim3(k.G, 1, k.batch)
-#define KLAUNCH(name) name<<<KGRID, KB, 0, s>>>(k); return cudaGetLastError();
+#define KLAUNCH(name) pdl_launch(name, KGRID, KB, 0, s, k); return cudaGetLastError();
 
 KrylovVecs instance_of(const KrylovVecs& k, int b) {
   KrylovVecs r = offset_instance(k, b);
@@ -493,33 +504,33 @@ KrylovVecs instance_of(const KrylovVecs& k, int b) {
 }
 
 cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s) {
-  shadow_kernel<<<1024, 256, 0, s>>>(rhat, N, seed);
+  pdl_launch(shadow_kernel, 1024, 256, 0, s, rhat, N, seed);
   return cudaGetLastError();
 }
 cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s) {
-  k_init_kernel<<<KGRID, KB, 0, s>>>(k, tol, maxit, hist_cap);
+  pdl_launch(k_init_kernel, KGRID, KB, 0, s, k, tol, maxit, hist_cap);
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_p_kernel) }
 cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) {
-  if (k.y32) k_apply_rv_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32);
-  else k_apply_rv_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y);
+  if (k.y32) pdl_launch(k_apply_rv_kernel<float2>, KGRID, KB, 0, s, k, k.y32);
+  else pdl_launch(k_apply_rv_kernel<double2>, KGRID, KB, 0, s, k, k.y);
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_s_kernel) }
 cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s) {
-  if (k.y32) k_x_half_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32);
-  else k_x_half_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y);
+  if (k.y32) pdl_launch(k_x_half_kernel<float2>, KGRID, KB, 0, s, k, k.y32);
+  else pdl_launch(k_x_half_kernel<double2>, KGRID, KB, 0, s, k, k.y);
   return cudaGetLastError();
 }
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) {
-  if (k.z32) k_apply_ts_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.z32);
-  else k_apply_ts_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.z);
+  if (k.z32) pdl_launch(k_apply_ts_kernel<float2>, KGRID, KB, 0, s, k, k.z32);
+  else pdl_launch(k_apply_ts_kernel<double2>, KGRID, KB, 0, s, k, k.z);
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) {
-  if (k.y32) k_update_xr_kernel<float2><<<KGRID, KB, 0, s>>>(k, k.y32, k.z32);
-  else k_update_xr_kernel<double2><<<KGRID, KB, 0, s>>>(k, k.y, k.z);
+  if (k.y32) pdl_launch(k_update_xr_kernel<float2>, KGRID, KB, 0, s, k, k.y32, k.z32);
+  else pdl_launch(k_update_xr_kernel<double2>, KGRID, KB, 0, s, k, k.y, k.z);
   return cudaGetLastError();
 }
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_true_residual_kernel) }
@@ -530,7 +541,7 @@ cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, in
   long long N = (long long)(n + 1) * (n + 1);
   int G = (int)((N + KB - 1) / KB);
   if (G > 4096) G = 4096;
-  apply_fp64_kernel<<<G, KB, 0, s>>>(v, u, kh, n, beta, out_scale);
+  pdl_launch(apply_fp64_kernel, G, KB, 0, s, v, u, kh, n, beta, out_scale);
   return cudaGetLastError();
 }
 

@@ -252,6 +252,7 @@ __device__ __forceinline__ void sr_run(unsigned char* ring, const SRArgs& A, int
 template <bool VF>
 __global__ void __launch_bounds__(32 * WPB) smooth_restrict_stream_kernel(SRArgs A, int strips, int seg_rows,
                                                                            const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   const int strip = blockIdx.x * WPB + threadIdx.y;
   if (strip >= strips) return;  // whole warp
@@ -400,6 +401,7 @@ __device__ __forceinline__ void ps_run(unsigned char* ring, const PSArgs& A, int
 template <bool V>
 __global__ void __launch_bounds__(32 * WPB) prolong_smooth_stream_kernel(PSArgs A, int strips, int seg_rows,
                                                                           const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   const int strip = blockIdx.x * WPB + threadIdx.y;
   if (strip >= strips) return;
@@ -436,9 +438,9 @@ cudaError_t launch_smooth_restrict_stream(void* u, int pu, void* fc, int pc, con
   dim3 grid((strips + WPB - 1) / WPB, segs, bi.count);
   constexpr size_t sm = (size_t)WPB * SR_R * SR_SLOT;
   if (aligned16(f, pf, bi.sf))
-    smooth_restrict_stream_kernel<true><<<grid, dim3(32, WPB), sm, s>>>(A, strips, seg_rows, stop, bi);
+    pdl_launch(smooth_restrict_stream_kernel<true>, grid, dim3(32, WPB), sm, s, A, strips, seg_rows, stop, bi);
   else
-    smooth_restrict_stream_kernel<false><<<grid, dim3(32, WPB), sm, s>>>(A, strips, seg_rows, stop, bi);
+    pdl_launch(smooth_restrict_stream_kernel<false>, grid, dim3(32, WPB), sm, s, A, strips, seg_rows, stop, bi);
   return cudaGetLastError();
 }
 
@@ -453,9 +455,9 @@ cudaError_t launch_prolong_smooth_stream(void* out, int po, const void* upre, in
   dim3 grid((strips + WPB - 1) / WPB, segs, bi.count);
   constexpr size_t sm = (size_t)WPB * PS_R * PS_SLOT;
   if (aligned16(f, pf, bi.sf) && aligned16(out, po, bi.so))
-    prolong_smooth_stream_kernel<true><<<grid, dim3(32, WPB), sm, s>>>(A, strips, seg_rows, stop, bi);
+    pdl_launch(prolong_smooth_stream_kernel<true>, grid, dim3(32, WPB), sm, s, A, strips, seg_rows, stop, bi);
   else
-    prolong_smooth_stream_kernel<false><<<grid, dim3(32, WPB), sm, s>>>(A, strips, seg_rows, stop, bi);
+    pdl_launch(prolong_smooth_stream_kernel<false>, grid, dim3(32, WPB), sm, s, A, strips, seg_rows, stop, bi);
   return cudaGetLastError();
 }
 

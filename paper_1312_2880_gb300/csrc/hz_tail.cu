@@ -22,6 +22,7 @@ constexpr int TAIL_THREADS = 1024;
 
 template <class T>
 __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const c2<T>* fin = reinterpret_cast<const c2<T>*>(A.f_in) + blockIdx.z * bi.sf;
@@ -130,9 +131,9 @@ cudaError_t launch_tail(bool fp32, const TailArgs& A, size_t smem, const int* st
   }
   dim3 grid(1, 1, bi.count);
   if (fp32)
-    tail_kernel<float><<<grid, TAIL_THREADS, smem, s>>>(A, stop, bi);
+    pdl_launch(tail_kernel<float>, grid, TAIL_THREADS, smem, s, A, stop, bi);
   else
-    tail_kernel<double><<<grid, TAIL_THREADS, smem, s>>>(A, stop, bi);
+    pdl_launch(tail_kernel<double>, grid, TAIL_THREADS, smem, s, A, stop, bi);
   return cudaGetLastError();
 }
 

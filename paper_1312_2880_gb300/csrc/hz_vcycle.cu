@@ -28,6 +28,7 @@ template <class T, class F2>
 __global__ void gs_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                  const T* __restrict__ kh, int pk, int n, int colour, T beta,
                                  const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   f += blockIdx.z * bi.sf;
@@ -50,6 +51,7 @@ template <class T, class F2>
 __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                 const T* __restrict__ kh, int pk, int n, int colour, T beta,
                                 const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   f += blockIdx.z * bi.sf;
@@ -74,6 +76,7 @@ template <class T, class F2>
 __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                    const T* __restrict__ kh, int pk, int n, int colour, T beta,
                                    const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   f += blockIdx.z * bi.sf;
@@ -109,6 +112,7 @@ template <class T, class F2>
 __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c2<T>* __restrict__ u, int pu,
                                          const F2* __restrict__ f, int pf, const T* __restrict__ kh, int pk, int n,
                                          T beta, const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   fc += blockIdx.z * bi.sc;
   u += blockIdx.z * bi.su;
@@ -141,6 +145,7 @@ __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c
 template <class T>
 __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* __restrict__ ec, int pc, int n,
                                    const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   ec += blockIdx.z * bi.sc;
@@ -165,6 +170,7 @@ __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* _
 template <class T>
 __global__ void coarse_solve_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* __restrict__ f, int pf,
                                     const c2<T>* __restrict__ ainvT, int nc, const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   u += blockIdx.z * bi.su;
   f += blockIdx.z * bi.su;
@@ -182,6 +188,7 @@ __global__ void coarse_solve_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* 
 template <class T>
 __global__ void coarse_setup_kernel(c2<T>* __restrict__ ainvT, double2* __restrict__ work, const T* __restrict__ kh,
                                     int pk, int nc, double beta, int* __restrict__ status) {
+  pdl_enter();
   int w = nc + 1, m = w * w;
   double2* A = work;
   double2* B = work + (long long)m * m;
@@ -279,6 +286,7 @@ __global__ void coarse_setup_kernel(c2<T>* __restrict__ ainvT, double2* __restri
 template <class T>
 __global__ void import_kernel(c2<T>* __restrict__ dst, int pd, const double2* __restrict__ src, int ps, int n,
                               double scale) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -289,6 +297,7 @@ __global__ void import_kernel(c2<T>* __restrict__ dst, int pd, const double2* __
 template <class T>
 __global__ void export_kernel(double2* __restrict__ dst, int pd, const c2<T>* __restrict__ src, int ps, int n,
                               double scale, const int* __restrict__ stop) {
+  pdl_enter();
   if (stop && *stop) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -300,6 +309,7 @@ __global__ void export_kernel(double2* __restrict__ dst, int pd, const c2<T>* __
 template <class T>
 __global__ void inject_kh_kernel(T* __restrict__ kh, int pk, const double* __restrict__ k0, int n0, int stride,
                                  int nl, double H) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I > nl || J > nl) return;
@@ -311,7 +321,7 @@ cudaError_t gs_colour_t(void* u, int pu, const void* f, int pf, const void* kh, 
                         const int* stop, cudaStream_t s, const Inst& bi) {
   dim3 g = grid2((n + 2) / 2, n + 1);
   g.z = bi.count;
-  gs_colour_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+  pdl_launch(gs_colour_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
                                                      (T)beta, stop, bi);
   return cudaGetLastError();
 }
@@ -320,7 +330,7 @@ cudaError_t gs_first_t(void* u, int pu, const void* f, int pf, const void* kh, i
                        const int* stop, cudaStream_t s, const Inst& bi) {
   dim3 g = grid2(n + 1, n + 1);
   g.z = bi.count;
-  gs_first_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+  pdl_launch(gs_first_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
                                                     (T)beta, stop, bi);
   return cudaGetLastError();
 }
@@ -329,7 +339,7 @@ cudaError_t kacz_colour_t(void* u, int pu, const void* f, int pf, const void* kh
                           double beta, const int* stop, cudaStream_t s, const Inst& bi) {
   dim3 g = grid2((n + 5) / 5, n + 1);
   g.z = bi.count;
-  kacz_colour_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
+  pdl_launch(kacz_colour_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
                                                        (T)beta, stop, bi);
   return cudaGetLastError();
 }
@@ -338,7 +348,7 @@ cudaError_t restrict_t(void* fc, int pc, const void* u, int pu, const void* f, i
                        double beta, const int* stop, cudaStream_t s, const Inst& bi) {
   dim3 g = grid2(n / 2 + 1, n / 2 + 1);
   g.z = bi.count;
-  restrict_residual_kernel<T, F2><<<g, dim3(BX, BY), 0, s>>>((c2<T>*)fc, pc, (const c2<T>*)u, pu, (const F2*)f, pf,
+  pdl_launch(restrict_residual_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)fc, pc, (const c2<T>*)u, pu, (const F2*)f, pf,
                                                              (const T*)kh, pk, n, (T)beta, stop, bi);
   return cudaGetLastError();
 }
@@ -379,9 +389,9 @@ cudaError_t launch_prolong_add(bool fp32, void* u, int pu, const void* ec, int p
   dim3 g = grid2(n + 1, n + 1);
   g.z = bi.count;
   if (fp32)
-    prolong_add_kernel<float><<<g, dim3(BX, BY), 0, s>>>((float2*)u, pu, (const float2*)ec, pc, n, stop, bi);
+    pdl_launch(prolong_add_kernel<float>, g, dim3(BX, BY), 0, s, (float2*)u, pu, (const float2*)ec, pc, n, stop, bi);
   else
-    prolong_add_kernel<double><<<g, dim3(BX, BY), 0, s>>>((double2*)u, pu, (const double2*)ec, pc, n, stop, bi);
+    pdl_launch(prolong_add_kernel<double>, g, dim3(BX, BY), 0, s, (double2*)u, pu, (const double2*)ec, pc, n, stop, bi);
   return cudaGetLastError();
 }
 
@@ -391,10 +401,10 @@ cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int p
   int threads = m < 256 ? ((m + 31) / 32) * 32 : 256;
   dim3 g(1, 1, bi.count);
   if (fp32)
-    coarse_solve_kernel<float><<<g, threads, m * sizeof(float2), s>>>((float2*)u, pu, (const float2*)f, pf,
+    pdl_launch(coarse_solve_kernel<float>, g, threads, m * sizeof(float2), s, (float2*)u, pu, (const float2*)f, pf,
                                                                        (const float2*)ainvT, nc, stop, bi);
   else
-    coarse_solve_kernel<double><<<g, threads, m * sizeof(double2), s>>>((double2*)u, pu, (const double2*)f, pf,
+    pdl_launch(coarse_solve_kernel<double>, g, threads, m * sizeof(double2), s, (double2*)u, pu, (const double2*)f, pf,
                                                                          (const double2*)ainvT, nc, stop, bi);
   return cudaGetLastError();
 }
@@ -402,18 +412,18 @@ cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int p
 cudaError_t launch_import(bool fp32, void* dst, int pd, const double2* src, int ps, int n, double scale,
                           cudaStream_t s) {
   if (fp32)
-    import_kernel<float><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>((float2*)dst, pd, src, ps, n, scale);
+    pdl_launch(import_kernel<float>, grid2(n + 1, n + 1), dim3(BX, BY), 0, s, (float2*)dst, pd, src, ps, n, scale);
   else
-    import_kernel<double><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>((double2*)dst, pd, src, ps, n, scale);
+    pdl_launch(import_kernel<double>, grid2(n + 1, n + 1), dim3(BX, BY), 0, s, (double2*)dst, pd, src, ps, n, scale);
   return cudaGetLastError();
 }
 
 cudaError_t launch_export(bool fp32, double2* dst, int pd, const void* src, int ps, int n, double scale,
                           const int* stop, cudaStream_t s) {
   if (fp32)
-    export_kernel<float><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>(dst, pd, (const float2*)src, ps, n, scale, stop);
+    pdl_launch(export_kernel<float>, grid2(n + 1, n + 1), dim3(BX, BY), 0, s, dst, pd, (const float2*)src, ps, n, scale, stop);
   else
-    export_kernel<double><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>(dst, pd, (const double2*)src, ps, n, scale,
+    pdl_launch(export_kernel<double>, grid2(n + 1, n + 1), dim3(BX, BY), 0, s, dst, pd, (const double2*)src, ps, n, scale,
                                                                        stop);
   return cudaGetLastError();
 }
@@ -421,9 +431,9 @@ cudaError_t launch_export(bool fp32, double2* dst, int pd, const void* src, int 
 cudaError_t launch_inject_kh(bool fp32, void* kh, int pk, const double* k0, int n0, int stride, int nl, double H,
                              cudaStream_t s) {
   if (fp32)
-    inject_kh_kernel<float><<<grid2(nl + 1, nl + 1), dim3(BX, BY), 0, s>>>((float*)kh, pk, k0, n0, stride, nl, H);
+    pdl_launch(inject_kh_kernel<float>, grid2(nl + 1, nl + 1), dim3(BX, BY), 0, s, (float*)kh, pk, k0, n0, stride, nl, H);
   else
-    inject_kh_kernel<double><<<grid2(nl + 1, nl + 1), dim3(BX, BY), 0, s>>>((double*)kh, pk, k0, n0, stride, nl, H);
+    pdl_launch(inject_kh_kernel<double>, grid2(nl + 1, nl + 1), dim3(BX, BY), 0, s, (double*)kh, pk, k0, n0, stride, nl, H);
   return cudaGetLastError();
 }
 
@@ -431,9 +441,9 @@ cudaError_t launch_coarse_setup(bool fp32, void* ainvT, double2* work, const voi
                                 int* status, cudaStream_t s) {
   if ((nc + 1) * (nc + 1) > 1089) return cudaErrorInvalidValue;
   if (fp32)
-    coarse_setup_kernel<float><<<1, 1024, 0, s>>>((float2*)ainvT, work, (const float*)kh, pk, nc, beta, status);
+    pdl_launch(coarse_setup_kernel<float>, 1, 1024, 0, s, (float2*)ainvT, work, (const float*)kh, pk, nc, beta, status);
   else
-    coarse_setup_kernel<double><<<1, 1024, 0, s>>>((double2*)ainvT, work, (const double*)kh, pk, nc, beta, status);
+    pdl_launch(coarse_setup_kernel<double>, 1, 1024, 0, s, (double2*)ainvT, work, (const double*)kh, pk, nc, beta, status);
   return cudaGetLastError();
 }
 
