@@ -481,7 +481,7 @@ def run_ours(args):
         "kernel_share": shares(per_small),
         "gpu_launches": gpu_launches,
         "tile_autotuner": {wl.name: results["fp32"]["forms"], rw.name: roof_forms,
-                           "forms": "0 = shared-memory tiles; v = 1..5: register streaming, 2^(v+3) rows per warp"},
+                           "forms": "0 = shared-memory tiles; v = 1..6: register streaming, 2^(v+2) rows per warp"},
         "clocks": results["fp32"]["clocks"],
         "clocks_fp64_form": results["fp64"]["clocks"],
     }
@@ -569,7 +569,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=15.0)
     ap.add_argument("--profile-precision", default="fp32")
     ap.add_argument("--pass-variant", type=int, default=-1,
-                    help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..5: streaming)")
+                    help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..6: streaming)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

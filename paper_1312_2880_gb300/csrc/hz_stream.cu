@@ -113,6 +113,17 @@ __device__ __forceinline__ void store_pair(float2* __restrict__ row, int c0, int
   }
 }
 
+// Four-row window after two stages: slot k takes the row of slot k + 2 (mod 4), so the stage code
+// written for slots 0 and 1 serves every pair of rows.
+template <class X>
+__device__ __forceinline__ void rotate2(X (&w)[4]) {
+  const X a = w[0], b = w[1];
+  w[0] = w[2];
+  w[1] = w[3];
+  w[2] = a;
+  w[3] = b;
+}
+
 struct Lane {  // per-lane constants of a strip
   int c0, m0, m1;
   float sc0, sc1;  // twice the boundary sides of the two columns
@@ -240,11 +251,15 @@ __device__ __forceinline__ void sr_run(unsigned char* ring, const SRArgs& A, int
   for (int k = 0; k < 4; ++k) S.U[k].a = S.U[k].b = make_float2(0.f, 0.f);
   S.hS = S.hC = make_float2(0.f, 0.f);
   for (int t = 0; t < SR_R - 1; ++t) sr_issue<EDGE, VF>(ring, A, t, T, y0, q);
-  for (int t0 = 0; t0 < T; t0 += 4) {
+  // two stages of code per iteration (a small loop body keeps the instruction cache warm when
+  // few warps run); the four-row windows rotate by two rows between iterations
+#pragma unroll 1
+  for (int t0 = 0; t0 < T; t0 += 2) {
     sr_stage<0, EDGE, VF>(S, ring, A, t0 + 0, T, y0, row_end, gx, q);
     sr_stage<1, EDGE, VF>(S, ring, A, t0 + 1, T, y0, row_end, gx, q);
-    sr_stage<2, EDGE, VF>(S, ring, A, t0 + 2, T, y0, row_end, gx, q);
-    sr_stage<3, EDGE, VF>(S, ring, A, t0 + 3, T, y0, row_end, gx, q);
+    rotate2(S.U);
+    rotate2(S.F);
+    rotate2(S.K);
   }
   cp_wait<0>();
 }
@@ -389,11 +404,13 @@ __device__ __forceinline__ void ps_run(unsigned char* ring, const PSArgs& A, int
   for (int k = 0; k < 4; ++k) S.U[k].a = S.U[k].b = make_float2(0.f, 0.f);
   S.Ee = make_float2(0.f, 0.f);
   for (int t = 0; t < PS_R - 1; ++t) ps_issue<EDGE, V>(ring, A, t, T, y0, q, ci);
-  for (int t0 = 0; t0 < T; t0 += 4) {
+#pragma unroll 1
+  for (int t0 = 0; t0 < T; t0 += 2) {
     ps_stage<0, EDGE, V>(S, ring, A, t0 + 0, T, y0, row_end, gx, q, ci);
     ps_stage<1, EDGE, V>(S, ring, A, t0 + 1, T, y0, row_end, gx, q, ci);
-    ps_stage<2, EDGE, V>(S, ring, A, t0 + 2, T, y0, row_end, gx, q, ci);
-    ps_stage<3, EDGE, V>(S, ring, A, t0 + 3, T, y0, row_end, gx, q, ci);
+    rotate2(S.U);
+    rotate2(S.F);
+    rotate2(S.K);
   }
   cp_wait<0>();
 }

@@ -122,7 +122,7 @@ def _ptr(t) -> c_void_p:
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
               pass_variant=-1, coarse_tail=True) -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
-    memory tiles; 1..5 = register streaming with 2**(v+3) rows per warp (FP32 form)."""
+    memory tiles; 1..6 = register streaming with 2**(v+2) rows per warp (FP32 form)."""
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]

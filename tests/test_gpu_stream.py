@@ -1,5 +1,5 @@
 """Kernel forms of the fused Gauss-Seidel passes (FP32 form): shared-memory tiles (form 0) and
-register streaming with 16 .. 256 rows per warp (forms 1..5), and the tile autotuner that picks one
+register streaming with 8 .. 256 rows per warp (forms 1..6), and the tile autotuner that picks one
 per level.
 
 Every form takes the same fixed-rounding operations in the same order on every node, so the
@@ -76,7 +76,7 @@ def test_forms_are_bitwise_identical(name):
     fused = [l for l, d in enumerate(sched0) if d["pass_down"] >= 0]
     assert fused, "no fused level in this hierarchy"
     assert all(sched0[l]["pass_down"] == 0 and sched0[l]["pass_up"] == 0 for l in fused)
-    for form in range(1, 6):
+    for form in range(1, 7):
         z, sched = vcycle(wl, form, r)
         for l in fused:
             want = form if sched[l]["n"] >= 4 else 0
@@ -90,7 +90,7 @@ def test_streaming_form_matches_oracle(name):
     H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
     r = rand_c((wl.n + 1) ** 2, 92)
     ref = o.vcycle(H, r.ravel())
-    for form in (1, 3, 5):
+    for form in (1, 3, 6):
         z, _ = vcycle(wl, form, r)
         err = np.abs(z.ravel() - ref).max() / np.abs(ref).max()
         assert err <= 2e-5, (form, err)
@@ -103,7 +103,7 @@ def test_autotuned_forms_are_valid_and_bitwise_equal():
     z, sched = vcycle(wl, -1, r)
     for d in sched:
         if d["pass_down"] >= 0:
-            assert 0 <= d["pass_down"] <= 5 and 0 <= d["pass_up"] <= 5
+            assert 0 <= d["pass_down"] <= 6 and 0 <= d["pass_up"] <= 6
     assert np.array_equal(z.view(np.uint64), z0.view(np.uint64))
 
 
