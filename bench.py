@@ -329,6 +329,38 @@ def cpu_baseline(wl, iters_full: float, sample_iters: int):
                       f"numpy/scipy, one thread), scaled by the {iters_full:g} iterations of the FP64 form"}
 
 
+def oracle_errors(wl, xs: dict, tol: float):
+    """max |x - x_oracle| / max |x_oracle| of each form's solution against the FP64 oracle's own
+    solve of the same system to the same tolerance (both stop at relres tol, so the difference is
+    of the order tol times the conditioning, not rounding)."""
+    import oracle as o
+
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    ref = o.bicgstab(A, wl.rhs.ravel(), lambda v: o.vcycle(H, v), tol=tol, maxit=5000)
+    scale = np.abs(ref.x).max()
+    out = {f"{p}_form": float(np.abs(x.ravel() - ref.x).max() / scale) for p, x in xs.items()}
+    out["oracle_iterations"] = ref.iterations
+    return out
+
+
+def small_case_errors(tol: float):
+    """The same comparison on the n = 64 plain workload (both forms)."""
+    import torch
+
+    from paper_1312_2880_gb300 import hz
+
+    wl = workload("plain64")
+    rhs = torch.from_numpy(wl.rhs).cuda()
+    xs = {}
+    for prec in ("fp32", "fp64"):
+        P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
+        x, _, _ = P.solve(rhs, tol=tol, maxit=5000)
+        xs[prec] = x.cpu().numpy()
+        P.close()
+    return oracle_errors(wl, xs, tol)
+
+
 def run_batched(precision: str, reps: int = 3):
     """Four constant-k problems (k, n) = (50, 96), (100, 192), (200, 384), (300, 576), 16 seeded
     point sources each, solved as one group (every right-hand side of every problem advances in
@@ -417,10 +449,10 @@ def run_ours(args):
         with ClockSampler(local) as clk:
             per, total, infos = time_solves(P, rhs, steps, warm, world, tol)
         ms = barrier_max(total / steps, world)
-        _, info_chk, _ = P.solve(rhs, tol=tol, maxit=5000)
+        x_chk, info_chk, _ = P.solve(rhs, tol=tol, maxit=5000)
         results[prec] = {"ms": ms, "per_step_ms": [round(x, 3) for x in per], "iterations": infos[-1]["iterations"],
                          "relres_true": infos[-1]["relres_true"], "clocks": clk.summary(), "P": P,
-                         "forms": pass_forms(P)}
+                         "forms": pass_forms(P), "x": x_chk.cpu().numpy()}
     P32 = results["fp32"]["P"]
     per_small = profile(P32, rhs, 2)
     launches_per_iter = sum(len(v) for k, v in per_small.items() if k[0] != "zero") // 2
@@ -487,6 +519,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, results["fp64"]["iterations"], args.cpu_sample_iters)
+        line["error_vs_oracle"] = {wl.name: oracle_errors(wl, {p: r["x"] for p, r in results.items()}, tol),
+                                   "plain_n64_k20": small_case_errors(tol)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

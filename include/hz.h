@@ -183,12 +183,14 @@ hz_status hz_solve_host(hz_problem* p, const double* rhs_host, double* x_host, d
                         double* history, int history_cap, hz_solve_info* info);
 
 /* ---- Non-blocking solve: one host thread can keep many problems' solves in flight (serving).
- * hz_solve_start validates, queues the start-up and the first iterations on the problem's stream
- * and returns; hz_solve_poll never waits: it reads the progress flags that have already landed,
- * queues further iterations, and sets *done = 1 once the solve has stopped (converged, broken
- * down, non-finite or maxit); hz_solve_finish waits for the end if needed and reports exactly as
+ * hz_solve_start validates, copies rhs into the problem's own buffer and queues the whole solve
+ * on the problem's stream (one graph launch whose iterations loop on the device, then the true
+ * residual) and returns; hz_solve_poll never waits: it checks whether that work has finished,
+ * queues a restart from the true residual when the recurrence converged without it, and sets
+ * *done = 1 once the solve has stopped (converged, broken down, non-finite or maxit);
+ * hz_solve_finish waits for the end if needed, copies the solution to x and reports exactly as
  * hz_solve does (status, history, info). x holds the result only after hz_solve_finish returns.
- * One solve per problem at a time (HZ_EINVAL otherwise); rhs and x must stay valid until
+ * One solve per problem at a time (HZ_EINVAL otherwise); x must stay valid until
  * hz_solve_finish. A CUDA error during polling ends the solve and is returned. */
 hz_status hz_solve_start(hz_problem* p, const double* rhs, double* x, double tol, int maxit);
 hz_status hz_solve_poll(hz_problem* p, int* done);
@@ -262,6 +264,15 @@ int hz_profile_iteration(hz_problem* p, const double* rhs, double* x, int iterat
  * the kernel's own, i.e. the kernel as it runs inside the solve's graph replay (back to back,
  * with the graph's launch gaps). Synchronises. */
 int hz_profile_graph(hz_problem* p, const double* rhs, double* x, int iterations, hz_kernel_time* out, int cap);
+
+/* Diagnostics: the Bi-CGSTAB scalars of one instance after the last solve, as 17 doubles:
+ * rho, alpha, omega, beta (complex, re/im pairs), |r|^2, |s|^2, |t|^2, |b|^2 (h^2-scaled), the
+ * iteration, the stop code (0 running, 1 converged, 2 breakdown, 3 non-finite, 4 maxit), the
+ * smallest |<r^, r>|^2 / (|r^|^2 |r|^2) seen, the number of near-breakdown restarts, and the
+ * smallest |omega|^2 |t|^2 / |r|^2 seen in iterations whose |<r^, r>|^2 / (|r^|^2 |r|^2) < 1e-12
+ * (a restart renews r^ when both ratios fall below 1e-12 and 1e-8).
+ * Returns 17, or -1 on error. Synchronises. */
+int hz_krylov_scalars(hz_problem* p, int instance, double* out);
 
 /* Name of an hz_kernel. */
 const char* hz_kernel_name(int kernel);

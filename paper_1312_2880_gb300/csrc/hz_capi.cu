@@ -23,8 +23,6 @@ constexpr int HIST_CAP = 32768;       // device history entries (two per iterati
 constexpr int MAX_COARSE_UNKNOWNS = 1089;
 constexpr int PARTIAL_SLOTS = 4;
 constexpr int MAX_G = 16384;
-constexpr unsigned long long SHADOW_SEED = 0x5EED1312ull;
-constexpr int PIPELINE = 3;  // iterations queued ahead of the convergence poll
 
 // Scale bins in c = k_ref H: geometric midpoints between the paper's scales 0.3125, 0.625, 1.25
 // and 2.5 (Sec. 4-5), and the guard band 1 < kH < 2 sqrt 2 for L relaxation.
@@ -121,7 +119,7 @@ bool make_plan(int n, const hz_hierarchy_opts& o, Plan* P, std::string* err) {
   P->off_kh64 = off;
   off = align256(off + N * 8);
   P->vec_bytes = align256(N * 16 * B);  // one slot: B consecutive vectors
-  P->rhat_bytes = align256(N * 16);      // the shadow residual is shared
+  P->rhat_bytes = P->vec_bytes;          // one shadow residual per instance (restarts renew it)
   P->off_vec = off;
   off += P->vec_bytes * (P->nvec - 1) + P->rhat_bytes;
   P->m_coarse = (nc + 1) * (nc + 1);
@@ -165,8 +163,6 @@ struct hz_problem {
   KrylovVecs kv{};
   double2* b_int = nullptr;  // host-buffer solve: rhs and x on the device
   double2* x_int = nullptr;
-  int* poll_host = nullptr;  // pinned: PIPELINE slots of 4 ints (it, first, done, half)
-  cudaEvent_t ev[PIPELINE]{};
   cudaGraphExec_t graph = nullptr;
   const double2* graph_b = nullptr;
   double2* graph_x = nullptr;
@@ -177,12 +173,12 @@ struct hz_problem {
   std::string err;
   // Solve in flight (see solve_begin/solve_advance/solve_end).
   struct Run {
-    enum Phase { IDLE = 0, RUNNING, FINAL_WAIT, DONE };
+    enum Phase { IDLE = 0, RUNNING, DONE };
     int phase = IDLE;
     double tol = 0;
     int maxit = 0;
-    long long launched = 0, polled = 0;
     int restarts = 0;
+    double* user_x = nullptr;  // where solve_end copies the solution
   } run;
   KState* kstate_host = nullptr;  // pinned copy of the device Krylov state at the end of a solve
   cudaEvent_t ev_final = nullptr;
@@ -496,20 +492,58 @@ cudaError_t enqueue_iteration(hz_problem* P) {
   return mark(P, launch_k_update_xr(k, s), HZ_K_UPDATE_XR, 0);
 }
 
+// The solve graph: the loop counter is zeroed, then a WHILE conditional node runs body() (one
+// Bi-CGSTAB iteration of every problem) followed by the loop control kernel for as long as that
+// kernel keeps the condition set. The whole iteration sequence of a solve is one graph launch.
+template <class Body>
+cudaError_t build_loop_graph(cudaStream_t s, LoopCtl ctl, Body body, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e) return e;
+  cudaGraphNode_t mset = nullptr, cond = nullptr;
+  cudaMemsetParams mp = {};
+  mp.dst = ctl.counter;
+  mp.value = 0;
+  mp.elementSize = sizeof(int);
+  mp.width = 1;
+  mp.height = 1;
+  mp.pitch = sizeof(int);
+  e = cudaGraphAddMemsetNode(&mset, g, nullptr, 0, &mp);
+  if (!e) e = cudaGraphConditionalHandleCreate(&ctl.handle, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = ctl.handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (!e) e = cudaGraphAddNode(&cond, g, &mset, nullptr, 1, &cp);
+  if (!e) e = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+  if (!e) {
+    cudaError_t eb = body();
+    if (!eb) eb = launch_loop_control(ctl, s);
+    cudaGraph_t captured = nullptr;  // the conditional node's own body graph
+    e = cudaStreamEndCapture(s, &captured);
+    if (eb) e = eb;
+  }
+  if (!e) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+int* loop_counter(hz_problem* P) { return P->status_dev + 16; }  // inside the 256-byte status block
+
 hz_status build_graph(hz_problem* P) {
   if (P->graph) {
     cudaGraphExecDestroy(P->graph);
     P->graph = nullptr;
   }
-  cudaGraph_t g = nullptr;
-  CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_iteration(P);
-  cudaError_t e2 = cudaStreamEndCapture(P->stream, &g);
-  if (e) return cuda_fail(P, e, "capture of one Bi-CGSTAB iteration");
-  if (e2) return cuda_fail(P, e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&P->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e) return cuda_fail(P, e, "cudaGraphInstantiate");
+  LoopCtl ctl{};
+  ctl.counter = loop_counter(P);
+  ctl.problems = 1;
+  ctl.st[0] = P->kv.st;
+  ctl.batch[0] = P->plan.batch;
+  cudaError_t e = build_loop_graph(P->stream, ctl, [&]() { return enqueue_iteration(P); }, &P->graph);
+  if (e) return cuda_fail(P, e, "building the solve graph");
   P->graph_b = P->kv.b;
   P->graph_x = P->kv.x;
   return HZ_OK;
@@ -518,21 +552,17 @@ hz_status build_graph(hz_problem* P) {
 // ------------------------------------------------------------------ resumable solve
 // A solve is a small state machine so that one host thread can drive many problems at once
 // (hz_solve_start / hz_solve_poll / hz_solve_finish); hz_solve runs the same machine blocking.
-// RUNNING keeps PIPELINE graph replays in flight and reads each one's 16-byte flag copy when its
-// event has completed; FINAL_WAIT waits for the true residual and the Krylov state.
+// RUNNING: the solve graph (all iterations, device-side loop), the true residual and a copy of
+// every instance's Krylov state are in flight behind ev_final; when they land, an instance whose
+// recurrence converged but whose true residual did not is restarted from it and the graph runs
+// again (at most 8 times); otherwise the solve is DONE.
 
-cudaError_t enqueue_replay(hz_problem* P) {
-  hz_problem::Run& R = P->run;
+cudaError_t launch_loop(hz_problem* P) {
   cudaStream_t s = P->stream;
   cudaError_t e = cudaGraphLaunch(P->graph, s);
-  int slot = (int)(R.launched % PIPELINE);
-  const int B = P->plan.batch;
-  // the 16-byte flag block (it, first, done, half) of every instance
-  if (!e)
-    e = cudaMemcpy2DAsync(P->poll_host + 4 * B * slot, 4 * sizeof(int), &P->kv.st->it, sizeof(KState), 4 * sizeof(int),
-                          B, cudaMemcpyDeviceToHost, s);
-  if (!e) e = cudaEventRecord(P->ev[slot], s);
-  if (!e) ++R.launched;
+  if (!e) e = launch_k_true_residual(P->kv, s);
+  if (!e) e = cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * P->plan.batch, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaEventRecord(P->ev_final, s);
   return e;
 }
 
@@ -542,8 +572,13 @@ hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, i
   if (!rhs || !x || !(tol > 0) || maxit < 1) return fail(P, HZ_EINVAL, "bad solve arguments");
   if ((const double*)rhs == x) return fail(P, HZ_EINVAL, "rhs and x may not alias");
   if (maxit > HIST_CAP / 2 - 1) maxit = HIST_CAP / 2 - 1;
-  P->kv.b = (const double2*)rhs;
-  P->kv.x = (double2*)x;
+  // The solve graph works on the problem's own rhs and x buffers, so it is built once per problem
+  // (an instantiation per caller buffer would cost more than the two copies).
+  const size_t bytes = sizeof(double2) * (size_t)P->kv.N * P->plan.batch;
+  if ((const double2*)rhs != P->b_int)
+    CK(cudaMemcpyAsync(P->b_int, rhs, bytes, cudaMemcpyDeviceToDevice, P->stream));
+  P->kv.b = P->b_int;
+  P->kv.x = P->x_int;
   if (!P->graph || P->graph_b != P->kv.b || P->graph_x != P->kv.x) {
     hz_status st = build_graph(P);
     if (st) return st;
@@ -552,13 +587,13 @@ hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, i
   R = hz_problem::Run();
   R.tol = tol;
   R.maxit = maxit;
+  R.user_x = x;
   CK(launch_k_init(P->kv, tol, maxit, HIST_CAP, P->stream));
+  CK(launch_loop(P));
   R.phase = hz_problem::Run::RUNNING;
-  while (R.launched < PIPELINE && R.launched < (long long)maxit + 2) CK(enqueue_replay(P));
   return HZ_OK;
 }
 
-// Advance the solve; with block = false return as soon as the next step would wait.
 hz_status solve_advance(hz_problem* P, bool block, int* done) {
   hz_problem::Run& R = P->run;
   cudaStream_t s = P->stream;
@@ -569,32 +604,6 @@ hz_status solve_advance(hz_problem* P, bool block, int* done) {
       *done = 1;
       return HZ_OK;
     }
-    if (R.phase == hz_problem::Run::RUNNING) {
-      int slot = (int)(R.polled % PIPELINE);
-      if (block) {
-        CK(cudaEventSynchronize(P->ev[slot]));
-      } else {
-        cudaError_t q = cudaEventQuery(P->ev[slot]);
-        if (q == cudaErrorNotReady) return HZ_OK;
-        if (q != cudaSuccess) return cuda_fail(P, q, "cudaEventQuery");
-      }
-      const int B = P->plan.batch;
-      const int* flags = P->poll_host + 4 * B * slot;  // per instance: it, first, done, half
-      ++R.polled;
-      bool all_done = true;
-      for (int b = 0; b < B; ++b) all_done = all_done && flags[4 * b + 2] != 0;
-      const long long cap = (long long)R.maxit + 2;
-      if (all_done || (R.polled >= R.launched && R.launched >= cap)) {
-        CK(launch_k_true_residual(P->kv, s));
-        CK(cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * B, cudaMemcpyDeviceToHost, s));
-        CK(cudaEventRecord(P->ev_final, s));
-        R.phase = hz_problem::Run::FINAL_WAIT;
-        continue;
-      }
-      if (R.launched < cap) CK(enqueue_replay(P));
-      continue;
-    }
-    // FINAL_WAIT
     if (block) {
       CK(cudaEventSynchronize(P->ev_final));
     } else {
@@ -614,9 +623,7 @@ hz_status solve_advance(hz_problem* P, bool block, int* done) {
     }
     if (restarted) {
       ++R.restarts;
-      R.launched = R.polled = 0;
-      R.phase = hz_problem::Run::RUNNING;
-      while (R.launched < PIPELINE && R.launched < (long long)R.maxit + 2) CK(enqueue_replay(P));
+      CK(launch_loop(P));
       continue;
     }
     R.phase = hz_problem::Run::DONE;
@@ -627,7 +634,7 @@ hz_status instance_status(const KState& hs, int maxit, double* iters) {
   *iters = hs.iters_x2 * 0.5;
   if (hs.done == 2) return HZ_EBREAKDOWN;
   if (hs.done == 3) return HZ_ENONFINITE;
-  if (hs.done == 4 || hs.done == 0) {
+  if (hs.done == 4 || hs.done == 0 || hs.done == 5) {
     *iters = (double)maxit;
     return HZ_EMAXIT;
   }
@@ -640,6 +647,9 @@ hz_status solve_end(hz_problem* P, double* history, int history_cap, hz_solve_in
   if (R.phase != hz_problem::Run::DONE) return fail(P, HZ_EINVAL, "the solve has not finished");
   R.phase = hz_problem::Run::IDLE;
   const int B = P->plan.batch;
+  if (R.user_x && R.user_x != (double*)P->x_int)
+    CK(cudaMemcpyAsync(R.user_x, P->x_int, sizeof(double2) * (size_t)P->kv.N * B, cudaMemcpyDeviceToDevice,
+                       P->stream));
   double iters0 = 0;
   const hz_status st = instance_status(P->kstate_host[0], R.maxit, &iters0);
   int hl = std::min(P->kstate_host[0].hist_len, HIST_CAP);
@@ -659,7 +669,7 @@ hz_status solve_end(hz_problem* P, double* history, int history_cap, hz_solve_in
       info[b].relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.trr / hs.bnorm2) : 0.0;
       info[b].history_len = b == 0 ? std::min(hl, history_cap > 0 ? history_cap : 0) : 0;
       info[b].status = sb;
-      info[b].restarts = R.restarts;
+      info[b].restarts = R.restarts + hs.shadow_restarts;
     }
   }
   const hz_status res = B == 1 ? st : worst;
@@ -944,8 +954,6 @@ size_t hz_footprint_bytes(int n, const hz_hierarchy_opts* opts) {
 
 static void release(hz_problem* P) {
   if (P->graph) { cudaGraphExecDestroy(P->graph); P->graph = nullptr; }
-  for (auto& e : P->ev) if (e) { cudaEventDestroy(e); e = nullptr; }
-  if (P->poll_host) { cudaFreeHost(P->poll_host); P->poll_host = nullptr; }
   if (P->ev_in) { cudaEventDestroy(P->ev_in); P->ev_in = nullptr; }
   if (P->ev_final) { cudaEventDestroy(P->ev_final); P->ev_final = nullptr; }
   if (P->kstate_host) { cudaFreeHost(P->kstate_host); P->kstate_host = nullptr; }
@@ -986,14 +994,12 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaMallocHost(&P->poll_host, sizeof(int) * 4 * PIPELINE * pl.batch));
   CK(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_final, cudaEventDisableTiming));
   CK(cudaMallocHost(&P->kstate_host, sizeof(KState) * pl.batch));
   StreamScope scope(P);
-  for (auto& e : P->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   unsigned char* A = P->arena;
   int n = P->n;
   bool fp32 = pl.fp32;
@@ -1046,7 +1052,7 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   k.G = (int)std::min<long long>(want, std::min(8LL * P->num_sms, (long long)MAX_G));
   if (k.G < 1) k.G = 1;
   CK(cudaMemsetAsync(k.st, 0, sizeof(KState) * pl.batch, s));
-  CK(launch_shadow(k.rhat, k.N, SHADOW_SEED, s));
+  for (int b = 0; b < pl.batch; ++b) CK(launch_shadow(k.rhat + b * k.sv, k.N, SHADOW_SEED, s));
   // Coarsest: dense inverse on the device.
   Level& C = P->lv.back();
   P->ainvT = A + pl.off_ainv;
@@ -1292,7 +1298,6 @@ int hz_profile_iteration(hz_problem* P, const double* rhs, double* x, int iterat
   }
   for (auto& r : recs) cudaEventDestroy(r.ev);
   cudaEventDestroy(start);
-  P->graph_b = nullptr;  // the captured graph still refers to the previous buffers only by value
   return count;
 }
 
@@ -1338,7 +1343,6 @@ int hz_profile_graph(hz_problem* P, const double* rhs, double* x, int iterations
   if (g) cudaGraphDestroy(g);
   for (auto& r : recs) cudaEventDestroy(r.ev);
   cudaEventDestroy(start);
-  P->graph_b = nullptr;
   return count;
 }
 
@@ -1349,21 +1353,15 @@ struct hz_group {
   cudaStream_t stream = nullptr;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
-  cudaEvent_t ev[PIPELINE]{};
-  int* flags = nullptr;  // pinned: PIPELINE slots x total instances x 4 ints
   int total = 0;
   cudaGraphExec_t graph = nullptr;
-  std::vector<const double*> graph_b;
-  std::vector<double*> graph_x;
   std::string err;
 };
 
 static void group_release(hz_group* g) {
   if (g->graph) cudaGraphExecDestroy(g->graph);
-  for (auto& e : g->ev) if (e) cudaEventDestroy(e);
   for (auto e : g->join) if (e) cudaEventDestroy(e);
   if (g->fork) cudaEventDestroy(g->fork);
-  if (g->flags) cudaFreeHost(g->flags);
   if (g->stream) cudaStreamDestroy(g->stream);
 }
 
@@ -1377,7 +1375,7 @@ static void group_release(hz_group* g) {
   } while (0)
 
 hz_status hz_group_create(hz_problem* const* probs, int count, hz_group** out) {
-  if (!out || !probs || count < 1) return HZ_EINVAL;
+  if (!out || !probs || count < 1 || count > LOOP_MAX_PROBLEMS) return HZ_EINVAL;
   *out = nullptr;
   hz_group* g = new hz_group();
   for (int i = 0; i < count; ++i) {
@@ -1389,9 +1387,6 @@ hz_status hz_group_create(hz_problem* const* probs, int count, hz_group** out) {
   if (!e) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
   g->join.assign(count, nullptr);
   for (int i = 0; i < count && !e; ++i) e = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming);
-  for (auto& ev : g->ev)
-    if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  if (!e) e = cudaMallocHost(&g->flags, sizeof(int) * 4 * PIPELINE * g->total);
   if (e) {
     group_release(g);
     delete g;
@@ -1401,32 +1396,35 @@ hz_status hz_group_create(hz_problem* const* probs, int count, hz_group** out) {
   return HZ_OK;
 }
 
-// One graph holding one iteration of every problem, each on its own branch.
+// The group's solve graph: the WHILE loop's body holds one iteration of every problem, each on
+// its own branch between a fork and a join; the control kernel watches every instance of every
+// problem (the loop counter lives in the first problem's status block).
 static hz_status group_graph(hz_group* g) {
   if (g->graph) {
     cudaGraphExecDestroy(g->graph);
     g->graph = nullptr;
   }
-  cudaGraph_t graph = nullptr;
-  GK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaEventRecord(g->fork, g->stream);
-  for (size_t i = 0; i < g->probs.size() && !e; ++i) {
-    hz_problem* P = g->probs[i];
-    e = cudaStreamWaitEvent(P->stream, g->fork, 0);
-    if (!e) e = enqueue_iteration(P);
-    if (!e) e = cudaEventRecord(g->join[i], P->stream);
-    if (!e) e = cudaStreamWaitEvent(g->stream, g->join[i], 0);
+  LoopCtl ctl{};
+  ctl.counter = loop_counter(g->probs[0]);
+  ctl.problems = (int)g->probs.size();
+  for (size_t i = 0; i < g->probs.size(); ++i) {
+    ctl.st[i] = g->probs[i]->kv.st;
+    ctl.batch[i] = g->probs[i]->plan.batch;
   }
-  cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
-  if (e || e2) {
-    if (graph) cudaGraphDestroy(graph);
-    g->err = std::string("capture of the group iteration: ") + cudaGetErrorString(e ? e : e2);
-    return HZ_ECUDA;
-  }
-  e = cudaGraphInstantiate(&g->graph, graph, 0);
-  cudaGraphDestroy(graph);
+  auto body = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventRecord(g->fork, g->stream);
+    for (size_t i = 0; i < g->probs.size() && !e; ++i) {
+      hz_problem* P = g->probs[i];
+      e = cudaStreamWaitEvent(P->stream, g->fork, 0);
+      if (!e) e = enqueue_iteration(P);
+      if (!e) e = cudaEventRecord(g->join[i], P->stream);
+      if (!e) e = cudaStreamWaitEvent(g->stream, g->join[i], 0);
+    }
+    return e;
+  };
+  cudaError_t e = build_loop_graph(g->stream, ctl, body, &g->graph);
   if (e) {
-    g->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+    g->err = std::string("building the group solve graph: ") + cudaGetErrorString(e);
     return HZ_ECUDA;
   }
   return HZ_OK;
@@ -1437,20 +1435,18 @@ hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x
   if (!g || !rhs || !x || !(tol > 0) || maxit < 1) return HZ_EINVAL;
   if (maxit > HIST_CAP / 2 - 1) maxit = HIST_CAP / 2 - 1;
   const size_t np = g->probs.size();
-  bool rebuild = !g->graph || g->graph_b.size() != np;
+  // every problem works on its own rhs and x buffers (copied in and out), so the group graph is
+  // built once
   for (size_t i = 0; i < np; ++i) {
     if (!rhs[i] || !x[i] || (const double*)x[i] == rhs[i]) return HZ_EINVAL;
     hz_problem* P = g->probs[i];
     if (P->run.phase != hz_problem::Run::IDLE) return HZ_EINVAL;
-    P->kv.b = (const double2*)rhs[i];
-    P->kv.x = (double2*)x[i];
-    if (!rebuild && (g->graph_b[i] != rhs[i] || g->graph_x[i] != x[i])) rebuild = true;
+    P->kv.b = P->b_int;
+    P->kv.x = P->x_int;
   }
-  if (rebuild) {
+  if (!g->graph) {
     hz_status st = group_graph(g);
     if (st) return st;
-    g->graph_b.assign(rhs, rhs + np);
-    g->graph_x.assign(x, x + np);
   }
   // order after the callers' streams, then the start-up of every problem
   for (size_t i = 0; i < np; ++i) {
@@ -1462,36 +1458,16 @@ hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x
   for (size_t i = 0; i < np; ++i) {
     hz_problem* P = g->probs[i];
     GK(cudaStreamWaitEvent(P->stream, g->fork, 0));
+    GK(cudaMemcpyAsync(P->b_int, rhs[i], sizeof(double2) * (size_t)P->kv.N * P->plan.batch,
+                       cudaMemcpyDeviceToDevice, P->stream));
     GK(launch_k_init(P->kv, tol, maxit, HIST_CAP, P->stream));
     GK(cudaEventRecord(g->join[i], P->stream));
     GK(cudaStreamWaitEvent(g->stream, g->join[i], 0));
   }
   int restarts = 0;
   for (;;) {
-    long long launched = 0, polled = 0;
-    const long long cap = (long long)maxit + 2;
-    bool done = false;
-    while (!done) {
-      if (launched < cap && launched - polled < PIPELINE) {
-        GK(cudaGraphLaunch(g->graph, g->stream));
-        int slot = (int)(launched % PIPELINE), off = 0;
-        for (size_t i = 0; i < np; ++i) {
-          hz_problem* P = g->probs[i];
-          GK(cudaMemcpy2DAsync(g->flags + 4 * (g->total * slot + off), 4 * sizeof(int), &P->kv.st->it, sizeof(KState),
-                               4 * sizeof(int), P->plan.batch, cudaMemcpyDeviceToHost, g->stream));
-          off += P->plan.batch;
-        }
-        GK(cudaEventRecord(g->ev[slot], g->stream));
-        ++launched;
-        continue;
-      }
-      int slot = (int)(polled % PIPELINE);
-      GK(cudaEventSynchronize(g->ev[slot]));
-      ++polled;
-      bool all = true;
-      for (int q = 0; q < g->total && all; ++q) all = g->flags[4 * (g->total * slot + q) + 2] != 0;
-      if (all || (polled >= launched && launched >= cap)) done = true;
-    }
+    // every iteration of every problem: one graph launch with a device-side loop
+    GK(cudaGraphLaunch(g->graph, g->stream));
     // true residuals and final states
     GK(cudaEventRecord(g->fork, g->stream));
     for (size_t i = 0; i < np; ++i) {
@@ -1519,6 +1495,12 @@ hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x
     if (!restarted) break;
     ++restarts;
   }
+  for (size_t i = 0; i < np; ++i) {
+    hz_problem* P = g->probs[i];
+    GK(cudaMemcpyAsync(x[i], P->x_int, sizeof(double2) * (size_t)P->kv.N * P->plan.batch, cudaMemcpyDeviceToDevice,
+                       P->stream));
+    GK(cudaStreamSynchronize(P->stream));
+  }
   hz_status worst = HZ_OK;
   int q = 0;
   for (size_t i = 0; i < np; ++i) {
@@ -1533,11 +1515,10 @@ hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x
         infos[q].relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.trr / hs.bnorm2) : 0.0;
         infos[q].history_len = 0;
         infos[q].status = sb;
-        infos[q].restarts = restarts;
+        infos[q].restarts = restarts + hs.shadow_restarts;
       }
     }
   }
-  for (size_t i = 0; i < np; ++i) g->probs[i]->graph_b = nullptr;  // their own graphs hold other buffers
   return worst;
 }
 
@@ -1556,6 +1537,17 @@ const char* hz_kernel_name(int k) {
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
                                 "kacz_sweep", "coarse_tail"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
+}
+
+int hz_krylov_scalars(hz_problem* P, int instance, double* out) {
+  if (!P || !P->setup || !out || instance < 0 || instance >= P->plan.batch) return -1;
+  KState ks;
+  if (cudaMemcpy(&ks, P->kv.st + instance, sizeof(KState), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  const double v[17] = {ks.rho.x, ks.rho.y, ks.alpha.x, ks.alpha.y, ks.omega.x, ks.omega.y, ks.beta.x, ks.beta.y,
+                        ks.rr, ks.ss, ks.tt, ks.bnorm2, (double)ks.it, (double)ks.done, ks.min_cos2,
+                        (double)ks.shadow_restarts, ks.min_step2};
+  for (int q = 0; q < 17; ++q) out[q] = v[q];
+  return 17;
 }
 
 const char* hz_last_error(const hz_problem* P) { return P ? P->err.c_str() : "null problem"; }

@@ -160,6 +160,7 @@ __host__ __device__ __forceinline__ KrylovVecs offset_instance(KrylovVecs k, lon
   if (b) {
     const long long o = b * k.sv;
     k.x += o; k.r += o; k.p += o; k.v += o; k.s += o; k.t += o; k.y += o; k.z += o; k.tr += o; k.b += o;
+    k.rhat += o;
     if (k.p32) { k.p32 += o; k.s32 += o; k.y32 += o; k.z32 += o; }
     k.st += b;
     k.partials += b * k.part_stride;
@@ -170,21 +171,25 @@ __host__ __device__ __forceinline__ KrylovVecs offset_instance(KrylovVecs k, lon
 // This block's instance (blockIdx.z).
 __device__ __forceinline__ KrylovVecs instance(const KrylovVecs& k) { return offset_instance(k, blockIdx.z); }
 
+// Counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c + 1 of the generator started
+// from `seed`, top 53 bits mapped to [0, 1); r^_p = (u_2p - 1/2) + i (u_2p+1 - 1/2).
+__device__ __forceinline__ double2 shadow_value(unsigned long long seed, long long p) {
+  double u[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(2 * p + c + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    u[c] = (double)(z >> 11) * 0x1.0p-53;
+  }
+  return make_double2(u[0] - 0.5, u[1] - 0.5);
+}
+
 __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long seed) {
   pdl_enter();
-  // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output number c + 1 of the generator
-  // started from `seed`, top 53 bits mapped to [0, 1); r^_p = (u_2p - 1/2) + i (u_2p+1 - 1/2).
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    double u[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(2 * p + c + 1);
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      z = z ^ (z >> 31);
-      u[c] = (double)(z >> 11) * 0x1.0p-53;
-    }
-    rhat[p] = make_double2(u[0] - 0.5, u[1] - 0.5);
+    rhat[p] = shadow_value(seed, p);
   }
 }
 
@@ -192,7 +197,7 @@ __global__ void shadow_kernel(double2* rhat, long long N, unsigned long long see
 __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap) {
   pdl_enter();
   k = instance(k);
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int N = (int)k.N;
   GRID_STRIDE(e, N) {
     double2 bv = k.b[e];
@@ -205,9 +210,10 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
     acc[0] = fma(r.x, r.x, fma(r.y, r.y, acc[0]));
     acc[1] = fma(rh.x, r.x, fma(rh.y, r.y, acc[1]));
     acc[2] = fma(rh.x, r.y, fma(-rh.y, r.x, acc[2]));
+    acc[3] = fma(rh.x, rh.x, fma(rh.y, rh.y, acc[3]));
   }
-  double tot[3];
-  if (!grid_sum<3>(acc, k.partials, &k.st->ticket[KT_INIT], tot)) return;
+  double tot[4];
+  if (!grid_sum<4>(acc, k.partials, &k.st->ticket[KT_INIT], tot)) return;
   if (threadIdx.x == 0) {
     KState* st = k.st;
     st->bnorm2 = tot[0];
@@ -226,6 +232,10 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
     st->maxit = maxit;
     st->done = 0;
     st->iters_x2 = 0;
+    st->shadow_restarts = 0;
+    st->rhat2 = tot[3];
+    st->min_cos2 = 1.0;
+    st->min_step2 = 1.0;
     if (!fin(tot[0]) || !fin(tot[1]) || !fin(tot[2])) st->done = 3;
     else if (tot[0] == 0.0) st->done = 1;
     else if (tot[1] == 0.0 && tot[2] == 0.0) st->done = 2;
@@ -237,6 +247,33 @@ __global__ void k_update_p_kernel(KrylovVecs k) {
   pdl_enter();
   k = instance(k);
   KState* st = k.st;
+  if (st->done == 5) {
+    // Near-breakdown restart: a new pseudo-random shadow residual (the next seed of the same
+    // generator), p = r, rho = <r^, r>.
+    const unsigned long long seed = SHADOW_SEED + 0x2545F4914F6CDD1Dull * (unsigned long long)(st->shadow_restarts + 1);
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int N = (int)k.N;
+    GRID_STRIDE(e, N) {
+      const double2 rh = shadow_value(seed, e), r = k.r[e];
+      k.rhat[e] = rh;
+      k.p[e] = r;
+      if (k.p32) k.p32[e] = narrow(r);
+      acc[0] = fma(rh.x, r.x, fma(rh.y, r.y, acc[0]));
+      acc[1] = fma(rh.x, r.y, fma(-rh.y, r.x, acc[1]));
+      acc[2] = fma(rh.x, rh.x, fma(rh.y, rh.y, acc[2]));
+    }
+    double tot[3];
+    if (!grid_sum<3>(acc, k.partials, &st->ticket[KT_SHADOW], tot)) return;
+    if (threadIdx.x == 0) {
+      st->rho = make_double2(tot[0], tot[1]);
+      st->rhat2 = tot[2];
+      st->first = 0;
+      st->shadow_restarts += 1;
+      st->done = (tot[0] == 0.0 && tot[1] == 0.0) ? 2 : 0;
+      if (st->done) st->iters_x2 = 2 * (st->it - 1);
+    }
+    return;
+  }
   if (st->done) return;
   if (st->it > st->maxit) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 4;
@@ -420,6 +457,19 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
       st->done = 2;
       st->iters_x2 = 2 * st->it;
     }
+    if (!st->done) {  // here |r|^2 > tol2 > 0
+      const double cos2 = (rho_new.x * rho_new.x + rho_new.y * rho_new.y) / (st->rhat2 * tot[2]);
+      st->min_cos2 = fmin(st->min_cos2, cos2);
+      const double step2 = (omega.x * omega.x + omega.y * omega.y) * st->tt / tot[2];
+      if (cos2 < STALL_COS2) st->min_step2 = fmin(st->min_step2, step2);
+      if (cos2 < STALL_COS2 && step2 < STALL_STEP2 && st->shadow_restarts < MAX_SHADOW_RESTARTS) {
+        // <r^, r> has collapsed relative to |r^| |r| and the iteration no longer moves r: the
+        // recurrences stall (alpha, omega -> 0) unless the shadow residual is renewed; the next
+        // direction update restarts from r.
+        st->done = 5;
+        st->it += 1;
+      }
+    }
     if (!st->done) {
       st->rho_old = st->rho;
       st->rho = rho_new;
@@ -428,6 +478,22 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
       st->it += 1;
     }
   }
+}
+
+// One thread: count the iteration and set the WHILE node's condition (see LoopCtl).
+__global__ void loop_control_kernel(LoopCtl c) {
+  pdl_enter();
+  if (threadIdx.x != 0) return;
+  const int cnt = ++*c.counter;
+  bool running = false;
+  int cap = 0;
+  for (int p = 0; p < c.problems; ++p)
+    for (int b = 0; b < c.batch[p]; ++b) {
+      const KState& s = c.st[p][b];
+      running = running || s.done == 0 || s.done == 5;
+      cap = max(cap, s.maxit + 2);
+    }
+  cudaGraphSetConditional(c.handle, (running && cnt < cap) ? 1u : 0u);
 }
 
 // tr = h^2 b - A x and |tr|^2, to confirm a recurrence-converged iterate.
@@ -534,6 +600,10 @@ cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_true_residual_kernel) }
+cudaError_t launch_loop_control(const LoopCtl& c, cudaStream_t s) {
+  pdl_launch(loop_control_kernel, 1, 32, 0, s, c);
+  return cudaGetLastError();
+}
 cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_restart_kernel) }
 
 cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, int n, double beta, double out_scale,

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "hz_coarse_solve": (c_int, [P, c_void_p, c_void_p]),
         "hz_profile_iteration": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
         "hz_profile_graph": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
+        "hz_krylov_scalars": (c_int, [P, c_int, POINTER(c_double)]),
         "hz_kernel_name": (ctypes.c_char_p, [c_int]),
         "hz_last_error": (ctypes.c_char_p, [P]),
         "hz_status_string": (ctypes.c_char_p, [c_int]),
@@ -319,6 +320,17 @@ class Problem:
         if cnt < 0:
             raise HzError(HZ_ECUDA, lib().hz_last_error(self._h).decode())
         return [(lib().hz_kernel_name(out[q].kernel).decode(), out[q].level, float(out[q].ms)) for q in range(min(cnt, cap))]
+
+    def krylov_scalars(self, instance: int = 0) -> dict:
+        """Bi-CGSTAB scalars of an instance after the last solve (diagnostics)."""
+        out = (c_double * 17)()
+        if lib().hz_krylov_scalars(self._h, instance, out) != 17:
+            raise HzError(HZ_ECUDA, lib().hz_last_error(self._h).decode())
+        v = list(out)
+        return {"rho": complex(v[0], v[1]), "alpha": complex(v[2], v[3]), "omega": complex(v[4], v[5]),
+                "beta": complex(v[6], v[7]), "rr": v[8], "ss": v[9], "tt": v[10], "bnorm2": v[11],
+                "it": int(v[12]), "done": int(v[13]), "min_cos2": v[14], "shadow_restarts": int(v[15]),
+                "min_step2": v[16]}
 
     def vcycle(self, r):
         self._stream()

@@ -168,6 +168,7 @@ class Server:
             "peak_hbm_bytes": self.peak_used,
             "peak_active": self.peak_active,
             "evictions": self.evictions,
+            "statuses": dict(collections.Counter(int(j.result.get("status", -1)) for j in self.done)),
         }
 
     def close(self):
