@@ -183,11 +183,13 @@ hz_status hz_solve_host(hz_problem* p, const double* rhs_host, double* x_host, d
                         double* history, int history_cap, hz_solve_info* info);
 
 /* ---- Non-blocking solve: one host thread can keep many problems' solves in flight (serving).
- * hz_solve_start validates, copies rhs into the problem's own buffer and queues the whole solve
- * on the problem's stream (one graph launch whose iterations loop on the device, then the true
- * residual) and returns; hz_solve_poll never waits: it checks whether that work has finished,
- * queues a restart from the true residual when the recurrence converged without it, and sets
- * *done = 1 once the solve has stopped (converged, broken down, non-finite or maxit);
+ * hz_solve_start validates, copies rhs into the problem's own buffer, queues the start-up and the
+ * first iterations (one graph launch each) on the problem's stream and returns; hz_solve_poll
+ * never waits: it reads the progress flags that have already landed, queues further iterations
+ * (or the true residual, and a restart from it when the recurrence converged without it), and
+ * sets *done = 1 once the solve has stopped (converged, broken down, non-finite or maxit). The
+ * iterations are launched from the host rather than looped on the device (as hz_solve does)
+ * because solves on different streams then overlap on the GPU;
  * hz_solve_finish waits for the end if needed, copies the solution to x and reports exactly as
  * hz_solve does (status, history, info). x holds the result only after hz_solve_finish returns.
  * One solve per problem at a time (HZ_EINVAL otherwise); x must stay valid until

@@ -32,6 +32,8 @@ const double BIN_HI = 1.25 * std::sqrt(2.0);
 const double GUARD_LO = 1.0;
 const double GUARD_HI = 2.0 * std::sqrt(2.0);
 
+constexpr int PIPELINE = 3;  // polled mode: iterations queued ahead of the convergence poll
+
 struct Level {
   int n = 0, pitch = 0;
   double H = 0;
@@ -167,17 +169,22 @@ struct hz_problem {
   const double2* graph_b = nullptr;
   double2* graph_x = nullptr;
   int num_sms = 0;
+  int* poll_host = nullptr;           // pinned: PIPELINE slots x batch x 4 ints (it, first, done, half)
+  cudaEvent_t ev_poll[PIPELINE]{};    // completion of each polled iteration
+  cudaGraphExec_t graph_iter = nullptr;  // one iteration, replayed from the host (polled mode)
   int tail_start = -1;  // first level run by the one-block coarse tail (-1: none)
   TailArgs tail{};
   size_t tail_smem = 0;
   std::string err;
   // Solve in flight (see solve_begin/solve_advance/solve_end).
   struct Run {
-    enum Phase { IDLE = 0, RUNNING, DONE };
+    enum Phase { IDLE = 0, RUNNING, POLLING, DONE };
     int phase = IDLE;
     double tol = 0;
     int maxit = 0;
     int restarts = 0;
+    bool polled = false;       // host-polled iterations instead of the device-side loop
+    long long launched = 0, seen = 0;
     double* user_x = nullptr;  // where solve_end copies the solution
   } run;
   KState* kstate_host = nullptr;  // pinned copy of the device Krylov state at the end of a solve
@@ -549,24 +556,74 @@ hz_status build_graph(hz_problem* P) {
   return HZ_OK;
 }
 
+// One Bi-CGSTAB iteration as a plain graph, replayed from the host (polled mode).
+hz_status build_iter_graph(hz_problem* P) {
+  if (P->graph_iter) return HZ_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_iteration(P);
+  cudaError_t e2 = cudaStreamEndCapture(P->stream, &g);
+  if (e) return cuda_fail(P, e, "capture of one Bi-CGSTAB iteration");
+  if (e2) return cuda_fail(P, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&P->graph_iter, g, 0);
+  cudaGraphDestroy(g);
+  if (e) return cuda_fail(P, e, "cudaGraphInstantiate");
+  return HZ_OK;
+}
+
+// Polled mode: one iteration graph, then the 16-byte flag block (it, first, done, half) of every
+// instance into pinned memory, then an event the host polls.
+cudaError_t enqueue_replay(hz_problem* P) {
+  hz_problem::Run& R = P->run;
+  cudaStream_t s = P->stream;
+  cudaError_t e = cudaGraphLaunch(P->graph_iter, s);
+  const int slot = (int)(R.launched % PIPELINE), B = P->plan.batch;
+  if (!e)
+    e = cudaMemcpy2DAsync(P->poll_host + 4 * B * slot, 4 * sizeof(int), &P->kv.st->it, sizeof(KState), 4 * sizeof(int),
+                          B, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaEventRecord(P->ev_poll[slot], s);
+  if (!e) ++R.launched;
+  return e;
+}
+
 // ------------------------------------------------------------------ resumable solve
 // A solve is a small state machine so that one host thread can drive many problems at once
 // (hz_solve_start / hz_solve_poll / hz_solve_finish); hz_solve runs the same machine blocking.
-// RUNNING: the solve graph (all iterations, device-side loop), the true residual and a copy of
-// every instance's Krylov state are in flight behind ev_final; when they land, an instance whose
-// recurrence converged but whose true residual did not is restarted from it and the graph runs
-// again (at most 8 times); otherwise the solve is DONE.
+// Two ways to run the iterations:
+//  * device loop (blocking solves): the solve graph runs every iteration in one launch;
+//  * polled (non-blocking solves): the host keeps PIPELINE iteration-graph launches in flight and
+//    reads each one's flag copy when its event completes. Graphs with a device-side loop launched
+//    on different streams were measured to run one after another, while plain graph launches
+//    overlap, so concurrent solves (serving) use this mode.
+// RUNNING: the iterations, the true residual and a copy of every instance's Krylov state are in
+// flight behind ev_final; when they land, an instance whose recurrence converged but whose true
+// residual did not is restarted from it (at most 8 times); otherwise the solve is DONE.
 
-cudaError_t launch_loop(hz_problem* P) {
+cudaError_t launch_final(hz_problem* P) {
   cudaStream_t s = P->stream;
-  cudaError_t e = cudaGraphLaunch(P->graph, s);
-  if (!e) e = launch_k_true_residual(P->kv, s);
+  cudaError_t e = launch_k_true_residual(P->kv, s);
   if (!e) e = cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * P->plan.batch, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaEventRecord(P->ev_final, s);
   return e;
 }
 
-hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, int maxit) {
+// Start (or, after a restart, resume) the iterations in the run's mode.
+cudaError_t launch_iterations(hz_problem* P) {
+  hz_problem::Run& R = P->run;
+  if (!R.polled) {
+    cudaError_t e = cudaGraphLaunch(P->graph, P->stream);
+    if (!e) e = launch_final(P);
+    R.phase = hz_problem::Run::RUNNING;
+    return e;
+  }
+  R.launched = R.seen = 0;
+  R.phase = hz_problem::Run::POLLING;
+  cudaError_t e = cudaSuccess;
+  while (!e && R.launched < PIPELINE && R.launched < (long long)R.maxit + 2) e = enqueue_replay(P);
+  return e;
+}
+
+hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, int maxit, bool polled = false) {
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
   if (P->run.phase != hz_problem::Run::IDLE) return fail(P, HZ_EINVAL, "a solve is already in flight on this problem");
   if (!rhs || !x || !(tol > 0) || maxit < 1) return fail(P, HZ_EINVAL, "bad solve arguments");
@@ -579,7 +636,10 @@ hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, i
     CK(cudaMemcpyAsync(P->b_int, rhs, bytes, cudaMemcpyDeviceToDevice, P->stream));
   P->kv.b = P->b_int;
   P->kv.x = P->x_int;
-  if (!P->graph || P->graph_b != P->kv.b || P->graph_x != P->kv.x) {
+  if (polled) {
+    hz_status st = build_iter_graph(P);
+    if (st) return st;
+  } else if (!P->graph || P->graph_b != P->kv.b || P->graph_x != P->kv.x) {
     hz_status st = build_graph(P);
     if (st) return st;
   }
@@ -588,9 +648,9 @@ hz_status solve_begin(hz_problem* P, const double* rhs, double* x, double tol, i
   R.tol = tol;
   R.maxit = maxit;
   R.user_x = x;
+  R.polled = polled;
   CK(launch_k_init(P->kv, tol, maxit, HIST_CAP, P->stream));
-  CK(launch_loop(P));
-  R.phase = hz_problem::Run::RUNNING;
+  CK(launch_iterations(P));
   return HZ_OK;
 }
 
@@ -603,6 +663,29 @@ hz_status solve_advance(hz_problem* P, bool block, int* done) {
     if (R.phase == hz_problem::Run::DONE) {
       *done = 1;
       return HZ_OK;
+    }
+    if (R.phase == hz_problem::Run::POLLING) {
+      const int slot = (int)(R.seen % PIPELINE);
+      if (block) {
+        CK(cudaEventSynchronize(P->ev_poll[slot]));
+      } else {
+        cudaError_t q = cudaEventQuery(P->ev_poll[slot]);
+        if (q == cudaErrorNotReady) return HZ_OK;
+        if (q != cudaSuccess) return cuda_fail(P, q, "cudaEventQuery");
+      }
+      const int B = P->plan.batch;
+      const int* flags = P->poll_host + 4 * B * slot;
+      ++R.seen;
+      bool all_done = true;  // done 5 (shadow restart pending) is still iterating
+      for (int b = 0; b < B; ++b) all_done = all_done && flags[4 * b + 2] != 0 && flags[4 * b + 2] != 5;
+      const long long cap = (long long)R.maxit + 2;
+      if (all_done || (R.seen >= R.launched && R.launched >= cap)) {
+        CK(launch_final(P));
+        R.phase = hz_problem::Run::RUNNING;
+      } else if (R.launched < cap) {
+        CK(enqueue_replay(P));
+      }
+      continue;
     }
     if (block) {
       CK(cudaEventSynchronize(P->ev_final));
@@ -623,7 +706,7 @@ hz_status solve_advance(hz_problem* P, bool block, int* done) {
     }
     if (restarted) {
       ++R.restarts;
-      CK(launch_loop(P));
+      CK(launch_iterations(P));
       continue;
     }
     R.phase = hz_problem::Run::DONE;
@@ -956,6 +1039,9 @@ static void release(hz_problem* P) {
   if (P->graph) { cudaGraphExecDestroy(P->graph); P->graph = nullptr; }
   if (P->ev_in) { cudaEventDestroy(P->ev_in); P->ev_in = nullptr; }
   if (P->ev_final) { cudaEventDestroy(P->ev_final); P->ev_final = nullptr; }
+  for (auto& e : P->ev_poll) if (e) { cudaEventDestroy(e); e = nullptr; }
+  if (P->poll_host) { cudaFreeHost(P->poll_host); P->poll_host = nullptr; }
+  if (P->graph_iter) { cudaGraphExecDestroy(P->graph_iter); P->graph_iter = nullptr; }
   if (P->kstate_host) { cudaFreeHost(P->kstate_host); P->kstate_host = nullptr; }
   P->run = hz_problem::Run();
   if (P->ev_out) { cudaEventDestroy(P->ev_out); P->ev_out = nullptr; }
@@ -999,6 +1085,8 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_final, cudaEventDisableTiming));
   CK(cudaMallocHost(&P->kstate_host, sizeof(KState) * pl.batch));
+  CK(cudaMallocHost(&P->poll_host, sizeof(int) * 4 * PIPELINE * pl.batch));
+  for (auto& e : P->ev_poll) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   StreamScope scope(P);
   unsigned char* A = P->arena;
   int n = P->n;
@@ -1165,7 +1253,7 @@ hz_status hz_solve_start(hz_problem* P, const double* rhs, double* x, double tol
   if (!P) return HZ_EINVAL;
   if (P->setup && P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: use hz_solve_batch");
   StreamScope scope(P);
-  return solve_begin(P, rhs, x, tol, maxit);
+  return solve_begin(P, rhs, x, tol, maxit, true);
 }
 
 hz_status hz_solve_poll(hz_problem* P, int* done) {
