@@ -61,6 +61,14 @@ typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
 typedef enum { HZ_OP_L = 0, HZ_OP_M = 1 } hz_op;
 typedef enum { HZ_SMOOTH_GS = 0, HZ_SMOOTH_KACZMARZ = 1, HZ_SMOOTH_DIRECT = 2 } hz_smoother;
 
+/* Kernel forms of a Kaczmarz level (Sec. 4): one launch per colour; the whole level (sweeps,
+   residual and full weighting, or correction and sweeps) in one block's shared memory; one launch
+   per sweep over halo tiles; the whole level in the shared memory of a thread-block cluster of up
+   to 16 blocks (row bands, neighbour rows through distributed shared memory). All four take the
+   same row actions in the same colour order with the same fixed-rounding arithmetic, so they give
+   the same bits; they differ in launches and parallelism only. */
+typedef enum { HZ_KACZ_COLOUR = 0, HZ_KACZ_LEVEL = 1, HZ_KACZ_TILE = 2, HZ_KACZ_CLUSTER = 3 } hz_kacz_form;
+
 typedef struct {
   int levels;    /* number of grids; 0 = coarsen while n_l is even and larger than 8 */
   int variant;   /* hz_variant, default HZ_VAR_HYB */
@@ -81,6 +89,11 @@ typedef struct {
                        fits one block's shared memory down to the coarsest, run as one launch (same
                        operations, same results as the per-level kernels for one-sweep Gauss-Seidel
                        and FP32 Kaczmarz levels); 0: one or more launches per level */
+  int kacz_form;    /* how Kaczmarz levels below the finest run (hz_kacz_form): -1 (default) = one
+                       block if the level fits its shared memory, else a thread-block cluster, else
+                       tiles (even sweep counts), else colour launches in the FP32 form; a cluster,
+                       else colour launches in the FP64 form. A form that does not apply to a level
+                       falls back to that default. */
 } hz_hierarchy_opts;
 
 typedef struct {
@@ -94,6 +107,7 @@ typedef struct {
                     or not yet set up */
   int pass_up;   /* form of the fused post-smoothing pass; -1 likewise */
   int in_tail;   /* 1 if the level runs inside the one-block coarse tail (see coarse_tail) */
+  int kacz_form; /* hz_kacz_form of a Kaczmarz level outside the tail; -1 otherwise or before setup */
 } hz_level_info;
 
 typedef struct {
@@ -245,6 +259,7 @@ typedef enum {
   HZ_K_KACZ_LEVEL,     /* whole Kaczmarz level in one block (pre: sweeps + residual + FW; post: correction + sweeps) */
   HZ_K_KACZ_SWEEP,     /* one five-colour Kaczmarz sweep over halo tiles */
   HZ_K_TAIL,           /* coarse tail: every level from hz_level_info.in_tail down, in one block */
+  HZ_K_KACZ_CLUSTER,   /* whole Kaczmarz level over a thread-block cluster (pre or post, as HZ_K_KACZ_LEVEL) */
   HZ_K_COUNT
 } hz_kernel;
 
@@ -271,10 +286,18 @@ int hz_profile_graph(hz_problem* p, const double* rhs, double* x, int iterations
  * rho, alpha, omega, beta (complex, re/im pairs), |r|^2, |s|^2, |t|^2, |b|^2 (h^2-scaled), the
  * iteration, the stop code (0 running, 1 converged, 2 breakdown, 3 non-finite, 4 maxit), the
  * smallest |<r^, r>|^2 / (|r^|^2 |r|^2) seen, the number of near-breakdown restarts, and the
- * smallest |omega|^2 |t|^2 / |r|^2 seen in iterations whose |<r^, r>|^2 / (|r^|^2 |r|^2) < 1e-12
- * (a restart renews r^ when both ratios fall below 1e-12 and 1e-8).
+ * smallest |omega|^2 |t|^2 / |r|^2 seen in iterations whose |<r^, r>|^2 / (|r^|^2 |r|^2) is below
+ * the near-breakdown threshold (see hz_set_stall_detection).
  * Returns 17, or -1 on error. Synchronises. */
 int hz_krylov_scalars(hz_problem* p, int instance, double* out);
+
+/* Near-breakdown detection of Bi-CGSTAB (a safeguard the paper does not discuss): after an
+ * iteration with |<r^, r>|^2 < cos2 |r^|^2 |r|^2 and |omega|^2 |t|^2 < step2 |r|^2 (the
+ * recurrences no longer move r), the shadow residual r^ is renewed with fresh pseudo-random
+ * values and the next direction restarts from r, at most max_restarts times per solve. Defaults
+ * 1e-12, 1e-8, 16; max_restarts = 0 turns it off. Applies to the solves started after the call.
+ * Returns HZ_EINVAL for a negative or non-finite threshold or max_restarts outside [0, 1024]. */
+hz_status hz_set_stall_detection(hz_problem* p, double cos2, double step2, int max_restarts);
 
 /* Name of an hz_kernel. */
 const char* hz_kernel_name(int kernel);

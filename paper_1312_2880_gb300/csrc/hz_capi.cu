@@ -44,6 +44,7 @@ struct Level {
   void* f = nullptr;  // working precision complex (levels >= 1)
   void* u2 = nullptr; // result of the fused post-smoothing pass (levels >= 1)
   int var_down = 0, var_up = 0;  // fused-pass variants (FP32 form; picked by the tile autotuner)
+  int kform = 0;                 // hz_kacz_form of a Kaczmarz level (set up by plan_kaczmarz)
 };
 
 struct Plan {
@@ -300,15 +301,49 @@ bool fused(const hz_problem* P, int l) {
   return l < P->plan.levels - 1 && L.smoother == HZ_SMOOTH_GS && L.nu == 1;
 }
 
-// How an FP32 Kaczmarz level runs: whole level in one block, or one tiled launch per sweep (even
-// sweep counts, ping-pong between u and u2 ending in u). FP64 keeps one launch per colour: there
-// the FP64 pipe bounds the work and the tiles' halo would add to it.
-enum KaczPath { KACZ_COLOUR = 0, KACZ_LEVEL, KACZ_TILE };
+// How a Kaczmarz level runs (hz_kacz_form): one launch per colour, the whole level in one block,
+// one tiled launch per sweep (even sweep counts, ping-pong between u and u2 ending in u), or the
+// whole level over a thread-block cluster. The finest level keeps the colour launches (its
+// right-hand side is the FP64 Krylov vector in the FP32 form).
+enum KaczPath { KACZ_COLOUR = HZ_KACZ_COLOUR, KACZ_LEVEL = HZ_KACZ_LEVEL, KACZ_TILE = HZ_KACZ_TILE,
+                KACZ_CLUSTER = HZ_KACZ_CLUSTER };
 KaczPath kacz_path(const hz_problem* P, int l) {
   const Level& L = P->lv[l];
-  if (l == 0 || !P->plan.fp32 || L.smoother != HZ_SMOOTH_KACZMARZ) return KACZ_COLOUR;
-  if (kacz_level_fits(true, L.n)) return KACZ_LEVEL;
-  return (L.nu % 2 == 0) ? KACZ_TILE : KACZ_COLOUR;
+  if (L.smoother != HZ_SMOOTH_KACZMARZ) return KACZ_COLOUR;
+  return (KaczPath)L.kform;
+}
+bool kform_ok(const hz_problem* P, int l, int form) {
+  const Level& L = P->lv[l];
+  const bool fp32 = P->plan.fp32;
+  switch (form) {
+    case HZ_KACZ_COLOUR: return true;
+    case HZ_KACZ_LEVEL: return l > 0 && kacz_level_fits(fp32, L.n);
+    case HZ_KACZ_TILE: return l > 0 && fp32 && L.nu % 2 == 0;
+    case HZ_KACZ_CLUSTER: return l > 0 && kacz_cluster_fits(fp32, L.n);
+  }
+  return false;
+}
+// Default form: FP32 - one block if the level fits, else a cluster, else tiles; FP64 - a cluster
+// (the FP64 pipe of one SM bounds the one-block form, and the tiles' halo adds FP64 work), else
+// colour launches. Measured per Bi-CGSTAB iteration (four level launches): FP32 n_l = 128 cluster
+// 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64 cluster 206 us,
+// colour launches 820 us.
+int default_kform(const hz_problem* P, int l) {
+  const int order32[] = {HZ_KACZ_LEVEL, HZ_KACZ_CLUSTER, HZ_KACZ_TILE}, order64[] = {HZ_KACZ_CLUSTER};
+  const int* o = P->plan.fp32 ? order32 : order64;
+  const int cnt = P->plan.fp32 ? 3 : 1;
+  for (int q = 0; q < cnt; ++q)
+    if (kform_ok(P, l, o[q])) return o[q];
+  return HZ_KACZ_COLOUR;
+}
+void plan_kaczmarz(hz_problem* P) {
+  for (int l = 0; l < P->plan.levels - 1; ++l) {
+    Level& L = P->lv[l];
+    L.kform = HZ_KACZ_COLOUR;
+    if (L.smoother != HZ_SMOOTH_KACZMARZ) continue;
+    const int want = P->opts.kacz_form;
+    L.kform = (want >= 0 && kform_ok(P, l, want)) ? want : default_kform(P, l);
+  }
 }
 
 // Tiled sweeps on level l: `first_in` is the input of the first sweep (null = zero guess).
@@ -355,8 +390,11 @@ cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop, bool all = 
                 HZ_K_SMOOTH_RESTRICT, l);
   KaczPath kp = kacz_path(P, l);
   if (kp == KACZ_LEVEL)
-    return mark(P, launch_kacz_level_pre(true, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop, s, bi),
+    return mark(P, launch_kacz_level_pre(fp32, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop, s, bi),
                 HZ_K_KACZ_LEVEL, l);
+  if (kp == KACZ_CLUSTER)
+    return mark(P, launch_kacz_cluster_pre(fp32, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop, s, bi),
+                HZ_K_KACZ_CLUSTER, l);
   if (kp == KACZ_TILE) {
     if ((e = kacz_tile_sweeps(P, l, f, nullptr, false, stop, bi))) return e;
     return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s, bi),
@@ -428,9 +466,16 @@ cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* 
   if (kp == KACZ_LEVEL) {
     int pk;
     const void* kh = kh_of(P, l, &pk);
-    return mark(P, launch_kacz_level_post(true, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
+    return mark(P, launch_kacz_level_post(fp32, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
                                           op_beta(P, L.relax_op), L.nu, stop, P->stream, bi),
                 HZ_K_KACZ_LEVEL, l);
+  }
+  if (kp == KACZ_CLUSTER) {
+    int pk;
+    const void* kh = kh_of(P, l, &pk);
+    return mark(P, launch_kacz_cluster_post(fp32, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
+                                            op_beta(P, L.relax_op), L.nu, stop, P->stream, bi),
+                HZ_K_KACZ_CLUSTER, l);
   }
   if ((e = mark(P, launch_prolong_add(fp32, L.u, L.pitch, ec, C.pitch, L.n, stop, P->stream, bi), HZ_K_PROLONG, l))) return e;
   if (kp == KACZ_TILE) {
@@ -838,7 +883,8 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
 bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
            o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024 ||
-           o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1);
+           o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1 ||
+           o.kacz_form < -1 || o.kacz_form > HZ_KACZ_CLUSTER);
 }
 
 // ------------------------------------------------------------------ coarse tail
@@ -1001,6 +1047,7 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->batch = 1;
   o->pass_variant = -1;
   o->coarse_tail = 1;
+  o->kacz_form = -1;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {
@@ -1140,7 +1187,6 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   k.G = (int)std::min<long long>(want, std::min(8LL * P->num_sms, (long long)MAX_G));
   if (k.G < 1) k.G = 1;
   CK(cudaMemsetAsync(k.st, 0, sizeof(KState) * pl.batch, s));
-  for (int b = 0; b < pl.batch; ++b) CK(launch_shadow(k.rhat + b * k.sv, k.N, SHADOW_SEED, s));
   // Coarsest: dense inverse on the device.
   Level& C = P->lv.back();
   P->ainvT = A + pl.off_ainv;
@@ -1151,6 +1197,7 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   CK(cudaMemcpyAsync(&status, P->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (status != 0) return fail(P, HZ_EINVAL, "coarsest operator is singular");
+  plan_kaczmarz(P);
   plan_tail(P);
   CK(autotune(P));
   CK(cudaStreamSynchronize(s));
@@ -1177,6 +1224,7 @@ int hz_describe_hierarchy(const hz_problem* P, const hz_hierarchy_opts* opts, hz
     out[l].nu = lv[l].nu;
     out[l].pass_down = out[l].pass_up = -1;  // chosen at setup
     out[l].in_tail = 0;
+    out[l].kacz_form = -1;
   }
   return pl.levels;
 }
@@ -1198,6 +1246,7 @@ hz_status hz_get_level_info(const hz_problem* P, int level, hz_level_info* info)
   info->pass_down = fz ? L.var_down : -1;
   info->pass_up = fz ? L.var_up : -1;
   info->in_tail = (P->tail_start > 0 && level >= P->tail_start) ? 1 : 0;
+  info->kacz_form = (L.smoother == HZ_SMOOTH_KACZMARZ && !info->in_tail) ? L.kform : -1;
   return HZ_OK;
 }
 
@@ -1619,11 +1668,22 @@ void hz_group_destroy(hz_group* g) {
   delete g;
 }
 
+hz_status hz_set_stall_detection(hz_problem* P, double cos2, double step2, int max_restarts) {
+  if (!P) return HZ_EINVAL;
+  if (!(cos2 >= 0.0) || !(step2 >= 0.0) || !std::isfinite(cos2) || !std::isfinite(step2) || max_restarts < 0 ||
+      max_restarts > 1024)
+    return fail(P, HZ_EINVAL, "stall detection: thresholds must be finite and >= 0, max_restarts in [0, 1024]");
+  P->kv.stall_cos2 = cos2;
+  P->kv.stall_step2 = step2;
+  P->kv.max_shadow_restarts = max_restarts;
+  return HZ_OK;
+}
+
 const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s", "k_x_half",
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
-                                "kacz_sweep", "coarse_tail"};
+                                "kacz_sweep", "coarse_tail", "kacz_cluster"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -89,6 +89,14 @@ cudaError_t launch_kacz_level_pre(bool fp32, void* u, int pu, void* fc, int pc, 
                                   int pk, int n, double bA, double bB, int nu, const int* stop, cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_kacz_level_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
                                    const void* kh, int pk, int n, double bA, int nu, const int* stop, cudaStream_t s, const Inst& bi = Inst());
+// Whole level over a thread-block cluster (row bands, distributed shared memory; up to 16 blocks).
+bool kacz_cluster_fits(bool fp32, int n);
+cudaError_t launch_kacz_cluster_pre(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
+                                    int pk, int n, double bA, double bB, int nu, const int* stop, cudaStream_t s,
+                                    const Inst& bi = Inst());
+cudaError_t launch_kacz_cluster_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
+                                     const void* kh, int pk, int n, double bA, int nu, const int* stop, cudaStream_t s,
+                                     const Inst& bi = Inst());
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
                                    bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
                                    cudaStream_t s, const Inst& bi = Inst());
@@ -148,7 +156,9 @@ struct KState {
   int shadow_restarts;  // near-breakdown restarts with a new shadow residual
   double rhat2;         // |r^|^2 of the current shadow residual
   double min_cos2;      // smallest |<r^, r>|^2 / (|r^|^2 |r|^2) seen in the solve (diagnostics)
-  double min_step2;     // smallest |omega|^2 |t|^2 / |r|^2 seen while cos2 < 1e-12 (diagnostics)
+  double min_step2;     // smallest |omega|^2 |t|^2 / |r|^2 seen while cos2 < stall_cos2 (diagnostics)
+  double stall_cos2, stall_step2;  // near-breakdown thresholds of this solve (below)
+  int max_shadow_restarts;
   unsigned int ticket[16];  // last-block counters, one per reduction kernel
 };
 
@@ -160,7 +170,8 @@ constexpr unsigned long long SHADOW_SEED = 0x5EED1312ull;
 //   |<r^, r>|^2 < STALL_COS2 |r^|^2 |r|^2   and   |omega|^2 |t|^2 < STALL_STEP2 |r|^2
 // the shadow residual is renewed (at most MAX_SHADOW_RESTARTS times per solve). Measured on the
 // serving and parity workloads: converging solves keep the second ratio above 1.7e-5 whenever the
-// first is below 1e-12; the two stalled ones reached 7.5e-20 and 5.2e-19.
+// first is below 1e-12; the two stalled ones reached 7.5e-20 and 5.2e-19. These are the defaults
+// of hz_set_stall_detection.
 constexpr double STALL_COS2 = 1e-12;
 constexpr double STALL_STEP2 = 1e-8;
 constexpr int MAX_SHADOW_RESTARTS = 16;
@@ -200,12 +211,13 @@ struct KrylovVecs {
   long long sv = 0;
   long long part_stride = 0;
   int hist_stride = 0;
+  double stall_cos2 = STALL_COS2, stall_step2 = STALL_STEP2;  // copied into each KState at the start
+  int max_shadow_restarts = MAX_SHADOW_RESTARTS;
 };
 
 // The vectors and state of instance b (host side, for launches that touch a single instance).
 KrylovVecs instance_of(const KrylovVecs& k, int b);
 
-cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s);
 cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s);

@@ -12,7 +12,14 @@
 // kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a 10-node halo:
 //   a colour phase moves information two nodes (a row reads and writes its neighbours), so after
 //   five phases the tile interior holds exactly the sequential sweep's values. Out of place.
+// kacz_cluster_*: the kacz_level_* operations with the level split into row bands over a
+//   thread-block cluster of up to 16 blocks (distributed shared memory, one cluster barrier per
+//   colour), for levels too large for one block or, in FP64, too slow on one SM's FP64 pipe.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
 
 #include "hz_common.cuh"
 #include "hz_internal.h"
@@ -29,42 +36,24 @@ constexpr int KH = 10;    // halo: 2 nodes per colour phase
 constexpr int KR = KT + 2 * KH;
 
 // Row action on row (i, j) of a level whose values sit in shared arrays of row pitch w with
-// origin (gx, gy): all indices are grid indices, translated to shared positions.
+// origin (gx, gy): the row constants come from k H as in the whole-level forms, and the action is
+// lvl::act_at, so a tiled sweep gives the same bits as the whole-level and cluster forms.
 template <class T>
 __device__ __forceinline__ void row_action(c2<T>* su, const c2<T>* sf, const T* sk, int w, int gx, int gy, int i,
                                            int j, int n, T beta) {
-  Nbr b = neighbours(i, j, n);
-  const int c = i - gx, r = j - gy;
-  const int p = r * w + c;
-  const int qw = r * w + (b.iw - gx), qe = r * w + (b.ie - gx), qs = (b.js - gy) * w + c, qn = (b.jn - gy) * w + c;
-  c2<T> d = row_diag<T>(sk[p], b.sides, beta);
-  c2<T> up = su[p];
-  c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(su[qw], su[qe]), cadd<T>(su[qs], su[qn])));
-  c2<T> res = csub<T>(sf[p], au);
-  T cx = (i == 0 || i == n) ? (T)4 : (T)2;
-  T cy = (j == 0 || j == n) ? (T)4 : (T)2;
-  c2<T> delta = cscale<T>(res, rcp(cabs2<T>(d) + cx + cy));
-  su[p] = cadd<T>(up, cmulc<T>(d, delta));
-  su[qw] = cadd<T>(su[qw], delta);
-  su[qe] = cadd<T>(su[qe], delta);
-  su[qs] = cadd<T>(su[qs], delta);
-  su[qn] = cadd<T>(su[qn], delta);
+  const int p = (j - gy) * w + (i - gx);
+  c2<T> d;
+  T inv;
+  lvl::row_consts<T>(sk[p], i, j, n, beta, &d, &inv);
+  lvl::act_at<T>(su, sf[p], d, inv, p, i > 0 ? -1 : 1, i < n ? 1 : -1, j > 0 ? -w : w, j < n ? w : -w);
 }
 
-// The same row action for a node strictly inside the square: neighbours at p +- 1, p +- w, no
-// boundary term, |a_p|^2 = |d|^2 + 4.
+// The same row action for a node strictly inside the square (no mirror, no boundary term).
 template <class T>
 __device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, const T* sk, int w, int p, T beta) {
-  const T k = sk[p], k2 = k * k;
-  const c2<T> d = mk<T>(k2 - (T)4, beta * k2);
-  const c2<T> up = su[p];
-  c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(su[p - 1], su[p + 1]), cadd<T>(su[p - w], su[p + w])));
-  c2<T> delta = cscale<T>(csub<T>(sf[p], au), rcp(cabs2<T>(d) + (T)4));
-  su[p] = cadd<T>(up, cmulc<T>(d, delta));
-  su[p - 1] = cadd<T>(su[p - 1], delta);
-  su[p + 1] = cadd<T>(su[p + 1], delta);
-  su[p - w] = cadd<T>(su[p - w], delta);
-  su[p + w] = cadd<T>(su[p + w], delta);
+  const c2<T> d = xr::diag<T>(sk[p], 0, beta);
+  const T inv = xr::rcp(xr::add(xr::cabs2<T>(d), (T)4));
+  lvl::act_at<T>(su, sf[p], d, inv, p, -1, 1, -w, w);
 }
 
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
@@ -262,6 +251,199 @@ cudaError_t launch_kacz_level_post(bool fp32, void* u, int pu, const void* ec, i
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ whole level in a cluster
+// The level's rows are split into bands over the C blocks of a thread-block cluster (C <= 16),
+// each block holding its band of u, f~, the row diagonals and 1/|a_p|^2 in shared memory. A row
+// action on a band's first or last row reads and updates one node of the neighbouring band
+// through distributed shared memory; rows of one colour have disjoint supports, so no node is
+// touched twice in a colour, and a cluster barrier separates the colours. Same operations as the
+// one-block form (hz_level.cuh), spread over C SMs: for the FP64 form this is C times the FP64
+// rate of one SM on the Kaczmarz level.
+namespace {
+
+namespace cgx = cooperative_groups;
+constexpr int KC_THREADS = 256;
+
+template <class T>
+struct ClusterLevel {
+  c2<T>* su;   // [band][w]
+  c2<T>* sf;
+  c2<T>* sd;
+  T* sinv;
+  c2<T>* sr;   // residual (pre), in place of the diagonals once the sweeps are done
+  int w, n, rows, r0, r1;  // band rows [r0, r1), rows per band
+  __device__ ClusterLevel(unsigned char* smem, int n_, int rows_, int rank) {
+    n = n_;
+    w = n + 1;
+    rows = rows_;
+    r0 = min(rank * rows, n + 1);
+    r1 = min(r0 + rows, w);
+    const int cells = rows * w;
+    su = reinterpret_cast<c2<T>*>(smem);
+    sf = su + cells;
+    sd = sf + cells;
+    sr = sd;
+    sinv = reinterpret_cast<T*>(sd + cells);
+  }
+  // row j of array a (one of su, sr), in whichever block of the cluster owns it
+  __device__ c2<T>* row(cgx::cluster_group& cl, c2<T>* a, int j) const {
+    const int owner = j / rows;
+    c2<T>* base = cl.map_shared_rank(a, owner);
+    return base + (j - owner * rows) * w;
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void cluster_act(cgx::cluster_group& cl, const ClusterLevel<T>& L, int i, int j) {
+  const int n = L.n;
+  const int lr = j - L.r0;
+  c2<T>* rp = L.su + lr * L.w;
+  const int jS = j > 0 ? j - 1 : 1, jN = j < n ? j + 1 : n - 1;
+  c2<T>* rs = (jS >= L.r0 && jS < L.r1) ? L.su + (jS - L.r0) * L.w : L.row(cl, L.su, jS);
+  c2<T>* rn = (jN >= L.r0 && jN < L.r1) ? L.su + (jN - L.r0) * L.w : L.row(cl, L.su, jN);
+  const int iW = i > 0 ? i - 1 : 1, iE = i < n ? i + 1 : n - 1;
+  const int p = lr * L.w + i;
+  lvl::act_nodes<T>(rp + i, rp + iW, rp + iE, rs + i, rn + i, L.sf[p], L.sd[p], L.sinv[p]);
+}
+
+template <class T>
+__device__ void cluster_sweeps(cgx::cluster_group& cl, const ClusterLevel<T>& L, int nu, bool post) {
+  const int M = (L.w + 4) / 5, nrow = L.r1 - L.r0;
+  for (int s = 0; s < nu; ++s)
+    for (int k = 0; k < 5; ++k) {
+      const int colour = post ? 4 - k : k;
+      for (int t = threadIdx.x; t < nrow * M; t += blockDim.x) {
+        const int jl = t / M, m = t - jl * M, j = L.r0 + jl;
+        int i0 = colour + (3 * j) % 5;
+        i0 = i0 >= 5 ? i0 - 5 : i0;
+        const int i = i0 + 5 * m;
+        if (i <= L.n) cluster_act<T>(cl, L, i, j);
+      }
+      cl.sync();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(KC_THREADS) kacz_cluster_pre_kernel(c2<T>* __restrict__ u, int pu,
+                                                                       c2<T>* __restrict__ fc, int pc,
+                                                                       const c2<T>* __restrict__ f, int pf,
+                                                                       const T* __restrict__ kh, int pk, int n, T bA,
+                                                                       T bB, int nu, int rows,
+                                                                       const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;  // the whole cluster (one instance) returns
+  cgx::cluster_group cl = cgx::this_cluster();
+  u += blockIdx.z * bi.su;
+  fc += blockIdx.z * bi.sc;
+  f += blockIdx.z * bi.sf;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ClusterLevel<T> L(smem, n, rows, (int)cl.block_rank());
+  const int w = L.w, cells = (L.r1 - L.r0) * w;
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+    const int j = L.r0 + q / w, i = q % w;
+    L.su[q] = mk<T>(0, 0);
+    L.sf[q] = f[(long long)j * pf + i];
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &L.sd[q], &L.sinv[q]);
+  }
+  cl.sync();
+  cluster_sweeps<T>(cl, L, nu, false);
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+    const int j = L.r0 + q / w, i = q % w;
+    u[(long long)j * pu + i] = L.su[q];
+    const int jS = j > 0 ? j - 1 : 1, jN = j < n ? j + 1 : n - 1;
+    const int iW = i > 0 ? i - 1 : 1, iE = i < n ? i + 1 : n - 1;
+    const c2<T>* rs = L.row(cl, L.su, jS);
+    const c2<T>* rn = L.row(cl, L.su, jN);
+    const c2<T>* rp = L.su + (j - L.r0) * w;
+    const c2<T> nb = xr::nb4<T>(rp[iW], rp[iE], rs[i], rn[i]);
+    L.sr[q] = xr::resid<T>(L.sf[q], L.su[q], nb, xr::diag<T>(kh[(long long)j * pk + i], lvl::sides_at(i, j, n), bB));
+  }
+  cl.sync();
+  // full weighting of the coarse rows whose centre row lies in this band
+  const int wc = n / 2 + 1, J0 = (L.r0 + 1) / 2, J1 = min((L.r1 + 1) / 2, wc);  // 2J in [r0, r1)
+  for (int q = threadIdx.x; q < (J1 - J0) * wc; q += blockDim.x) {
+    const int J = J0 + q / wc, I = q % wc;
+    c2<T> rowsum[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const c2<T>* rr = L.row(cl, L.sr, reflect(2 * J + b - 1, n));
+      rowsum[b] = xr::fw3<T>(rr[reflect(2 * I - 1, n)], rr[2 * I], rr[reflect(2 * I + 1, n)]);
+    }
+    fc[(long long)J * pc + I] = xr::cscale<T>(xr::fw3<T>(rowsum[0], rowsum[1], rowsum[2]), (T)0.25);
+  }
+  cl.sync();  // no block leaves while others may still read its shared memory
+}
+
+template <class T>
+__global__ void __launch_bounds__(KC_THREADS) kacz_cluster_post_kernel(c2<T>* __restrict__ u, int pu,
+                                                                        const c2<T>* __restrict__ ec, int pc,
+                                                                        const c2<T>* __restrict__ f, int pf,
+                                                                        const T* __restrict__ kh, int pk, int n, T bA,
+                                                                        int nu, int rows, const int* __restrict__ stop,
+                                                                        Inst bi) {
+  pdl_enter();
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  cgx::cluster_group cl = cgx::this_cluster();
+  u += blockIdx.z * bi.su;
+  ec += blockIdx.z * bi.sc;
+  f += blockIdx.z * bi.sf;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ClusterLevel<T> L(smem, n, rows, (int)cl.block_rank());
+  const int w = L.w, cells = (L.r1 - L.r0) * w;
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+    const int j = L.r0 + q / w, i = q % w;
+    const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
+    L.su[q] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
+    L.sf[q] = f[(long long)j * pf + i];
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &L.sd[q], &L.sinv[q]);
+  }
+  cl.sync();
+  cluster_sweeps<T>(cl, L, nu, true);
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) u[(long long)(L.r0 + q / w) * pu + q % w] = L.su[q];
+  cl.sync();
+}
+
+template <class T>
+size_t cluster_smem(int n, int rows) {
+  return (size_t)rows * (n + 1) * (3 * sizeof(c2<T>) + sizeof(T));
+}
+
+template <class T>
+cudaError_t cluster_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kacz_cluster_pre_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       KACZ_LEVEL_MAX_SMEM);
+  if (!e) e = cudaFuncSetAttribute(kacz_cluster_post_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   KACZ_LEVEL_MAX_SMEM);
+  if (!e) e = cudaFuncSetAttribute(kacz_cluster_pre_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (!e) e = cudaFuncSetAttribute(kacz_cluster_post_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (!e) done = true;
+  return e;
+}
+
+template <class T, class... Args>
+cudaError_t launch_cluster_kernel(void (*kernel)(Args...), int c, size_t smem, cudaStream_t s, const Inst& bi,
+                                  Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c, 1, bi.count);
+  cfg.blockDim = dim3(KC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
 template <class T, class F2>
 cudaError_t tile_attr() {
   static bool done = false;
@@ -298,6 +480,94 @@ cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* ui
                                                               (const float2*)f, pf, (const float*)kh, pk, n, (float)bA,
                                                               post, stop, bi);
   return cudaGetLastError();
+}
+
+namespace {
+
+// Cluster shape of a level: the most blocks (16, 8, 4 or 2; 16 is beyond the portable cluster
+// size) whose bands fit KACZ_LEVEL_MAX_SMEM and that the device can co-schedule, found once per
+// (precision, n). c = 0: no cluster form for this level.
+struct ClusterShape {
+  int c = 0, rows = 0;
+  size_t smem = 0;
+};
+template <class T>
+ClusterShape cluster_shape(int n) {
+  static std::mutex mu;
+  static std::map<int, ClusterShape> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(n);
+  if (it != cache.end()) return it->second;
+  ClusterShape best;
+  if (!cluster_attr<T>()) {
+    for (int c = 16; c >= 2 && !best.c; c /= 2) {
+      const int rows = (n + 1 + c - 1) / c;
+      const size_t smem = cluster_smem<T>(n, rows);
+      if (smem > (size_t)KACZ_LEVEL_MAX_SMEM) break;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c, 1, 1);
+      cfg.blockDim = dim3(KC_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = c;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      int active = 0;
+      if (cudaOccupancyMaxActiveClusters(&active, kacz_cluster_pre_kernel<T>, &cfg) == cudaSuccess && active > 0 &&
+          cudaOccupancyMaxActiveClusters(&active, kacz_cluster_post_kernel<T>, &cfg) == cudaSuccess && active > 0)
+        best = ClusterShape{c, rows, smem};
+    }
+    cudaGetLastError();  // an unsupported shape leaves no sticky error
+  }
+  cache[n] = best;
+  return best;
+}
+
+}  // namespace
+
+bool kacz_cluster_fits(bool fp32, int n) { return (fp32 ? cluster_shape<float>(n) : cluster_shape<double>(n)).c > 0; }
+
+cudaError_t launch_kacz_cluster_pre(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
+                                    int pk, int n, double bA, double bB, int nu, const int* stop, cudaStream_t s,
+                                    const Inst& bi) {
+  cudaError_t e;
+  if (fp32) {
+    const ClusterShape C = cluster_shape<float>(n);
+    if (!C.c) return cudaErrorInvalidValue;
+    e = launch_cluster_kernel<float>(kacz_cluster_pre_kernel<float>, C.c, C.smem, s, bi, (float2*)u, pu, (float2*)fc,
+                                     pc, (const float2*)f, pf, (const float*)kh, pk, n, (float)bA, (float)bB, nu, C.rows,
+                                     stop, bi);
+  } else {
+    const ClusterShape C = cluster_shape<double>(n);
+    if (!C.c) return cudaErrorInvalidValue;
+    e = launch_cluster_kernel<double>(kacz_cluster_pre_kernel<double>, C.c, C.smem, s, bi, (double2*)u, pu,
+                                      (double2*)fc, pc, (const double2*)f, pf, (const double*)kh, pk, n, bA, bB, nu,
+                                      C.rows, stop, bi);
+  }
+  return e ? e : cudaGetLastError();
+}
+
+cudaError_t launch_kacz_cluster_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
+                                     const void* kh, int pk, int n, double bA, int nu, const int* stop, cudaStream_t s,
+                                     const Inst& bi) {
+  cudaError_t e;
+  if (fp32) {
+    const ClusterShape C = cluster_shape<float>(n);
+    if (!C.c) return cudaErrorInvalidValue;
+    e = launch_cluster_kernel<float>(kacz_cluster_post_kernel<float>, C.c, C.smem, s, bi, (float2*)u, pu,
+                                     (const float2*)ec, pc, (const float2*)f, pf, (const float*)kh, pk, n, (float)bA,
+                                     nu, C.rows, stop, bi);
+  } else {
+    const ClusterShape C = cluster_shape<double>(n);
+    if (!C.c) return cudaErrorInvalidValue;
+    e = launch_cluster_kernel<double>(kacz_cluster_post_kernel<double>, C.c, C.smem, s, bi, (double2*)u, pu,
+                                      (const double2*)ec, pc, (const double2*)f, pf, (const double*)kh, pk, n, bA, nu,
+                                      C.rows, stop, bi);
+  }
+  return e ? e : cudaGetLastError();
 }
 
 }  // namespace hz

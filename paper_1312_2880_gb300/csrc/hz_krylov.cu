@@ -186,14 +186,8 @@ __device__ __forceinline__ double2 shadow_value(unsigned long long seed, long lo
   return make_double2(u[0] - 0.5, u[1] - 0.5);
 }
 
-__global__ void shadow_kernel(double2* rhat, long long N, unsigned long long seed) {
-  pdl_enter();
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    rhat[p] = shadow_value(seed, p);
-  }
-}
-
-// x = 0, r = h^2 b, p = v = 0; |r|^2 and <r^, r> start the iteration.
+// x = 0, r = h^2 b, p = v = 0, r^ = the first shadow residual (a restart in an earlier solve may
+// have renewed it, and every solve starts from the same one); |r|^2 and <r^, r> start the iteration.
 __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap) {
   pdl_enter();
   k = instance(k);
@@ -202,7 +196,8 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
   GRID_STRIDE(e, N) {
     double2 bv = k.b[e];
     double2 r = make_double2(bv.x * k.scale_b, bv.y * k.scale_b);
-    double2 rh = k.rhat[e];
+    const double2 rh = shadow_value(SHADOW_SEED, e);
+    k.rhat[e] = rh;
     k.r[e] = r;
     k.x[e] = make_double2(0, 0);
     k.p[e] = make_double2(0, 0);
@@ -236,6 +231,9 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
     st->rhat2 = tot[3];
     st->min_cos2 = 1.0;
     st->min_step2 = 1.0;
+    st->stall_cos2 = k.stall_cos2;
+    st->stall_step2 = k.stall_step2;
+    st->max_shadow_restarts = k.max_shadow_restarts;
     if (!fin(tot[0]) || !fin(tot[1]) || !fin(tot[2])) st->done = 3;
     else if (tot[0] == 0.0) st->done = 1;
     else if (tot[1] == 0.0 && tot[2] == 0.0) st->done = 2;
@@ -461,8 +459,8 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
       const double cos2 = (rho_new.x * rho_new.x + rho_new.y * rho_new.y) / (st->rhat2 * tot[2]);
       st->min_cos2 = fmin(st->min_cos2, cos2);
       const double step2 = (omega.x * omega.x + omega.y * omega.y) * st->tt / tot[2];
-      if (cos2 < STALL_COS2) st->min_step2 = fmin(st->min_step2, step2);
-      if (cos2 < STALL_COS2 && step2 < STALL_STEP2 && st->shadow_restarts < MAX_SHADOW_RESTARTS) {
+      if (cos2 < st->stall_cos2) st->min_step2 = fmin(st->min_step2, step2);
+      if (cos2 < st->stall_cos2 && step2 < st->stall_step2 && st->shadow_restarts < st->max_shadow_restarts) {
         // <r^, r> has collapsed relative to |r^| |r| and the iteration no longer moves r: the
         // recurrences stall (alpha, omega -> 0) unless the shadow residual is renewed; the next
         // direction update restarts from r.
@@ -569,10 +567,6 @@ KrylovVecs instance_of(const KrylovVecs& k, int b) {
   return r;
 }
 
-cudaError_t launch_shadow(double2* rhat, long long N, unsigned long long seed, cudaStream_t s) {
-  pdl_launch(shadow_kernel, 1024, 256, 0, s, rhat, N, seed);
-  return cudaGetLastError();
-}
 cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_cap, cudaStream_t s) {
   pdl_launch(k_init_kernel, KGRID, KB, 0, s, k, tol, maxit, hist_cap);
   return cudaGetLastError();

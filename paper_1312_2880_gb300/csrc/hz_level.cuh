@@ -23,30 +23,41 @@ __device__ __forceinline__ void row_consts(T kh, int i, int j, int n, T beta, c2
   *inv = xr::rcp(xr::add(xr::cabs2<T>(*d), cx + cy));
 }
 
-// Row action u += conj(a_p) (f_p - a_p u) / |a_p|^2 on row (i, j): the five values are read once
-// and written once. A mirror neighbour across the boundary is the same node on both sides
-// (coefficient 2 in the row), so it receives 2 delta in one update.
+// Row action u += conj(a_p) (f_p - a_p u) / |a_p|^2 on the node at up with its neighbours at
+// uw, ue, us, un (a mirror neighbour across the boundary is the same node on both sides, so its
+// two pointers coincide and it receives 2 delta in one update). The five values are read once and
+// written once. Every Kaczmarz kernel form goes through this function, so they give the same bits.
+template <class T>
+__device__ __forceinline__ void act_nodes(c2<T>* pp, c2<T>* pw, c2<T>* pe, c2<T>* ps, c2<T>* pn, c2<T> f, c2<T> d,
+                                          T inv) {
+  const c2<T> up = *pp, uw = *pw, ue = *pe, us = *ps, un = *pn;
+  const c2<T> delta = xr::cscale<T>(xr::resid<T>(f, up, xr::nb4<T>(uw, ue, us, un), d), inv);
+  *pp = xr::cadd<T>(up, xr::cmulc<T>(d, delta));
+  if (pw == pe) {
+    *pw = xr::cadd<T>(uw, xr::cscale<T>(delta, (T)2));
+  } else {
+    *pw = xr::cadd<T>(uw, delta);
+    *pe = xr::cadd<T>(ue, delta);
+  }
+  if (ps == pn) {
+    *ps = xr::cadd<T>(us, xr::cscale<T>(delta, (T)2));
+  } else {
+    *ps = xr::cadd<T>(us, delta);
+    *pn = xr::cadd<T>(un, delta);
+  }
+}
+// The same at shared position p with neighbour offsets dw, de, ds, dn.
+template <class T>
+__device__ __forceinline__ void act_at(c2<T>* su, c2<T> f, c2<T> d, T inv, int p, int dw, int de, int ds, int dn) {
+  act_nodes<T>(su + p, su + p + dw, su + p + de, su + p + ds, su + p + dn, f, d, inv);
+}
+
+// Row action on row (i, j) of a level stored whole with row pitch w.
 template <class T>
 __device__ __forceinline__ void act(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int i, int j,
                                     int n) {
   const int p = j * w + i;
-  const int dw = i > 0 ? -1 : 1, de = i < n ? 1 : -1, ds = j > 0 ? -w : w, dn = j < n ? w : -w;
-  const c2<T> d = sd[p];
-  const c2<T> up = su[p], uw = su[p + dw], ue = su[p + de], us = su[p + ds], un = su[p + dn];
-  const c2<T> delta = xr::cscale<T>(xr::resid<T>(sf[p], up, xr::nb4<T>(uw, ue, us, un), d), sinv[p]);
-  su[p] = xr::cadd<T>(up, xr::cmulc<T>(d, delta));
-  if (dw == de) {
-    su[p + dw] = xr::cadd<T>(uw, xr::cscale<T>(delta, (T)2));
-  } else {
-    su[p + dw] = xr::cadd<T>(uw, delta);
-    su[p + de] = xr::cadd<T>(ue, delta);
-  }
-  if (ds == dn) {
-    su[p + ds] = xr::cadd<T>(us, xr::cscale<T>(delta, (T)2));
-  } else {
-    su[p + ds] = xr::cadd<T>(us, delta);
-    su[p + dn] = xr::cadd<T>(un, delta);
-  }
+  act_at<T>(su, sf[p], sd[p], sinv[p], p, i > 0 ? -1 : 1, i < n ? 1 : -1, j > 0 ? -w : w, j < n ? w : -w);
 }
 
 // Thread -> row of a colour (i + 2j) mod 5: grid row j holds the colour at i = i0(j) + 5m,

@@ -70,8 +70,8 @@ __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restr
 
 // One colour of a row-action Kaczmarz sweep on A u = f (Gauss-Seidel on A A^H y = f with
 // u = A^H y): for each row p of colour (i + 2j) % 5, delta = (f~_p - (A u)_p) / |a_p|^2 and
-// u_q += conj(a_pq) delta over the row's support. Mirror neighbours at the boundary carry
-// coefficient 2 (they appear twice in the index list and receive delta twice).
+// u_q += conj(a_pq) delta over the row's support (lvl::act_nodes, the row action of every
+// Kaczmarz form). A mirror neighbour at the boundary carries coefficient 2 and receives 2 delta.
 template <class T, class F2>
 __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
                                    const T* __restrict__ kh, int pk, int n, int colour, T beta,
@@ -85,22 +85,13 @@ __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __re
   if (j > n) return;
   int i = ((colour - 2 * j) % 5 + 5) % 5 + 5 * m;
   if (i > n) return;
-  Nbr b = neighbours(i, j, n);
-  long long p = (long long)j * pu + i;
-  c2<T> d = row_diag<T>(kh[(long long)j * pk + i], b.sides, beta);
-  c2<T> up = u[p];
-  c2<T> au = cadd<T>(cmul<T>(d, up), cadd<T>(cadd<T>(u[(long long)j * pu + b.iw], u[(long long)j * pu + b.ie]),
-                                            cadd<T>(u[(long long)b.js * pu + i], u[(long long)b.jn * pu + i])));
-  c2<T> r = csub<T>(ldc<T>(f, (long long)j * pf + i), au);
-  T cx = (i == 0 || i == n) ? (T)4 : (T)2;
-  T cy = (j == 0 || j == n) ? (T)4 : (T)2;
-  c2<T> delta = cscale<T>(r, rcp(cabs2<T>(d) + cx + cy));
-  u[p] = cadd<T>(up, cmulc<T>(d, delta));
-  long long q;
-  q = (long long)j * pu + b.iw; u[q] = cadd<T>(u[q], delta);
-  q = (long long)j * pu + b.ie; u[q] = cadd<T>(u[q], delta);
-  q = (long long)b.js * pu + i; u[q] = cadd<T>(u[q], delta);
-  q = (long long)b.jn * pu + i; u[q] = cadd<T>(u[q], delta);
+  const Nbr b = neighbours(i, j, n);
+  c2<T> d;
+  T inv;
+  lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, beta, &d, &inv);
+  c2<T>* row = u + (long long)j * pu;
+  lvl::act_nodes<T>(row + i, row + b.iw, row + b.ie, u + (long long)b.js * pu + i, u + (long long)b.jn * pu + i,
+                    ldc<T>(f, (long long)j * pf + i), d, inv);
 }
 
 // ---------------------------------------------------------------- transfers (Sec. 5)
@@ -121,24 +112,24 @@ __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   int nc = n / 2;
   if (I > nc || J > nc) return;
-  c2<T> acc = mk<T>(0, 0);
+  // the same operations and order as the whole-level forms (lvl::residual, xr::fw_node)
+  c2<T> rows[3];
 #pragma unroll
-  for (int bj = -1; bj <= 1; ++bj) {
-    int j = reflect(2 * J + bj, n);
-    c2<T> row = mk<T>(0, 0);
+  for (int b = 0; b < 3; ++b) {
+    const int j = reflect(2 * J + b - 1, n);
+    c2<T> r[3];
 #pragma unroll
-    for (int ai = -1; ai <= 1; ++ai) {
-      int i = reflect(2 * I + ai, n);
-      Nbr b = neighbours(i, j, n);
-      c2<T> au = cadd<T>(cmul<T>(row_diag<T>(kh[(long long)j * pk + i], b.sides, beta), u[(long long)j * pu + i]),
-                         cadd<T>(cadd<T>(u[(long long)j * pu + b.iw], u[(long long)j * pu + b.ie]),
-                                 cadd<T>(u[(long long)b.js * pu + i], u[(long long)b.jn * pu + i])));
-      c2<T> r = csub<T>(ldc<T>(f, (long long)j * pf + i), au);
-      row = cadd<T>(row, ai == 0 ? cscale<T>(r, (T)2) : r);
+    for (int a = 0; a < 3; ++a) {
+      const int i = reflect(2 * I + a - 1, n);
+      const Nbr nb = neighbours(i, j, n);
+      const c2<T>* row = u + (long long)j * pu;
+      r[a] = xr::resid<T>(ldc<T>(f, (long long)j * pf + i), row[i],
+                          xr::nb4<T>(row[nb.iw], row[nb.ie], u[(long long)nb.js * pu + i], u[(long long)nb.jn * pu + i]),
+                          xr::diag<T>(kh[(long long)j * pk + i], lvl::sides_at(i, j, n), beta));
     }
-    acc = cadd<T>(acc, bj == 0 ? cscale<T>(row, (T)2) : row);
+    rows[b] = xr::fw3<T>(r[0], r[1], r[2]);
   }
-  fc[(long long)J * pc + I] = cscale<T>(acc, (T)0.25);
+  fc[(long long)J * pc + I] = xr::cscale<T>(xr::fw3<T>(rows[0], rows[1], rows[2]), (T)0.25);
 }
 
 // u += P e_c, bilinear interpolation from the (n/2+1)^2 grid.
@@ -152,16 +143,9 @@ __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* _
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
-  int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
-  c2<T> e = ec[(long long)J * pc + I];
-  if (oi) e = cadd<T>(e, ec[(long long)J * pc + I + 1]);
-  if (oj) {
-    e = cadd<T>(e, ec[(long long)(J + 1) * pc + I]);
-    if (oi) e = cadd<T>(e, ec[(long long)(J + 1) * pc + I + 1]);
-  }
-  T w = (oi && oj) ? (T)0.25 : ((oi || oj) ? (T)0.5 : (T)1);
-  long long p = (long long)j * pu + i;
-  u[p] = cadd<T>(u[p], cscale<T>(e, w));
+  const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
+  const long long p = (long long)j * pu + i;
+  u[p] = xr::cadd<T>(u[p], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
 }
 
 // ---------------------------------------------------------------- coarsest grid

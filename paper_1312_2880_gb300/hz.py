@@ -33,12 +33,13 @@ class HzError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
                 ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int),
-                ("pass_variant", c_int), ("coarse_tail", c_int)]
+                ("pass_variant", c_int), ("coarse_tail", c_int), ("kacz_form", c_int)]
 
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", c_int), ("H", c_double), ("relax_op", c_int), ("smoother", c_int), ("resid_op", c_int),
-                ("nu", c_int), ("pass_down", c_int), ("pass_up", c_int), ("in_tail", c_int)]
+                ("nu", c_int), ("pass_down", c_int), ("pass_up", c_int), ("in_tail", c_int),
+                ("kacz_form", c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
         "hz_profile_iteration": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
         "hz_profile_graph": (c_int, [P, c_void_p, c_void_p, c_int, POINTER(KernelTime), c_int]),
         "hz_krylov_scalars": (c_int, [P, c_int, POINTER(c_double)]),
+        "hz_set_stall_detection": (c_int, [P, c_double, c_double, c_int]),
         "hz_kernel_name": (ctypes.c_char_p, [c_int]),
         "hz_last_error": (ctypes.c_char_p, [P]),
         "hz_status_string": (ctypes.c_char_p, [c_int]),
@@ -120,16 +122,22 @@ def _ptr(t) -> c_void_p:
     return c_void_p(t.data_ptr())
 
 
+KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3}
+
+
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
-              pass_variant=-1, coarse_tail=True) -> Opts:
+              pass_variant=-1, coarse_tail=True, kacz_form="auto") -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
-    memory tiles; 1..6 = register streaming with 2**(v+2) rows per warp (FP32 form)."""
+    memory tiles; 1..6 = register streaming with 2**(v+2) rows per warp (FP32 form).
+    kacz_form: kernel form of the Kaczmarz levels below the finest (one of KACZ_FORMS); a form that
+    does not apply to a level falls back to the default."""
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
     o.nu_gs, o.nu_kacz, o.guard, o.k_ref, o.batch = nu_gs, nu_kacz, int(bool(guard)), float(k_ref), int(batch)
     o.pass_variant = int(pass_variant)
     o.coarse_tail = int(bool(coarse_tail))
+    o.kacz_form = KACZ_FORMS[kacz_form]
     return o
 
 
@@ -141,7 +149,8 @@ def _level_dict(li: LevelInfo) -> dict:
     inv = {v: k for k, v in OPS.items()}
     return {"n": li.n, "H": li.H, "relax_op": inv[li.relax_op], "smoother": SMOOTHERS[li.smoother],
             "resid_op": inv[li.resid_op], "nu": li.nu, "pass_down": li.pass_down, "pass_up": li.pass_up,
-            "in_tail": bool(li.in_tail)}
+            "in_tail": bool(li.in_tail),
+            "kacz_form": {v: k for k, v in KACZ_FORMS.items()}.get(li.kacz_form) if li.kacz_form >= 0 else None}
 
 
 def describe_hierarchy(n: int, kfield, beta: float = 0.5, **opts) -> list:
@@ -171,7 +180,8 @@ class Problem:
     """
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
-                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1, coarse_tail=True):
+                 nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1, coarse_tail=True,
+                 kacz_form="auto"):
         import torch
 
         L = lib()
@@ -185,7 +195,7 @@ class Problem:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
         self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant,
-                              coarse_tail)
+                              coarse_tail, kacz_form)
         self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
@@ -320,6 +330,10 @@ class Problem:
         if cnt < 0:
             raise HzError(HZ_ECUDA, lib().hz_last_error(self._h).decode())
         return [(lib().hz_kernel_name(out[q].kernel).decode(), out[q].level, float(out[q].ms)) for q in range(min(cnt, cap))]
+
+    def set_stall_detection(self, cos2: float = 1e-12, step2: float = 1e-8, max_restarts: int = 16):
+        """Near-breakdown thresholds of the following solves (hz_set_stall_detection)."""
+        self._check(lib().hz_set_stall_detection(self._h, float(cos2), float(step2), int(max_restarts)))
 
     def krylov_scalars(self, instance: int = 0) -> dict:
         """Bi-CGSTAB scalars of an instance after the last solve (diagnostics)."""

@@ -307,3 +307,66 @@ def test_invalid_arguments():
     assert e.value.status == hz.HZ_EINVAL
     with pytest.raises(hz.HzError):
         P.level_presmooth(P.num_levels - 1, b)
+
+
+@pytest.mark.slow
+def test_formerly_stalled_fp32_solve_converges():
+    """n = 1024 wedge, k = 0.2 n, source at (302, 48): an FP32-form solve that once froze at
+    relres 0.38 (rho and the omega step collapsing together) while the FP64 form converged in 374
+    iterations. Whether it stalls depends on the last bit of the FP32 V-cycle; with the
+    near-breakdown restart it converges either way."""
+    hz = hzmod()
+    n, k = 1024, 0.2 * 1024
+    kf = I.wedge_k(n, k, I.SEED_BASE + 1001)
+    rhs = np.zeros((n + 1, n + 1), dtype=np.complex128)
+    rhs[48, 302] = n * n
+    P = hz.Problem(n, kf, 0.5, variant="hyb", precision="fp32", k_ref=k)
+    x, info, _ = P.solve(dev(rhs), tol=1e-6, maxit=3000)
+    P.close()
+    assert info["status"] == 0 and info["relres_true"] <= 1e-6
+    assert info["iterations"] < 1500
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_forced_shadow_restarts_keep_the_solve_correct(precision):
+    """Thresholds that every iteration meets force a shadow-residual renewal after each of the first
+    iterations, up to the cap: the solve must still reach the tolerance on the true residual and
+    report the renewals; with the cap at 0 none happens and the solve equals the default one."""
+    hz = hzmod()
+    wl = small_wedge()
+    P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=precision, levels=wl.levels, k_ref=wl.k_ref)
+    try:
+        x0, info0, _ = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+        P.set_stall_detection(2.0, 1e300, 5)
+        x1, info1, _ = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+        sc1 = P.krylov_scalars()
+        P.set_stall_detection(2.0, 1e300, 0)
+        x2, info2, _ = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+        sc2 = P.krylov_scalars()
+        with pytest.raises(hz.HzError):
+            P.set_stall_detection(-1.0, 1e-8, 4)
+        with pytest.raises(hz.HzError):
+            P.set_stall_detection(1e-12, float("nan"), 4)
+        with pytest.raises(hz.HzError):
+            P.set_stall_detection(1e-12, 1e-8, -1)
+    finally:
+        P.close()
+    assert sc1["shadow_restarts"] == 5 and info1["status"] == 0 and info1["relres_true"] <= 1e-6
+    assert info1["restarts"] >= 5
+    assert sc2["shadow_restarts"] == 0
+    assert info2["iterations"] == info0["iterations"]
+    assert np.array_equal(x2.cpu().numpy().view(np.uint64), x0.cpu().numpy().view(np.uint64))
+    A = o.helmholtz_matrix(wl.n, wl.kfield, 0.0)
+    assert o.true_relres(A, wl.rhs.ravel(), x1.cpu().numpy().ravel()) <= 1e-6
+
+
+def test_converging_solves_never_restart_the_shadow_residual():
+    hz = hzmod()
+    for wl in (I.plain_n64(), small_wedge()):
+        for prec in ("fp32", "fp64"):
+            P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
+            _, info, _ = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+            sc = P.krylov_scalars()
+            P.close()
+            assert sc["shadow_restarts"] == 0 and info["restarts"] == 0
+            assert sc["min_step2"] > 1e-6 or sc["min_cos2"] >= 1e-12

@@ -1,9 +1,9 @@
 """The one-block coarse tail: the smallest levels of the V-cycle in one launch.
 
-With the tail the V-cycle must give the same bits as without it in the FP32 form (the tail and
-the per-level kernels take the same fixed-rounding operations for one-sweep Gauss-Seidel levels
-and for whole-level Kaczmarz), and stay within the FP64 step tolerance of the oracle in the FP64
-form (where the per-level Kaczmarz kernels run colour by colour with other rounding). Cases: all
+With the tail the V-cycle must give the same bits as without it (the tail and the per-level
+kernels take the same fixed-rounding operations for one-sweep Gauss-Seidel levels and for every
+Kaczmarz form), in FP32 and FP64, and the FP64 tail stays within the V-cycle tolerance of the
+oracle. Cases: all
 Gauss-Seidel levels (plain n = 64), a Kaczmarz level inside the tail (wedge n = 256, k = 50:
 kH = 1.56 on the n = 32 level), batches, and the tail's level flags.
 """
@@ -56,12 +56,13 @@ def vcycle(wl, precision, tail, r, batch=1):
     return z, sched
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_fp32_tail_is_bitwise_the_per_level_cycle(name):
+def test_tail_is_bitwise_the_per_level_cycle(name, precision):
     wl = CASES[name]()
     r = rand_c((wl.n + 1) ** 2, 95)
-    z1, s1 = vcycle(wl, "fp32", True, r)
-    z0, s0 = vcycle(wl, "fp32", False, r)
+    z1, s1 = vcycle(wl, precision, True, r)
+    z0, s0 = vcycle(wl, precision, False, r)
     tail = [l for l, d in enumerate(s1) if d["in_tail"]]
     assert tail and tail[-1] == len(s1) - 1 and tail[0] >= 1, tail
     assert not any(d["in_tail"] for d in s0)
