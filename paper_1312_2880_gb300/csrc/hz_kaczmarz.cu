@@ -59,7 +59,8 @@ __device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, con
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
 
 // ------------------------------------------------------------------ whole level in one block
-// Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node.
+// Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node, each
+// array colour-planar (lvl::Planar, N = lvl::planar_cells(n) cells).
 template <class T>
 struct LevelSmem {
   c2<T>* su;
@@ -85,20 +86,24 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
   fc += blockIdx.z * bi.sc;
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = n + 1, N = w * w;
-  LevelSmem<T> S(smem, N);
+  const int w = n + 1, N = w * w, Np = lvl::planar_cells(n);
+  const lvl::Planar lay = lvl::planar(n);
+  LevelSmem<T> S(smem, Np);
+  for (int q = threadIdx.x; q < Np; q += LB) S.su[q] = mk<T>(0, 0);
   for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    S.su[q] = mk<T>(0, 0);
-    S.sf[q] = f[(long long)j * pf + i];
-    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
+    const int j = q / w, i = q - j * w, p = lay.at(i, j);
+    S.sf[p] = f[(long long)j * pf + i];
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
   }
   __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
-  for (int q = threadIdx.x; q < N; q += LB) u[(long long)(q / w) * pu + q % w] = S.su[q];
-  lvl::residual<T>(S.sd, S.su, S.sf, kh, pk, n, bB);  // the residual replaces the diagonals
+  for (int q = threadIdx.x; q < N; q += LB) {
+    const int j = q / w, i = q - j * w;
+    u[(long long)j * pu + i] = S.su[lay.at(i, j)];
+  }
+  lvl::residual<T>(S.sd, S.su, S.sf, lay, kh, pk, n, bB);  // the residual (natural) replaces the diagonals
   __syncthreads();
-  lvl::restrict_fw<T>(fc, pc, S.sd, n);
+  lvl::restrict_fw<T>(fc, lvl::Natural{pc}, S.sd, n);
 }
 
 template <class T>
@@ -114,17 +119,21 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = n + 1, N = w * w;
-  LevelSmem<T> S(smem, N);
+  const lvl::Planar lay = lvl::planar(n);
+  LevelSmem<T> S(smem, lvl::planar_cells(n));
   for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
+    const int j = q / w, i = q - j * w, p = lay.at(i, j);
     const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
-    S.su[q] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
-    S.sf[q] = f[(long long)j * pf + i];
-    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[q], &S.sinv[q]);
+    S.su[p] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
+    S.sf[p] = f[(long long)j * pf + i];
+    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
   }
   __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
-  for (int q = threadIdx.x; q < N; q += LB) u[(long long)(q / w) * pu + q % w] = S.su[q];
+  for (int q = threadIdx.x; q < N; q += LB) {
+    const int j = q / w, i = q - j * w;
+    u[(long long)j * pu + i] = S.su[lay.at(i, j)];
+  }
 }
 
 template <class T, class F2>
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
 
 template <class T>
 size_t level_smem(int n) {
-  return (size_t)(n + 1) * (n + 1) * (3 * sizeof(c2<T>) + sizeof(T));
+  return (size_t)lvl::planar_cells(n) * (3 * sizeof(c2<T>) + sizeof(T));
 }
 
 template <class T>

@@ -1,4 +1,5 @@
-// Whole-level operations on a small grid held in one block's shared memory (row pitch n + 1):
+// Whole-level operations on a small grid held in one block's shared memory (natural row-major
+// storage, or colour-planar for Kaczmarz levels):
 // Kaczmarz row actions over the five colours, one red-black Gauss-Seidel sweep each way, the
 // residual, full weighting, bilinear correction and the coarsest dense solve. They run with all
 // threads of the block striding over the nodes and a barrier between dependent phases, and use
@@ -12,6 +13,24 @@ namespace hz {
 namespace lvl {
 
 __device__ __forceinline__ int sides_at(int i, int j, int n) { return (i == 0) + (i == n) + (j == 0) + (j == n); }
+
+// ------------------------------------------------------------------ storage of a level
+// Natural: row-major with pitch w. Planar (Kaczmarz levels): the nodes of colour
+// c = (i + 2j) mod 5 in grid row j are contiguous, at ((c w + j) M + i div 5) with M = ceil(w / 5)
+// (node (i, j) has i mod 5 = (c + 3j) mod 5). A colour phase then reads and writes every array
+// with unit stride across the threads of a warp instead of stride 5 across grid rows (which cost
+// ~1.7 extra shared-memory wavefronts per access), and 5 w M >= w^2 cells hold the level.
+struct Natural {
+  int w;
+  __device__ __forceinline__ int at(int i, int j) const { return j * w + i; }
+};
+struct Planar {
+  int w, M;
+  __device__ __forceinline__ int at(int i, int j) const { return (((i + 2 * j) % 5) * w + j) * M + i / 5; }
+};
+__host__ __device__ __forceinline__ int planar_cols(int n) { return (n + 5) / 5; }
+__host__ __device__ __forceinline__ int planar_cells(int n) { return 5 * (n + 1) * planar_cols(n); }
+__device__ __forceinline__ Planar planar(int n) { return Planar{n + 1, planar_cols(n)}; }
 
 // ------------------------------------------------------------------ Kaczmarz (Sec. 4)
 // Row constants: the diagonal d_p of the relaxation operator and 1 / |a_p|^2 (|d_p|^2 plus the
@@ -52,54 +71,48 @@ __device__ __forceinline__ void act_at(c2<T>* su, c2<T> f, c2<T> d, T inv, int p
   act_nodes<T>(su + p, su + p + dw, su + p + de, su + p + ds, su + p + dn, f, d, inv);
 }
 
-// Row action on row (i, j) of a level stored whole with row pitch w.
+// Row action of colour c on a Planar level, thread slot t = (j, m) = (t div M, t mod M): the node
+// (i, j) with i = (c + 3j) mod 5 + 5m (b = 3j mod 5), planar index c w M + t. Its west and east
+// neighbours have colours c - 1 and c + 1 in the same row (column m, or m -+ 1 where i mod 5 is
+// 0 or 4), south and north colours c - 2 and c + 2 in rows j -+ 1, column m; at the boundary the
+// mirror neighbour is the node on the other side.
 template <class T>
-__device__ __forceinline__ void act(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int w, int i, int j,
-                                    int n) {
-  const int p = j * w + i;
-  act_at<T>(su, sf[p], sd[p], sinv[p], p, i > 0 ? -1 : 1, i < n ? 1 : -1, j > 0 ? -w : w, j < n ? w : -w);
-}
-
-// Thread -> row of a colour (i + 2j) mod 5: grid row j holds the colour at i = i0(j) + 5m,
-// m < M = ceil((n+1)/5), i0 = (colour + 3j) mod 5; slot t is (j, m) = (t / M, t % M). Rows of one
-// colour have disjoint supports, so a colour is one set of independent row actions.
-struct ColourSlot {
-  int j, m, b;  // b = 3j mod 5
-};
-__device__ __forceinline__ ColourSlot colour_slot(int t, int M) {
-  ColourSlot c;
-  c.j = t / M;
-  c.m = t - c.j * M;
-  c.b = (3 * c.j) % 5;
-  return c;
-}
-template <class T>
-__device__ __forceinline__ void act_slot(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n,
-                                         int colour, const ColourSlot& cs) {
-  int i0 = colour + cs.b;
+__device__ __forceinline__ void act_planar(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n, int M,
+                                           int c, int t, int j, int m, int b) {
+  int i0 = c + b;
   i0 = i0 >= 5 ? i0 - 5 : i0;
-  const int i = i0 + 5 * cs.m;
-  if (i > n || cs.j > n) return;
-  act<T>(su, sf, sd, sinv, n + 1, i, cs.j, n);
+  const int i = i0 + 5 * m;
+  if (i > n) return;
+  const int plane = (n + 1) * M, row = j * M + m;
+  const int cw = c == 0 ? 4 : c - 1, ce = c == 4 ? 0 : c + 1, cs = c >= 2 ? c - 2 : c + 3, cn = c <= 2 ? c + 2 : c - 3;
+  const int p = c * plane + t;
+  const int pw = cw * plane + row - (i0 == 0), pe = ce * plane + row + (i0 == 4);
+  const int ps = cs * plane + row - M, pn = cn * plane + row + M;
+  act_nodes<T>(su + p, su + (i == 0 ? pe : pw), su + (i == n ? pw : pe), su + (j == 0 ? pn : ps),
+               su + (j == n ? ps : pn), sf[p], sd[p], sinv[p]);
 }
 
-// nu Kaczmarz sweeps over the colours 0..4 (or 4..0 when `post`), a barrier after each colour.
+// nu Kaczmarz sweeps over the colours 0..4 (or 4..0 when `post`) on a Planar level, a barrier
+// after each colour. Rows of one colour have disjoint supports, so a colour is one set of
+// independent row actions.
 template <class T>
 __device__ __forceinline__ void kacz_sweeps(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n, int nu,
                                             bool post) {
-  const int w = n + 1, M = (w + 4) / 5;
-  if (w * M <= (int)blockDim.x) {
-    const ColourSlot cs = colour_slot(threadIdx.x, M);
+  const int M = planar_cols(n), S = (n + 1) * M;
+  if (S <= (int)blockDim.x) {
+    const int t = threadIdx.x, j = t / M, m = t - j * M, b = (3 * j) % 5;
     for (int s = 0; s < nu; ++s)
       for (int k = 0; k < 5; ++k) {
-        act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, cs);
+        if (t < S) act_planar<T>(su, sf, sd, sinv, n, M, post ? 4 - k : k, t, j, m, b);
         __syncthreads();
       }
   } else {
     for (int s = 0; s < nu; ++s)
       for (int k = 0; k < 5; ++k) {
-        for (int t = threadIdx.x; t < w * M; t += blockDim.x)
-          act_slot<T>(su, sf, sd, sinv, n, post ? 4 - k : k, colour_slot(t, M));
+        for (int t = threadIdx.x; t < S; t += blockDim.x) {
+          const int j = t / M;
+          act_planar<T>(su, sf, sd, sinv, n, M, post ? 4 - k : k, t, j, t - j * M, (3 * j) % 5);
+        }
         __syncthreads();
       }
   }
@@ -151,32 +164,49 @@ __device__ __forceinline__ void gs_post(c2<T>* u, const c2<T>* f, const T* k, in
 }
 
 // ------------------------------------------------------------------ residual and transfers
-// r = f~ - B u, with k H from `k` (pitch pk; shared or global).
-template <class T>
-__device__ __forceinline__ void residual(c2<T>* r, const c2<T>* u, const c2<T>* f, const T* k, int pk, int n, T bB) {
+// r (natural, pitch n + 1) = f~ - B u, u and f~ stored with layout lu, k H from `k` (pitch pk;
+// shared or global).
+template <class T, class LU>
+__device__ __forceinline__ void residual(c2<T>* r, const c2<T>* u, const c2<T>* f, LU lu, const T* k, int pk, int n,
+                                         T bB) {
   const int w = n + 1, N = w * w;
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     const int j = q / w, i = q - j * w;
-    r[q] = xr::resid<T>(f[q], u[q], nb_at<T>(u, i, j, n), xr::diag<T>(k[(long long)j * pk + i], sides_at(i, j, n), bB));
+    const Nbr b = neighbours(i, j, n);
+    const int p = lu.at(i, j);
+    r[q] = xr::resid<T>(f[p], u[p], xr::nb4<T>(u[lu.at(b.iw, j)], u[lu.at(b.ie, j)], u[lu.at(i, b.js)], u[lu.at(i, b.jn)]),
+                        xr::diag<T>(k[(long long)j * pk + i], sides_at(i, j, n), bB));
   }
 }
-// fc (pitch pc) = full weighting of r onto the (n/2 + 1)^2 grid.
-template <class T>
-__device__ __forceinline__ void restrict_fw(c2<T>* fc, int pc, const c2<T>* r, int n) {
+// fc (layout lc) = full weighting of r (natural) onto the (n/2 + 1)^2 grid.
+template <class T, class LC>
+__device__ __forceinline__ void restrict_fw(c2<T>* fc, LC lc, const c2<T>* r, int n) {
   const int wc = n / 2 + 1;
   for (int q = threadIdx.x; q < wc * wc; q += blockDim.x) {
     const int J = q / wc, I = q - J * wc;
-    fc[(long long)J * pc + I] = xr::fw_node<T>(r, n + 1, n, I, J);
+    fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J);
   }
 }
-// u += P e (e: (n/2 + 1)^2 grid, pitch pe).
-template <class T>
-__device__ __forceinline__ void prolong_add(c2<T>* u, const c2<T>* e, int pe, int n) {
+// Bilinear interpolation of e (layout le) at fine node (2I + oi, 2J + oj), in the operation order
+// of xr::bilinear.
+template <class T, class LE>
+__device__ __forceinline__ c2<T> bilinear_at(const c2<T>* e, LE le, int I, int J, int oi, int oj) {
+  if (oi && oj)
+    return xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]),
+                                     xr::cadd<T>(e[le.at(I + 1, J)], e[le.at(I + 1, J + 1)])),
+                         (T)0.25);
+  if (oi) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I + 1, J)]), (T)0.5);
+  if (oj) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]), (T)0.5);
+  return e[le.at(I, J)];
+}
+// u (layout lu) += P e (e: (n/2 + 1)^2 grid, layout le).
+template <class T, class LU, class LE>
+__device__ __forceinline__ void prolong_add(c2<T>* u, LU lu, const c2<T>* e, LE le, int n) {
   const int w = n + 1, N = w * w;
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     const int j = q / w, i = q - j * w;
-    const c2<T>* e0 = e + (long long)(j >> 1) * pe;
-    u[q] = xr::cadd<T>(u[q], xr::bilinear<T>(e0, e0 + pe, i >> 1, i & 1, j & 1));
+    const int p = lu.at(i, j);
+    u[p] = xr::cadd<T>(u[p], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
   }
 }
 // Row r of the coarsest solve u = A^-1 f (inverse stored transposed, m x m).

@@ -4,8 +4,8 @@
 // on the way up. Below a few thousand nodes a level's kernels are bound by launch and ramp
 // latency, not by work, so this replaces 2 (L - lt) - 1 launches by one. Each level's operations
 // are the ones the per-level kernels perform (hz_level.cuh, fixed-rounding arithmetic), so the
-// result is bitwise the same as without the tail wherever those kernels use the same forms
-// (one-sweep Gauss-Seidel levels, whole-level Kaczmarz in FP32).
+// result is bitwise the same as without the tail (one-sweep Gauss-Seidel levels and every
+// Kaczmarz form).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,22 +35,33 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   c2<T>* R = reinterpret_cast<c2<T>*>(smem + A.off_r);
   const int last = A.count - 1;
 
+  // Kaczmarz levels are stored colour-planar, the others row-major (lvl::Natural, lvl::Planar)
+  auto with_layout = [&](int l, auto&& fn) {
+    const int nl = A.lv[l].n;
+    if (A.lv[l].kind == TAIL_KACZ)
+      fn(lvl::planar(nl));
+    else
+      fn(lvl::Natural{nl + 1});
+  };
+
   // right-hand side of the first level; k H (Gauss-Seidel) or row constants (Kaczmarz) of every
   // relaxation level; zero guess of the Kaczmarz levels
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
     const int w = L.n + 1, N = w * w;
     const T* kh = reinterpret_cast<const T*>(L.kh);
-    for (int q = threadIdx.x; q < N; q += TAIL_THREADS) {
-      const int j = q / w, i = q - j * w;
-      if (l == 0) F(0)[q] = fin[(long long)j * A.pf + i];
-      if (L.kind == TAIL_GS) {
-        K(l)[q] = kh[(long long)j * L.pk + i];
-      } else {
-        lvl::row_consts<T>(kh[(long long)j * L.pk + i], i, j, L.n, (T)L.bA, &D(l)[q], &V(l)[q]);
-        U(l)[q] = mk<T>(0, 0);
+    if (L.kind == TAIL_KACZ)
+      for (int q = threadIdx.x; q < lvl::planar_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
+    with_layout(l, [&](auto lay) {
+      for (int q = threadIdx.x; q < N; q += TAIL_THREADS) {
+        const int j = q / w, i = q - j * w, p = lay.at(i, j);
+        if (l == 0) F(0)[p] = fin[(long long)j * A.pf + i];
+        if (L.kind == TAIL_GS)
+          K(l)[q] = kh[(long long)j * L.pk + i];
+        else
+          lvl::row_consts<T>(kh[(long long)j * L.pk + i], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
       }
-    }
+    });
   }
   __syncthreads();
 
@@ -59,13 +70,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
     const TailLevel& L = A.lv[l];
     if (L.kind == TAIL_GS) {
       lvl::gs_pre<T>(U(l), F(l), K(l), L.n, (T)L.bA);
-      lvl::residual<T>(R, U(l), F(l), K(l), L.n + 1, L.n, (T)L.bB);
+      lvl::residual<T>(R, U(l), F(l), lvl::Natural{L.n + 1}, K(l), L.n + 1, L.n, (T)L.bB);
     } else {
       lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, false);
-      lvl::residual<T>(R, U(l), F(l), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
+      lvl::residual<T>(R, U(l), F(l), lvl::planar(L.n), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
     }
     __syncthreads();
-    lvl::restrict_fw<T>(F(l + 1), A.lv[l + 1].n + 1, R, L.n);
+    with_layout(l + 1, [&](auto lc) { lvl::restrict_fw<T>(F(l + 1), lc, R, L.n); });
     __syncthreads();
   }
 
@@ -80,7 +91,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   // up: bilinear correction, relaxation in the reverse order
   for (int l = last - 1; l >= 0; --l) {
     const TailLevel& L = A.lv[l];
-    lvl::prolong_add<T>(U(l), U(l + 1), A.lv[l + 1].n + 1, L.n);
+    with_layout(l, [&](auto lu) {
+      with_layout(l + 1, [&](auto le) { lvl::prolong_add<T>(U(l), lu, U(l + 1), le, L.n); });
+    });
     __syncthreads();
     if (L.kind == TAIL_GS)
       lvl::gs_post<T>(U(l), F(l), K(l), L.n, (T)L.bA);
@@ -89,7 +102,12 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   }
 
   const int w = A.lv[0].n + 1;
-  for (int q = threadIdx.x; q < w * w; q += TAIL_THREADS) uout[(long long)(q / w) * A.po + q % w] = U(0)[q];
+  with_layout(0, [&](auto lay) {
+    for (int q = threadIdx.x; q < w * w; q += TAIL_THREADS) {
+      const int j = q / w, i = q - j * w;
+      uout[(long long)j * A.po + i] = U(0)[lay.at(i, j)];
+    }
+  });
 }
 
 }  // namespace
@@ -104,7 +122,8 @@ size_t tail_layout(bool fp32, TailArgs* A) {
   };
   for (int l = 0; l < A->count; ++l) {
     TailLevel& L = A->lv[l];
-    const size_t N = (size_t)(L.n + 1) * (L.n + 1);
+    const size_t Nn = (size_t)(L.n + 1) * (L.n + 1);
+    const size_t N = L.kind == TAIL_KACZ ? (size_t)lvl::planar_cells(L.n) : Nn;  // cells of u, f~, d, 1/|a|^2
     L.off_u = take(N * c);
     L.off_f = take(N * c);
     L.off_k = L.off_d = L.off_inv = 0;
@@ -113,7 +132,7 @@ size_t tail_layout(bool fp32, TailArgs* A) {
       L.off_d = take(N * c);
       L.off_inv = take(N * r);
     }
-    if (L.kind != TAIL_COARSE) rmax = std::max(rmax, N);
+    if (L.kind != TAIL_COARSE) rmax = std::max(rmax, Nn);
   }
   A->off_r = take(rmax * c);
   return off;
