@@ -60,7 +60,7 @@ __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
 
 // ------------------------------------------------------------------ whole level in one block
 // Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node, each
-// array colour-planar (lvl::Planar, N = lvl::planar_cells(n) cells).
+// array colour-blocked (lvl::Blocked, N = lvl::blocked_cells(n) cells).
 template <class T>
 struct LevelSmem {
   c2<T>* su;
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
   fc += blockIdx.z * bi.sc;
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = n + 1, N = w * w, Np = lvl::planar_cells(n);
-  const lvl::Planar lay = lvl::planar(n);
+  const int w = n + 1, N = w * w, Np = lvl::blocked_cells(n);
+  const lvl::Blocked lay = lvl::blocked(n);
   LevelSmem<T> S(smem, Np);
   for (int q = threadIdx.x; q < Np; q += LB) S.su[q] = mk<T>(0, 0);
   for (int q = threadIdx.x; q < N; q += LB) {
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = n + 1, N = w * w;
-  const lvl::Planar lay = lvl::planar(n);
-  LevelSmem<T> S(smem, lvl::planar_cells(n));
+  const lvl::Blocked lay = lvl::blocked(n);
+  LevelSmem<T> S(smem, lvl::blocked_cells(n));
   for (int q = threadIdx.x; q < N; q += LB) {
     const int j = q / w, i = q - j * w, p = lay.at(i, j);
     const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
 
 template <class T>
 size_t level_smem(int n) {
-  return (size_t)lvl::planar_cells(n) * (3 * sizeof(c2<T>) + sizeof(T));
+  return (size_t)lvl::blocked_cells(n) * (3 * sizeof(c2<T>) + sizeof(T));
 }
 
 template <class T>

@@ -1,5 +1,5 @@
-// Whole-level operations on a small grid held in one block's shared memory (natural row-major
-// storage, or colour-planar for Kaczmarz levels):
+// Whole-level operations on a small grid held in one block's shared memory (row-major storage,
+// or colour-blocked for Kaczmarz levels):
 // Kaczmarz row actions over the five colours, one red-black Gauss-Seidel sweep each way, the
 // residual, full weighting, bilinear correction and the coarsest dense solve. They run with all
 // threads of the block striding over the nodes and a barrier between dependent phases, and use
@@ -15,22 +15,61 @@ namespace lvl {
 __device__ __forceinline__ int sides_at(int i, int j, int n) { return (i == 0) + (i == n) + (j == 0) + (j == n); }
 
 // ------------------------------------------------------------------ storage of a level
-// Natural: row-major with pitch w. Planar (Kaczmarz levels): the nodes of colour
-// c = (i + 2j) mod 5 in grid row j are contiguous, at ((c w + j) M + i div 5) with M = ceil(w / 5)
-// (node (i, j) has i mod 5 = (c + 3j) mod 5). A colour phase then reads and writes every array
-// with unit stride across the threads of a warp instead of stride 5 across grid rows (which cost
-// ~1.7 extra shared-memory wavefronts per access), and 5 w M >= w^2 cells hold the level.
+// Natural: row-major with pitch w. Blocked (Kaczmarz levels): the five nodes i = 5m .. 5m + 4 of
+// grid row j form slot t = j M + m (M = ceil(w / 5)) of five cells, each node in the cell of its
+// colour c = (i + 2j) mod 5: node (i, j) at 5 (j M + i div 5) + (i + 2j) mod 5; 5 w M >= w^2
+// cells hold the level. In a colour phase thread t acts on the node of that colour in slot t:
+// consecutive threads touch cells 5 apart (no shared-memory bank conflicts, where row-major
+// storage cost ~1.7 extra wavefronts per access), and the neighbours lie at fixed cell offsets
+// from the slot, so a phase needs almost no index arithmetic.
 struct Natural {
   int w;
   __device__ __forceinline__ int at(int i, int j) const { return j * w + i; }
 };
-struct Planar {
-  int w, M;
-  __device__ __forceinline__ int at(int i, int j) const { return (((i + 2 * j) % 5) * w + j) * M + i / 5; }
+struct Blocked {
+  int M;
+  __device__ __forceinline__ int at(int i, int j) const { return 5 * (j * M + i / 5) + (i + 2 * j) % 5; }
 };
-__host__ __device__ __forceinline__ int planar_cols(int n) { return (n + 5) / 5; }
-__host__ __device__ __forceinline__ int planar_cells(int n) { return 5 * (n + 1) * planar_cols(n); }
-__device__ __forceinline__ Planar planar(int n) { return Planar{n + 1, planar_cols(n)}; }
+__host__ __device__ __forceinline__ int blocked_cols(int n) { return (n + 5) / 5; }
+__host__ __device__ __forceinline__ int blocked_cells(int n) { return 5 * (n + 1) * blocked_cols(n); }
+__device__ __forceinline__ Blocked blocked(int n) { return Blocked{blocked_cols(n)}; }
+
+// Asynchronous global -> shared copy of one element of B = 4, 8 or 16 bytes (cp.async); the
+// copies in flight complete at cp_async_wait_all.
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else if constexpr (B == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Calls fn(q, i, j) for q = threadIdx.x, threadIdx.x + blockDim.x, ... < count with
+// (i, j) = (q mod w, q div w), advanced without a division per step. Threads without a node
+// leave at once: on the small levels most warps of the block have none, and their setup would
+// otherwise take issue slots from the warps that do.
+template <class F>
+__device__ __forceinline__ void for_nodes(int w, int count, F&& fn) {
+  if ((int)threadIdx.x >= count) return;
+  const int step = blockDim.x, dj = step / w, di = step - dj * w;
+  int j = threadIdx.x / w, i = threadIdx.x - j * w;
+  for (int q = threadIdx.x; q < count; q += step) {
+    fn(q, i, j);
+    i += di;
+    j += dj;
+    if (i >= w) {
+      i -= w;
+      ++j;
+    }
+  }
+}
 
 // ------------------------------------------------------------------ Kaczmarz (Sec. 4)
 // Row constants: the diagonal d_p of the relaxation operator and 1 / |a_p|^2 (|d_p|^2 plus the
@@ -71,50 +110,74 @@ __device__ __forceinline__ void act_at(c2<T>* su, c2<T> f, c2<T> d, T inv, int p
   act_nodes<T>(su + p, su + p + dw, su + p + de, su + p + ds, su + p + dn, f, d, inv);
 }
 
-// Row action of colour c on a Planar level, thread slot t = (j, m) = (t div M, t mod M): the node
-// (i, j) with i = (c + 3j) mod 5 + 5m (b = 3j mod 5), planar index c w M + t. Its west and east
-// neighbours have colours c - 1 and c + 1 in the same row (column m, or m -+ 1 where i mod 5 is
-// 0 or 4), south and north colours c - 2 and c + 2 in rows j -+ 1, column m; at the boundary the
-// mirror neighbour is the node on the other side.
-template <class T>
-__device__ __forceinline__ void act_planar(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n, int M,
-                                           int c, int t, int j, int m, int b) {
-  int i0 = c + b;
-  i0 = i0 >= 5 ? i0 - 5 : i0;
-  const int i = i0 + 5 * m;
-  if (i > n) return;
-  const int plane = (n + 1) * M, row = j * M + m;
-  const int cw = c == 0 ? 4 : c - 1, ce = c == 4 ? 0 : c + 1, cs = c >= 2 ? c - 2 : c + 3, cn = c <= 2 ? c + 2 : c - 3;
-  const int p = c * plane + t;
-  const int pw = cw * plane + row - (i0 == 0), pe = ce * plane + row + (i0 == 4);
-  const int ps = cs * plane + row - M, pn = cn * plane + row + M;
-  act_nodes<T>(su + p, su + (i == 0 ? pe : pw), su + (i == n ? pw : pe), su + (j == 0 ? pn : ps),
-               su + (j == n ? ps : pn), sf[p], sd[p], sinv[p]);
+// A thread's slot t = (j, m) of a Blocked Kaczmarz level: the first cell of the slot (o = 5t) and
+// of the slots one grid row down and up (for j = 0 and j = n the mirror row 1 or n - 1 stands in
+// for the missing one), and b = 3j mod 5 (the node of colour c in the slot is
+// i = 5m + (c + b) mod 5).
+struct KaczSlot {
+  int o, os, on, m, b, n;
+  bool j0, jn;
+};
+__device__ __forceinline__ KaczSlot kacz_slot(int n, int t) {
+  const int M = blocked_cols(n), j = t / M;
+  KaczSlot s;
+  s.o = 5 * t;
+  s.on = 5 * (j < n ? t + M : t - M);
+  s.os = 5 * (j > 0 ? t - M : t + M);
+  s.m = t - j * M;
+  s.b = (3 * j) % 5;
+  s.n = n;
+  s.j0 = j == 0;
+  s.jn = j == n;
+  return s;
 }
-
-// nu Kaczmarz sweeps over the colours 0..4 (or 4..0 when `post`) on a Planar level, a barrier
+// Cell offsets of colour c's neighbours within a slot: west c - 1, east c + 1, south c - 2,
+// north c + 2 (mod 5), the same for every thread of a phase.
+struct ColourOffsets {
+  int c, cw, ce, cs, cn;
+  __device__ __forceinline__ explicit ColourOffsets(int c_)
+      : c(c_), cw(c_ == 0 ? 4 : c_ - 1), ce(c_ == 4 ? 0 : c_ + 1), cs(c_ >= 2 ? c_ - 2 : c_ + 3),
+        cn(c_ <= 2 ? c_ + 2 : c_ - 3) {}
+};
+// Row action of colour k.c in slot s: the west neighbour lies in the slot before when the node
+// starts its block, the east one in the next slot when it ends it, south and north one grid row
+// away; at the boundary the mirror neighbour is the node on the other side.
+template <class T>
+__device__ __forceinline__ void act_slot(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv,
+                                         const KaczSlot& s, const ColourOffsets& k) {
+  int i0 = k.c + s.b;
+  i0 = i0 >= 5 ? i0 - 5 : i0;
+  const int i = i0 + 5 * s.m;
+  if (i > s.n) return;
+  const int w = s.o + k.cw - (i0 == 0 ? 5 : 0), e = s.o + k.ce + (i0 == 4 ? 5 : 0);
+  const int so = s.j0 ? s.on + k.cn : s.os + k.cs, no = s.jn ? s.os + k.cs : s.on + k.cn;
+  const int p = s.o + k.c;
+  act_nodes<T>(su + p, su + (i == 0 ? e : w), su + (i == s.n ? w : e), su + so, su + no, sf[p], sd[p], sinv[p]);
+}
+// nu Kaczmarz sweeps over the colours 0..4 (or 4..0 when `post`) on a Blocked level, a barrier
 // after each colour. Rows of one colour have disjoint supports, so a colour is one set of
 // independent row actions.
 template <class T>
 __device__ __forceinline__ void kacz_sweeps(c2<T>* su, const c2<T>* sf, const c2<T>* sd, const T* sinv, int n, int nu,
                                             bool post) {
-  const int M = planar_cols(n), S = (n + 1) * M;
-  if (S <= (int)blockDim.x) {
-    const int t = threadIdx.x, j = t / M, m = t - j * M, b = (3 * j) % 5;
-    for (int s = 0; s < nu; ++s)
-      for (int k = 0; k < 5; ++k) {
-        if (t < S) act_planar<T>(su, sf, sd, sinv, n, M, post ? 4 - k : k, t, j, m, b);
-        __syncthreads();
-      }
+  const int S = (n + 1) * blocked_cols(n);
+  if (S <= (int)blockDim.x) {  // one slot per thread, set up once
+    const bool act = threadIdx.x < (unsigned)S;
+    const KaczSlot s = kacz_slot(n, act ? threadIdx.x : 0);
+#pragma unroll 1
+    for (int q = 0; q < 5 * nu; ++q) {
+      const int r = q % 5;
+      if (act) act_slot<T>(su, sf, sd, sinv, s, ColourOffsets(post ? 4 - r : r));
+      __syncthreads();
+    }
   } else {
-    for (int s = 0; s < nu; ++s)
-      for (int k = 0; k < 5; ++k) {
-        for (int t = threadIdx.x; t < S; t += blockDim.x) {
-          const int j = t / M;
-          act_planar<T>(su, sf, sd, sinv, n, M, post ? 4 - k : k, t, j, t - j * M, (3 * j) % 5);
-        }
-        __syncthreads();
-      }
+#pragma unroll 1
+    for (int q = 0; q < 5 * nu; ++q) {
+      const int r = q % 5;
+      const ColourOffsets k(post ? 4 - r : r);
+      for (int t = threadIdx.x; t < S; t += blockDim.x) act_slot<T>(su, sf, sd, sinv, kacz_slot(n, t), k);
+      __syncthreads();
+    }
   }
 }
 
@@ -123,10 +186,10 @@ __device__ __forceinline__ void kacz_sweeps(c2<T>* su, const c2<T>* sf, const c2
 template <class T, class F>
 __device__ __forceinline__ void for_colour(int n, int colour, F&& fn) {
   const int w = n + 1, HW = (w + 1) / 2;
-  for (int q = threadIdx.x; q < w * HW; q += blockDim.x) {
-    const int j = q / HW, i = 2 * (q - j * HW) + ((colour + j) & 1);
+  for_nodes(HW, w * HW, [&](int, int h, int j) {
+    const int i = 2 * h + ((colour + j) & 1);
     if (i <= n) fn(i, j);
-  }
+  });
 }
 template <class T>
 __device__ __forceinline__ c2<T> nb_at(const c2<T>* u, int i, int j, int n) {
@@ -169,23 +232,19 @@ __device__ __forceinline__ void gs_post(c2<T>* u, const c2<T>* f, const T* k, in
 template <class T, class LU>
 __device__ __forceinline__ void residual(c2<T>* r, const c2<T>* u, const c2<T>* f, LU lu, const T* k, int pk, int n,
                                          T bB) {
-  const int w = n + 1, N = w * w;
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
-    const int j = q / w, i = q - j * w;
+  const int w = n + 1;
+  for_nodes(w, w * w, [&](int q, int i, int j) {
     const Nbr b = neighbours(i, j, n);
     const int p = lu.at(i, j);
     r[q] = xr::resid<T>(f[p], u[p], xr::nb4<T>(u[lu.at(b.iw, j)], u[lu.at(b.ie, j)], u[lu.at(i, b.js)], u[lu.at(i, b.jn)]),
                         xr::diag<T>(k[(long long)j * pk + i], sides_at(i, j, n), bB));
-  }
+  });
 }
 // fc (layout lc) = full weighting of r (natural) onto the (n/2 + 1)^2 grid.
 template <class T, class LC>
 __device__ __forceinline__ void restrict_fw(c2<T>* fc, LC lc, const c2<T>* r, int n) {
   const int wc = n / 2 + 1;
-  for (int q = threadIdx.x; q < wc * wc; q += blockDim.x) {
-    const int J = q / wc, I = q - J * wc;
-    fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J);
-  }
+  for_nodes(wc, wc * wc, [&](int, int I, int J) { fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J); });
 }
 // Bilinear interpolation of e (layout le) at fine node (2I + oi, 2J + oj), in the operation order
 // of xr::bilinear.
@@ -202,18 +261,28 @@ __device__ __forceinline__ c2<T> bilinear_at(const c2<T>* e, LE le, int I, int J
 // u (layout lu) += P e (e: (n/2 + 1)^2 grid, layout le).
 template <class T, class LU, class LE>
 __device__ __forceinline__ void prolong_add(c2<T>* u, LU lu, const c2<T>* e, LE le, int n) {
-  const int w = n + 1, N = w * w;
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
-    const int j = q / w, i = q - j * w;
+  const int w = n + 1;
+  for_nodes(w, w * w, [&](int, int i, int j) {
     const int p = lu.at(i, j);
     u[p] = xr::cadd<T>(u[p], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
-  }
+  });
 }
-// Row r of the coarsest solve u = A^-1 f (inverse stored transposed, m x m).
+// Row r of the coarsest solve u = A^-1 f (inverse stored transposed, m x m), accumulated in column
+// order. The inverse is read from global memory eight columns at a time before they are summed,
+// so eight loads are in flight instead of one.
 template <class T>
 __device__ __forceinline__ c2<T> coarse_row(const c2<T>* __restrict__ ainvT, const c2<T>* f, int m, int r) {
+  constexpr int B = 8;
   c2<T> acc = mk<T>(0, 0);
-  for (int c = 0; c < m; ++c) acc = xr::cadd<T>(acc, xr::cmul<T>(ainvT[(long long)c * m + r], f[c]));
+  int c = 0;
+  for (; c + B <= m; c += B) {
+    c2<T> a[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) a[q] = ainvT[(long long)(c + q) * m + r];
+#pragma unroll
+    for (int q = 0; q < B; ++q) acc = xr::cadd<T>(acc, xr::cmul<T>(a[q], f[c + q]));
+  }
+  for (; c < m; ++c) acc = xr::cadd<T>(acc, xr::cmul<T>(ainvT[(long long)c * m + r], f[c]));
   return acc;
 }
 

@@ -35,32 +35,43 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   c2<T>* R = reinterpret_cast<c2<T>*>(smem + A.off_r);
   const int last = A.count - 1;
 
-  // Kaczmarz levels are stored colour-planar, the others row-major (lvl::Natural, lvl::Planar)
+  // Kaczmarz levels are stored colour-blocked, the others row-major (lvl::Natural, lvl::Blocked)
   auto with_layout = [&](int l, auto&& fn) {
     const int nl = A.lv[l].n;
     if (A.lv[l].kind == TAIL_KACZ)
-      fn(lvl::planar(nl));
+      fn(lvl::blocked(nl));
     else
       fn(lvl::Natural{nl + 1});
   };
 
-  // right-hand side of the first level; k H (Gauss-Seidel) or row constants (Kaczmarz) of every
-  // relaxation level; zero guess of the Kaczmarz levels
+  // Right-hand side of the first level and k H of every relaxation level, all copied at once
+  // (cp.async, one wait for all of them): k H into K(l) on Gauss-Seidel levels, into the cells of
+  // 1/|a|^2 on Kaczmarz levels, where the row constants replace it below; zero guess of the
+  // Kaczmarz levels.
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
-    const int w = L.n + 1, N = w * w;
+    const int w = L.n + 1;
     const T* kh = reinterpret_cast<const T*>(L.kh);
     if (L.kind == TAIL_KACZ)
-      for (int q = threadIdx.x; q < lvl::planar_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
+      for (int q = threadIdx.x; q < lvl::blocked_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
     with_layout(l, [&](auto lay) {
-      for (int q = threadIdx.x; q < N; q += TAIL_THREADS) {
-        const int j = q / w, i = q - j * w, p = lay.at(i, j);
-        if (l == 0) F(0)[p] = fin[(long long)j * A.pf + i];
-        if (L.kind == TAIL_GS)
-          K(l)[q] = kh[(long long)j * L.pk + i];
-        else
-          lvl::row_consts<T>(kh[(long long)j * L.pk + i], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
-      }
+      lvl::for_nodes(w, w * w, [&](int q, int i, int j) {
+        const int p = lay.at(i, j);
+        lvl::cp_async<sizeof(T)>(L.kind == TAIL_GS ? &K(l)[q] : &V(l)[p], kh + (long long)j * L.pk + i);
+        if (l == 0) lvl::cp_async<sizeof(c2<T>)>(&F(0)[p], fin + (long long)j * A.pf + i);
+      });
+    });
+  }
+  lvl::cp_async_wait_all();
+  __syncthreads();
+  for (int l = 0; l < last; ++l) {
+    const TailLevel& L = A.lv[l];
+    if (L.kind != TAIL_KACZ) continue;
+    const int w = L.n + 1;
+    const lvl::Blocked lay = lvl::blocked(L.n);
+    lvl::for_nodes(w, w * w, [&](int, int i, int j) {
+      const int p = lay.at(i, j);
+      lvl::row_consts<T>(V(l)[p], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
     });
   }
   __syncthreads();
@@ -73,7 +84,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
       lvl::residual<T>(R, U(l), F(l), lvl::Natural{L.n + 1}, K(l), L.n + 1, L.n, (T)L.bB);
     } else {
       lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, false);
-      lvl::residual<T>(R, U(l), F(l), lvl::planar(L.n), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
+      lvl::residual<T>(R, U(l), F(l), lvl::blocked(L.n), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
     }
     __syncthreads();
     with_layout(l + 1, [&](auto lc) { lvl::restrict_fw<T>(F(l + 1), lc, R, L.n); });
@@ -103,10 +114,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
 
   const int w = A.lv[0].n + 1;
   with_layout(0, [&](auto lay) {
-    for (int q = threadIdx.x; q < w * w; q += TAIL_THREADS) {
-      const int j = q / w, i = q - j * w;
-      uout[(long long)j * A.po + i] = U(0)[lay.at(i, j)];
-    }
+    lvl::for_nodes(w, w * w, [&](int, int i, int j) { uout[(long long)j * A.po + i] = U(0)[lay.at(i, j)]; });
   });
 }
 
@@ -123,7 +131,7 @@ size_t tail_layout(bool fp32, TailArgs* A) {
   for (int l = 0; l < A->count; ++l) {
     TailLevel& L = A->lv[l];
     const size_t Nn = (size_t)(L.n + 1) * (L.n + 1);
-    const size_t N = L.kind == TAIL_KACZ ? (size_t)lvl::planar_cells(L.n) : Nn;  // cells of u, f~, d, 1/|a|^2
+    const size_t N = L.kind == TAIL_KACZ ? (size_t)lvl::blocked_cells(L.n) : Nn;  // cells of u, f~, d, 1/|a|^2
     L.off_u = take(N * c);
     L.off_f = take(N * c);
     L.off_k = L.off_d = L.off_inv = 0;
