@@ -86,22 +86,17 @@ __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ 
   fc += blockIdx.z * bi.sc;
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = n + 1, N = w * w, Np = lvl::blocked_cells(n);
-  const lvl::Blocked lay = lvl::blocked(n);
+  const int Np = lvl::blocked_cells(n);
   LevelSmem<T> S(smem, Np);
   for (int q = threadIdx.x; q < Np; q += LB) S.su[q] = mk<T>(0, 0);
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w, p = lay.at(i, j);
+  lvl::for_blocked(n, [&](int i, int j, int p) {
     S.sf[p] = f[(long long)j * pf + i];
     lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
-  }
+  });
   __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = S.su[lay.at(i, j)];
-  }
-  lvl::residual<T>(S.sd, S.su, S.sf, lay, kh, pk, n, bB);  // the residual (natural) replaces the diagonals
+  lvl::for_blocked(n, [&](int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
+  lvl::residual_blocked<T>(S.sd, S.su, S.sf, kh, pk, n, bB);  // the residual (natural) replaces the diagonals
   __syncthreads();
   lvl::restrict_fw<T>(fc, lvl::Natural{pc}, S.sd, n);
 }
@@ -118,22 +113,16 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   ec += blockIdx.z * bi.sc;
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = n + 1, N = w * w;
-  const lvl::Blocked lay = lvl::blocked(n);
   LevelSmem<T> S(smem, lvl::blocked_cells(n));
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w, p = lay.at(i, j);
+  lvl::for_blocked(n, [&](int i, int j, int p) {
     const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
     S.su[p] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
     S.sf[p] = f[(long long)j * pf + i];
     lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
-  }
+  });
   __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
-  for (int q = threadIdx.x; q < N; q += LB) {
-    const int j = q / w, i = q - j * w;
-    u[(long long)j * pu + i] = S.su[lay.at(i, j)];
-  }
+  lvl::for_blocked(n, [&](int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
 }
 
 template <class T, class F2>

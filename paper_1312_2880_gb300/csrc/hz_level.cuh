@@ -23,10 +23,12 @@ __device__ __forceinline__ int sides_at(int i, int j, int n) { return (i == 0) +
 // storage cost ~1.7 extra wavefronts per access), and the neighbours lie at fixed cell offsets
 // from the slot, so a phase needs almost no index arithmetic.
 struct Natural {
+  static constexpr bool blocked = false;
   int w;
   __device__ __forceinline__ int at(int i, int j) const { return j * w + i; }
 };
 struct Blocked {
+  static constexpr bool blocked = true;
   int M;
   __device__ __forceinline__ int at(int i, int j) const { return 5 * (j * M + i / 5) + (i + 2 * j) % 5; }
 };
@@ -110,6 +112,30 @@ __device__ __forceinline__ void act_at(c2<T>* su, c2<T> f, c2<T> d, T inv, int p
   act_nodes<T>(su + p, su + p + dw, su + p + de, su + p + ds, su + p + dn, f, d, inv);
 }
 
+// Calls fn(i, j, p) for every node (i, j) of a Blocked level with its cell p, slot by slot: slot
+// t = (j, m) holds the nodes i = 5m .. 5m + 4, node i = 5m + r in cell 5t + (r + 2j) mod 5. No
+// per-node division or modulo.
+template <class F>
+__device__ __forceinline__ void for_blocked(int n, F&& fn) {
+  const int M = blocked_cols(n), S = (n + 1) * M;
+  if ((int)threadIdx.x >= S) return;
+  const int dj = blockDim.x / M, dm = blockDim.x - dj * M;
+  int j = threadIdx.x / M, m = threadIdx.x - j * M;
+  for (int t = threadIdx.x; t < S; t += blockDim.x) {
+    int c = (2 * j) % 5;
+    for (int i = 5 * m; i <= min(5 * m + 4, n); ++i) {
+      fn(i, j, 5 * t + c);
+      c = c == 4 ? 0 : c + 1;
+    }
+    m += dm;
+    j += dj;
+    if (m >= M) {
+      m -= M;
+      ++j;
+    }
+  }
+}
+
 // A thread's slot t = (j, m) of a Blocked Kaczmarz level: the first cell of the slot (o = 5t) and
 // of the slots one grid row down and up (for j = 0 and j = n the mirror row 1 or n - 1 stands in
 // for the missing one), and b = 3j mod 5 (the node of colour c in the slot is
@@ -181,6 +207,18 @@ __device__ __forceinline__ void kacz_sweeps(c2<T>* su, const c2<T>* sf, const c2
   }
 }
 
+// Bilinear interpolation of e (layout le) at fine node (2I + oi, 2J + oj), in the operation order
+// of xr::bilinear.
+template <class T, class LE>
+__device__ __forceinline__ c2<T> bilinear_at(const c2<T>* e, LE le, int I, int J, int oi, int oj) {
+  if (oi && oj)
+    return xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]),
+                                     xr::cadd<T>(e[le.at(I + 1, J)], e[le.at(I + 1, J + 1)])),
+                         (T)0.25);
+  if (oi) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I + 1, J)]), (T)0.5);
+  if (oj) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]), (T)0.5);
+  return e[le.at(I, J)];
+}
 // ------------------------------------------------------------------ Gauss-Seidel (one sweep)
 // The nodes of colour c ((i + j) mod 2 == c): slot q is (j, i) = (q / HW, 2 (q % HW) + (c + j) mod 2).
 template <class T, class F>
@@ -197,16 +235,57 @@ __device__ __forceinline__ c2<T> nb_at(const c2<T>* u, int i, int j, int n) {
   const int w = n + 1;
   return xr::nb4<T>(u[j * w + b.iw], u[j * w + b.ie], u[b.js * w + i], u[b.jn * w + i]);
 }
-// Red nodes from a zero guess (u = f~ / d), then black nodes.
+// Red node of the pre-sweep from a zero guess: u = f~ / d.
 template <class T>
-__device__ __forceinline__ void gs_pre(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
+__device__ __forceinline__ c2<T> gs_red_zero(c2<T> f, T k, int i, int j, int n, T bA) {
+  return xr::cdiv<T>(f, xr::diag<T>(k, sides_at(i, j, n), bA));
+}
+// Red nodes from a zero guess, no barrier (the caller's next barrier ends the phase).
+template <class T>
+__device__ __forceinline__ void gs_red(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
   const int w = n + 1;
   for_colour<T>(n, 0, [&](int i, int j) {
     const int p = j * w + i;
-    u[p] = xr::cdiv<T>(f[p], xr::diag<T>(k[p], sides_at(i, j, n), bA));
+    u[p] = gs_red_zero<T>(f[p], k[p], i, j, n, bA);
+  });
+}
+// Black nodes from their red neighbours, then a barrier.
+template <class T>
+__device__ __forceinline__ void gs_black(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
+  const int w = n + 1;
+  for_colour<T>(n, 1, [&](int i, int j) {
+    const int p = j * w + i;
+    u[p] = xr::gs<T>(f[p], nb_at<T>(u, i, j, n), xr::diag<T>(k[p], sides_at(i, j, n), bA));
   });
   __syncthreads();
+}
+// Red nodes from a zero guess, then black nodes.
+template <class T>
+__device__ __forceinline__ void gs_pre(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
+  gs_red<T>(u, f, k, n, bA);
+  __syncthreads();
+  gs_black<T>(u, f, k, n, bA);
+}
+// Correction u += P e (e: layout le) and the post-sweep, black nodes then red, in two phases. A
+// Gauss-Seidel update does not read the node's own value, so the corrected values are needed
+// only at red nodes, as neighbours of the black update: the black phase forms them on the fly
+// (the same cadd of u and the bilinear value that a separate correction pass would store) and
+// the red phase reads the new black values. Same results as correction, then gs_post.
+template <class T, class LE>
+__device__ __forceinline__ void gs_post_corrected(c2<T>* u, const c2<T>* f, const T* k, int n, T bA, const c2<T>* e,
+                                                  LE le) {
+  const int w = n + 1;
+  auto corrected = [&](int i, int j) {
+    return xr::cadd<T>(u[j * w + i], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
+  };
   for_colour<T>(n, 1, [&](int i, int j) {
+    const Nbr b = neighbours(i, j, n);
+    const int p = j * w + i;
+    const c2<T> nb = xr::nb4<T>(corrected(b.iw, j), corrected(b.ie, j), corrected(i, b.js), corrected(i, b.jn));
+    u[p] = xr::gs<T>(f[p], nb, xr::diag<T>(k[p], sides_at(i, j, n), bA));
+  });
+  __syncthreads();
+  for_colour<T>(n, 0, [&](int i, int j) {
     const int p = j * w + i;
     u[p] = xr::gs<T>(f[p], nb_at<T>(u, i, j, n), xr::diag<T>(k[p], sides_at(i, j, n), bA));
   });
@@ -240,32 +319,55 @@ __device__ __forceinline__ void residual(c2<T>* r, const c2<T>* u, const c2<T>* 
                         xr::diag<T>(k[(long long)j * pk + i], sides_at(i, j, n), bB));
   });
 }
+// The same residual for u and f~ stored Blocked, visited slot by slot: the neighbours' cells
+// follow from the node's colour c and position r = i mod 5 in its slot (west c - 1 in this slot,
+// or the one before when r = 0; east c + 1, or the next slot when r = 4; south c - 2 and north
+// c + 2 one grid row away), mirrored at the boundary.
+template <class T>
+__device__ __forceinline__ void residual_blocked(c2<T>* r, const c2<T>* u, const c2<T>* f, const T* k, int pk, int n,
+                                                 T bB) {
+  const int w = n + 1, M5 = 5 * blocked_cols(n);
+  for_blocked(n, [&](int i, int j, int p) {
+    const int c = p % 5, t5 = p - c, ri = i % 5;
+    const int cw = c == 0 ? 4 : c - 1, ce = c == 4 ? 0 : c + 1, cs = c >= 2 ? c - 2 : c + 3, cn = c <= 2 ? c + 2 : c - 3;
+    const int pw = (ri > 0 ? t5 : t5 - 5) + cw, pe = (ri < 4 ? t5 : t5 + 5) + ce;
+    const int ps = t5 - M5 + cs, pn = t5 + M5 + cn;
+    const int qw = i > 0 ? pw : pe, qe = i < n ? pe : pw, qs = j > 0 ? ps : pn, qn = j < n ? pn : ps;
+    r[j * w + i] = xr::resid<T>(f[p], u[p], xr::nb4<T>(u[qw], u[qe], u[qs], u[qn]),
+                                xr::diag<T>(k[(long long)j * pk + i], sides_at(i, j, n), bB));
+  });
+}
 // fc (layout lc) = full weighting of r (natural) onto the (n/2 + 1)^2 grid.
+// Full weighting onto a row-major Gauss-Seidel level (pitch n/2 + 1), which also starts that
+// level's pre-sweep: its red nodes from a zero guess (k H of the coarse level kc, relaxation
+// beta bAc) need only their own restricted value.
+template <class T>
+__device__ __forceinline__ void restrict_fw_red(c2<T>* fc, c2<T>* uc, const T* kc, T bAc, const c2<T>* r, int n) {
+  const int nc = n / 2, wc = nc + 1;
+  for_nodes(wc, wc * wc, [&](int q, int I, int J) {
+    const c2<T> v = xr::fw_node<T>(r, n + 1, n, I, J);
+    fc[q] = v;
+    if (((I + J) & 1) == 0) uc[q] = gs_red_zero<T>(v, kc[q], I, J, nc, bAc);
+  });
+}
 template <class T, class LC>
 __device__ __forceinline__ void restrict_fw(c2<T>* fc, LC lc, const c2<T>* r, int n) {
   const int wc = n / 2 + 1;
-  for_nodes(wc, wc * wc, [&](int, int I, int J) { fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J); });
-}
-// Bilinear interpolation of e (layout le) at fine node (2I + oi, 2J + oj), in the operation order
-// of xr::bilinear.
-template <class T, class LE>
-__device__ __forceinline__ c2<T> bilinear_at(const c2<T>* e, LE le, int I, int J, int oi, int oj) {
-  if (oi && oj)
-    return xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]),
-                                     xr::cadd<T>(e[le.at(I + 1, J)], e[le.at(I + 1, J + 1)])),
-                         (T)0.25);
-  if (oi) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I + 1, J)]), (T)0.5);
-  if (oj) return xr::cscale<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]), (T)0.5);
-  return e[le.at(I, J)];
+  if constexpr (LC::blocked)
+    for_blocked(n / 2, [&](int I, int J, int p) { fc[p] = xr::fw_node<T>(r, n + 1, n, I, J); });
+  else
+    for_nodes(wc, wc * wc, [&](int, int I, int J) { fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J); });
 }
 // u (layout lu) += P e (e: (n/2 + 1)^2 grid, layout le).
 template <class T, class LU, class LE>
 __device__ __forceinline__ void prolong_add(c2<T>* u, LU lu, const c2<T>* e, LE le, int n) {
-  const int w = n + 1;
-  for_nodes(w, w * w, [&](int, int i, int j) {
-    const int p = lu.at(i, j);
+  auto add = [&](int i, int j, int p) {
     u[p] = xr::cadd<T>(u[p], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
-  });
+  };
+  if constexpr (LU::blocked)
+    for_blocked(n, add);
+  else
+    for_nodes(n + 1, (n + 1) * (n + 1), [&](int q, int i, int j) { add(i, j, q); });
 }
 // Row r of the coarsest solve u = A^-1 f (inverse stored transposed, m x m), accumulated in column
 // order. The inverse is read from global memory eight columns at a time before they are summed,

@@ -54,40 +54,49 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
     const T* kh = reinterpret_cast<const T*>(L.kh);
     if (L.kind == TAIL_KACZ)
       for (int q = threadIdx.x; q < lvl::blocked_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
-    with_layout(l, [&](auto lay) {
-      lvl::for_nodes(w, w * w, [&](int q, int i, int j) {
-        const int p = lay.at(i, j);
-        lvl::cp_async<sizeof(T)>(L.kind == TAIL_GS ? &K(l)[q] : &V(l)[p], kh + (long long)j * L.pk + i);
+    if (L.kind == TAIL_KACZ) {
+      lvl::for_blocked(L.n, [&](int i, int j, int p) {
+        lvl::cp_async<sizeof(T)>(&V(l)[p], kh + (long long)j * L.pk + i);
         if (l == 0) lvl::cp_async<sizeof(c2<T>)>(&F(0)[p], fin + (long long)j * A.pf + i);
       });
-    });
+    } else {
+      lvl::for_nodes(w, w * w, [&](int q, int i, int j) {
+        lvl::cp_async<sizeof(T)>(&K(l)[q], kh + (long long)j * L.pk + i);
+        if (l == 0) lvl::cp_async<sizeof(c2<T>)>(&F(0)[q], fin + (long long)j * A.pf + i);
+      });
+    }
   }
   lvl::cp_async_wait_all();
   __syncthreads();
+  // row constants of the Kaczmarz levels; the first level's red nodes if it is a Gauss-Seidel level
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
-    if (L.kind != TAIL_KACZ) continue;
-    const int w = L.n + 1;
-    const lvl::Blocked lay = lvl::blocked(L.n);
-    lvl::for_nodes(w, w * w, [&](int, int i, int j) {
-      const int p = lay.at(i, j);
-      lvl::row_consts<T>(V(l)[p], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
-    });
+    if (L.kind == TAIL_KACZ)
+      lvl::for_blocked(L.n, [&](int i, int j, int p) {
+        lvl::row_consts<T>(V(l)[p], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
+      });
+    else if (l == 0)
+      lvl::gs_red<T>(U(0), F(0), K(0), L.n, (T)L.bA);
   }
   __syncthreads();
 
-  // down: relax from a zero guess, residual with the (B) operator, full weighting
+  // down: relax from a zero guess (a Gauss-Seidel level's red nodes were set by the phase that
+  // produced its right-hand side), residual with the (B) operator, full weighting
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
     if (L.kind == TAIL_GS) {
-      lvl::gs_pre<T>(U(l), F(l), K(l), L.n, (T)L.bA);
+      lvl::gs_black<T>(U(l), F(l), K(l), L.n, (T)L.bA);
       lvl::residual<T>(R, U(l), F(l), lvl::Natural{L.n + 1}, K(l), L.n + 1, L.n, (T)L.bB);
     } else {
       lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, false);
-      lvl::residual<T>(R, U(l), F(l), lvl::blocked(L.n), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
+      lvl::residual_blocked<T>(R, U(l), F(l), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
     }
     __syncthreads();
-    with_layout(l + 1, [&](auto lc) { lvl::restrict_fw<T>(F(l + 1), lc, R, L.n); });
+    const TailLevel& C = A.lv[l + 1];
+    if (C.kind == TAIL_GS)
+      lvl::restrict_fw_red<T>(F(l + 1), U(l + 1), K(l + 1), (T)C.bA, R, L.n);
+    else
+      with_layout(l + 1, [&](auto lc) { lvl::restrict_fw<T>(F(l + 1), lc, R, L.n); });
     __syncthreads();
   }
 
@@ -99,23 +108,23 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
     __syncthreads();
   }
 
-  // up: bilinear correction, relaxation in the reverse order
+  // up: bilinear correction, relaxation in the reverse order (fused on Gauss-Seidel levels)
   for (int l = last - 1; l >= 0; --l) {
     const TailLevel& L = A.lv[l];
-    with_layout(l, [&](auto lu) {
-      with_layout(l + 1, [&](auto le) { lvl::prolong_add<T>(U(l), lu, U(l + 1), le, L.n); });
-    });
-    __syncthreads();
-    if (L.kind == TAIL_GS)
-      lvl::gs_post<T>(U(l), F(l), K(l), L.n, (T)L.bA);
-    else
+    if (L.kind == TAIL_GS) {
+      with_layout(l + 1, [&](auto le) { lvl::gs_post_corrected<T>(U(l), F(l), K(l), L.n, (T)L.bA, U(l + 1), le); });
+    } else {
+      with_layout(l + 1, [&](auto le) { lvl::prolong_add<T>(U(l), lvl::blocked(L.n), U(l + 1), le, L.n); });
+      __syncthreads();
       lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, true);
+    }
   }
 
   const int w = A.lv[0].n + 1;
-  with_layout(0, [&](auto lay) {
-    lvl::for_nodes(w, w * w, [&](int, int i, int j) { uout[(long long)j * A.po + i] = U(0)[lay.at(i, j)]; });
-  });
+  if (A.lv[0].kind == TAIL_KACZ)
+    lvl::for_blocked(A.lv[0].n, [&](int i, int j, int p) { uout[(long long)j * A.po + i] = U(0)[p]; });
+  else
+    lvl::for_nodes(w, w * w, [&](int q, int i, int j) { uout[(long long)j * A.po + i] = U(0)[q]; });
 }
 
 }  // namespace
