@@ -513,7 +513,7 @@ def run_ours(args):
         "kernel_share": shares(per_small),
         "gpu_launches": gpu_launches,
         "tile_autotuner": {wl.name: results["fp32"]["forms"], rw.name: roof_forms,
-                           "forms": "0 = shared-memory tiles; v = 1..6: register streaming, 2^(v+2) rows per warp"},
+                           "forms": "0 = shared-memory tiles; v = 1..8: register streaming, 2^v rows per warp"},
         "clocks": results["fp32"]["clocks"],
         "clocks_fp64_form": results["fp64"]["clocks"],
     }

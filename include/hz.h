@@ -84,7 +84,7 @@ typedef struct {
   int pass_variant; /* kernel form of the two fused passes of each Gauss-Seidel level in the FP32 form
                        (the FP64 form always uses 0): -1 (default) = chosen per level at setup by
                        timing every form on the level's arrays (tile autotuner); 0 = shared-memory
-                       tiles; 1..6 = register streaming with 2^(v+2) rows per warp */
+                       tiles; 1..8 = register streaming with 2^v rows per warp */
   int coarse_tail;  /* 1 (default): the smallest levels, from the first whose whole V-cycle below it
                        fits one block's shared memory down to the coarsest, run as one launch (same
                        operations, same results as the per-level kernels for one-sweep Gauss-Seidel

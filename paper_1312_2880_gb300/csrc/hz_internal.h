@@ -65,8 +65,8 @@ cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int p
 // coarse level); prolong_smooth writes out = post-sweep(upre + P ec), as double2 when out_f64.
 // variant (FP32 form only): 0 = shared-memory tiles; 1 .. FUSED_VARIANTS-1 = register streaming
 // (hz_stream.cu) with stream_rows(variant) rows per warp. The FP64 form always uses tiles.
-constexpr int FUSED_VARIANTS = 7;
-inline int stream_rows(int variant) { return 4 << variant; }
+constexpr int FUSED_VARIANTS = 9;
+inline int stream_rows(int variant) { return 1 << variant; }
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
                                    cudaStream_t s, const Inst& bi = Inst(), int variant = 0);

@@ -128,7 +128,7 @@ KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3}
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
               pass_variant=-1, coarse_tail=True, kacz_form="auto") -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
-    memory tiles; 1..6 = register streaming with 2**(v+2) rows per warp (FP32 form).
+    memory tiles; 1..8 = register streaming with 2**v rows per warp (FP32 form).
     kacz_form: kernel form of the Kaczmarz levels below the finest (one of KACZ_FORMS); a form that
     does not apply to a level falls back to the default."""
     o = Opts()

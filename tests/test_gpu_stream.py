@@ -1,5 +1,5 @@
 """Kernel forms of the fused Gauss-Seidel passes (FP32 form): shared-memory tiles (form 0) and
-register streaming with 8 .. 256 rows per warp (forms 1..6), and the tile autotuner that picks one
+register streaming with 2 .. 256 rows per warp (forms 1..8), and the tile autotuner that picks one
 per level.
 
 Every form takes the same fixed-rounding operations in the same order on every node, so the
@@ -76,7 +76,7 @@ def test_forms_are_bitwise_identical(name):
     fused = [l for l, d in enumerate(sched0) if d["pass_down"] >= 0]
     assert fused, "no fused level in this hierarchy"
     assert all(sched0[l]["pass_down"] == 0 and sched0[l]["pass_up"] == 0 for l in fused)
-    for form in range(1, 7):
+    for form in range(1, 9):
         z, sched = vcycle(wl, form, r)
         for l in fused:
             want = form if sched[l]["n"] >= 4 else 0
@@ -113,7 +113,7 @@ def test_batched_streaming_solve_equals_single_tile_solves():
     wl = wedge(128, 25.0)
     n = wl.n
     rhs = np.stack([I.point_source_rhs(n, I.random_interior_nodes(n, 2, s)) for s in (1, 2, 3)])
-    P = hz.Problem(n, wl.kfield, 0.5, variant="hyb", precision="fp32", k_ref=wl.k_ref, batch=3, pass_variant=2)
+    P = hz.Problem(n, wl.kfield, 0.5, variant="hyb", precision="fp32", k_ref=wl.k_ref, batch=3, pass_variant=4)
     xb, infos = P.solve_batch(torch.from_numpy(rhs).cuda(), tol=1e-6, maxit=1000)
     xb = xb.cpu().numpy()
     P.close()
