@@ -56,7 +56,6 @@ def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
         "k_update_s": 48 + w,
         "k_apply_ts": y + 8 + 16 + 16,
         "k_update_xr": 16 + 2 * y + 16 + 16 + 16 + 32,
-        "k_x_half": 32 + y,
     }
     return table.get(kernel, 0.0)
 
@@ -64,7 +63,7 @@ def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
 # FP64 work per node of the Krylov kernels: (flops with an FMA counted 2, FP64-pipe instructions).
 # The operator on an interior node: 3 complex adds (6), d = (kh)^2 - 4 (1 FMA), v = nb + d y (2 FMA).
 KRYLOV_FP64 = {"k_update_p": (16, 8), "k_apply_rv": (20, 13), "k_update_s": (12, 6), "k_apply_ts": (24, 15),
-               "k_update_xr": (36, 18), "k_x_half": (8, 4)}
+               "k_update_xr": (36, 18)}
 
 
 def kernel_fp64_flops_per_node(kernel: str) -> float:

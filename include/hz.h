@@ -251,8 +251,7 @@ typedef enum {
   HZ_K_UPDATE_P,       /* p = r + beta (p - omega v) */
   HZ_K_APPLY_RV,       /* v = A y with <r^, v> */
   HZ_K_UPDATE_S,       /* s = r - alpha v with |s|^2 */
-  HZ_K_X_HALF,         /* x += alpha y after a half-step stop */
-  HZ_K_APPLY_TS,       /* t = A z with <t, s>, <t, t> */
+  HZ_K_APPLY_TS,       /* t = A z with <t, s>, <t, t> (or, after a half-step stop, x += alpha y) */
   HZ_K_UPDATE_XR,      /* x, r updates with <r^, r>, |r|^2 */
   HZ_K_SMOOTH_RESTRICT, /* fused: GS sweep from a zero guess, residual, full weighting */
   HZ_K_PROLONG_SMOOTH, /* fused: bilinear correction and GS post-sweep */

@@ -538,7 +538,6 @@ cudaError_t enqueue_iteration(hz_problem* P) {
   if ((e = run_vcycle(P, fp32 ? (const void*)k.p32 : k.p, fp32 ? (void*)k.y32 : k.y, stop, true))) return e;
   if ((e = mark(P, launch_k_apply_rv(k, s), HZ_K_APPLY_RV, 0))) return e;
   if ((e = mark(P, launch_k_update_s(k, s), HZ_K_UPDATE_S, 0))) return e;
-  if ((e = mark(P, launch_k_x_half(k, s), HZ_K_X_HALF, 0))) return e;
   if ((e = run_vcycle(P, fp32 ? (const void*)k.s32 : k.s, fp32 ? (void*)k.z32 : k.z, stop, true))) return e;
   if ((e = mark(P, launch_k_apply_ts(k, s), HZ_K_APPLY_TS, 0))) return e;
   return mark(P, launch_k_update_xr(k, s), HZ_K_UPDATE_XR, 0);
@@ -1184,7 +1183,9 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   k.partials = (double*)(A + pl.off_partials);
   k.hist = (double*)(A + pl.off_hist);
   long long want = (k.N + 255) / 256;
-  k.G = (int)std::min<long long>(want, std::min(8LL * P->num_sms, (long long)MAX_G));
+  // two blocks per SM: enough warps for the FP64 pipe at every size measured (n = 256 .. 4096),
+  // and fewer block reductions than one block per 256 nodes
+  k.G = (int)std::min<long long>(want, std::min(2LL * P->num_sms, (long long)MAX_G));
   if (k.G < 1) k.G = 1;
   CK(cudaMemsetAsync(k.st, 0, sizeof(KState) * pl.batch, s));
   // Coarsest: dense inverse on the device.
@@ -1681,7 +1682,7 @@ hz_status hz_set_stall_detection(hz_problem* P, double cos2, double step2, int m
 
 const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
-                                "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s", "k_x_half",
+                                "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s",
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
                                 "kacz_sweep", "coarse_tail", "kacz_cluster"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";

@@ -222,7 +222,6 @@ cudaError_t launch_k_init(const KrylovVecs& k, double tol, int maxit, int hist_c
 cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s);
-cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s);

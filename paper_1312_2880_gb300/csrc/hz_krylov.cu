@@ -56,19 +56,27 @@ __device__ __forceinline__ void warp_sum(double (&v)[NV]) {
     for (int off = 16; off; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
 }
 
-// Sum over the block in a fixed order; the result is valid in thread 0.
+// Sum over the block in a fixed order; the result is valid in thread 0. Every thread stores its
+// values, lane L of warp 0 adds column L over the KB / 32 warps, then a shuffle tree. GB300's
+// FP64 pipe executes every lane of a warp instruction, so a shuffle tree in each of the KB / 32
+// warps costs as much FP64 issue as the kernel's own arithmetic on small grids (measured: the
+// reduction of an update at n = 512 took 8.6 us of 31); summing through shared memory first
+// leaves one warp's adds per block.
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[KB / 32]) {
-  warp_sum<NV>(v);
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[KB]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+  for (int k = 0; k < NV; ++k) sm[k][threadIdx.x] = v[k];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = lane < KB / 32 ? sm[k][lane] : 0.0;
+    for (int k = 0; k < NV; ++k) {
+      double s = sm[k][lane];
+#pragma unroll
+      for (int w = 1; w < KB / 32; ++w) s += sm[k][w * 32 + lane];
+      v[k] = s;
+    }
     warp_sum<NV>(v);
   }
 }
@@ -77,7 +85,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[KB / 32]
 // in block order and returns true with the totals in `tot` (in every thread of that block).
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket, double (&tot)[NV]) {
-  __shared__ double sm[NV][KB / 32];
+  __shared__ double sm[NV][KB];
   __shared__ int is_last;
   __shared__ double res[NV];
   block_sum<NV>(v, sm);
@@ -358,35 +366,30 @@ __global__ void k_update_s_kernel(KrylovVecs k) {
   }
 }
 
-// After a half-step stop: x += alpha y, once.
+// t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>. After a stop at the half step (the
+// second preconditioner application was skipped) it instead applies x += alpha y, once.
 template <class Y2>
-__global__ void k_x_half_kernel(KrylovVecs k, const Y2* __restrict__ y) {
+__global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ y, const Y2* __restrict__ z) {
   pdl_enter();
   k = instance(k);
   y += blockIdx.z * k.sv;
-  KState* st = k.st;
-  if (st->half != 1) return;
-  const double2 alpha = st->alpha;
-  const int N = (int)k.N;
-  GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, ldy(y, e)); }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int t = atomicAdd(&st->ticket[KT_XHALF], 1u);
-    if (t == gridDim.x - 1) {
-      st->half = 2;
-      st->ticket[KT_XHALF] = 0;
-    }
-  }
-}
-
-// t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>.
-template <class Y2>
-__global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ z) {
-  pdl_enter();
-  k = instance(k);
   z += blockIdx.z * k.sv;
   KState* st = k.st;
+  if (st->half == 1) {
+    const double2 alpha = st->alpha;
+    const int N = (int)k.N;
+    GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, ldy(y, e)); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned int t = atomicAdd(&st->ticket[KT_XHALF], 1u);
+      if (t == gridDim.x - 1) {
+        st->half = 2;
+        st->ticket[KT_XHALF] = 0;
+      }
+    }
+    return;
+  }
   if (st->done) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
@@ -578,14 +581,9 @@ cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_s_kernel) }
-cudaError_t launch_k_x_half(const KrylovVecs& k, cudaStream_t s) {
-  if (k.y32) pdl_launch(k_x_half_kernel<float2>, KGRID, KB, 0, s, k, k.y32);
-  else pdl_launch(k_x_half_kernel<double2>, KGRID, KB, 0, s, k, k.y);
-  return cudaGetLastError();
-}
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) {
-  if (k.z32) pdl_launch(k_apply_ts_kernel<float2>, KGRID, KB, 0, s, k, k.z32);
-  else pdl_launch(k_apply_ts_kernel<double2>, KGRID, KB, 0, s, k, k.z);
+  if (k.z32) pdl_launch(k_apply_ts_kernel<float2>, KGRID, KB, 0, s, k, k.y32, k.z32);
+  else pdl_launch(k_apply_ts_kernel<double2>, KGRID, KB, 0, s, k, k.y, k.z);
   return cudaGetLastError();
 }
 cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) {
