@@ -1182,10 +1182,12 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   k.st = (KState*)(A + pl.off_state);
   k.partials = (double*)(A + pl.off_partials);
   k.hist = (double*)(A + pl.off_hist);
-  long long want = (k.N + 255) / 256;
-  // two blocks per SM: enough warps for the FP64 pipe at every size measured (n = 256 .. 4096),
-  // and fewer block reductions than one block per 256 nodes
-  k.G = (int)std::min<long long>(want, std::min(2LL * P->num_sms, (long long)MAX_G));
+  // About four nodes per thread, between two and eight blocks per SM: on small grids fewer blocks
+  // mean fewer block reductions (n = 512: 2 per SM), on large ones more warps hide the FP64 and
+  // memory latency (n = 4096 update of x and r: 0.54 ms with 8 per SM, 0.60 ms with 2).
+  long long want = (k.N + 4 * 256 - 1) / (4 * 256);
+  want = std::max(want, std::min(2LL * P->num_sms, (k.N + 255) / 256));
+  k.G = (int)std::min<long long>(want, std::min(8LL * P->num_sms, (long long)MAX_G));
   if (k.G < 1) k.G = 1;
   CK(cudaMemsetAsync(k.st, 0, sizeof(KState) * pl.batch, s));
   // Coarsest: dense inverse on the device.
