@@ -585,6 +585,44 @@ def run_profile_case(args):
     P.close()
 
 
+def run_tables(args):
+    """Sec. 6, Tables 1, 2 and 6 re-run on the GPU: Bi-CGSTAB iterations to relres 1e-7 for HYB-V,
+    SL-V and HLM-V (no ray correction), FP64 and FP32 V-cycle forms; one JSON line per run and a
+    summary line with the paper's counts beside ours (context: the paper leaves the boundary
+    scheme, smoother ordering and shadow residual unstated, so only trends are comparable)."""
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    torch.cuda.set_device(0)
+    build.build()
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_iterations.json")))
+    summary = {}
+    for variant in ("hyb", "sl", "hlm"):
+        for table, col, wl in I.paper_table_workloads(variant=variant, max_n=args.tables_max_n):
+            rhs = torch.from_numpy(wl.rhs).cuda()
+            for prec in ("fp64", "fp32"):
+                P = hz.Problem(wl.n, wl.kfield, 0.5, variant=variant, precision=prec, k_ref=wl.k_ref)
+                try:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, info, _ = P.solve(rhs, tol=wl.tol, maxit=args.tables_maxit, allow_fail=True)
+                    torch.cuda.synchronize()
+                    ms = (time.perf_counter() - t0) * 1e3
+                finally:
+                    P.close()
+                it = info["iterations"] if info["status"] == 0 else None
+                print(json.dumps({"table": table, "column": col, "variant": variant, "precision": prec,
+                                  "n": wl.n, "iterations": it, "status": info["status"],
+                                  "relres_true": info["relres_true"], "ms": round(ms, 2)}), flush=True)
+                summary.setdefault(f"{table} {variant} {prec}", []).append(it)
+    paper = {}
+    for table in ("table1", "table2", "table6"):
+        for variant in ("sl", "hyb"):
+            paper[f"{table} {variant}"] = golden[table][variant]
+    print(json.dumps({"tables": summary, "paper": paper, "tol": 1e-7, "maxit": args.tables_maxit}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -602,9 +640,14 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=15.0)
     ap.add_argument("--profile-precision", default="fp32")
     ap.add_argument("--pass-variant", type=int, default=-1,
-                    help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..6: streaming)")
+                    help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..8: streaming)")
+    ap.add_argument("--tables", action="store_true", help="re-run the paper's Tables 1, 2 and 6 and exit")
+    ap.add_argument("--tables-maxit", type=int, default=400)
+    ap.add_argument("--tables-max-n", type=int, default=1024)
     args = ap.parse_args()
-    if args.profile_case:
+    if args.tables:
+        run_tables(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

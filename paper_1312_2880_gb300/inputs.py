@@ -179,6 +179,40 @@ def grf_n4096(seed: int = SEED_BASE + 3, n: int = 4096, k: float = 1000.0) -> Wo
                     meta={"medium": "k(1+0.3 g), g Gaussian random field", "rhs": "centre point source 1/h^2"})
 
 
+# Sec. 6, Tables 1, 2 and 6: (k, n) of each column; Table 6 columns are k_ref with k_ref h = 15/64.
+PAPER_TABLE1 = ((40.0, 64), (50.0, 80), (80.0, 128), (100.0, 160), (150.0, 240))
+PAPER_TABLE2 = ((40.0, 64), (40.0, 128), (40.0, 256), (40.0, 512))
+PAPER_TABLE6 = ((15.0, 64), (30.0, 128), (60.0, 256), (120.0, 512), (240.0, 1024))
+# The Table 6 wedge: the figure is missing; its caption puts k between k_ref and 2 k_ref and the
+# source at the middle of the upper boundary, so the layers read k_ref * {1, 1.5, 2} top to bottom.
+PAPER_WEDGE_FACTORS = (1.0, 1.5, 2.0)
+
+
+def paper_table_workloads(tables=("table1", "table2", "table6"), variant: str = "hyb", max_n: int = 1 << 30):
+    """The Bi-CGSTAB runs behind Sec. 6, Tables 1, 2 and 6 (tolerance 1e-7, x0 = 0): constant k with
+    a unit source at the centre (Tables 1-2), and the wedge with a unit source at the middle of
+    the upper boundary (Table 6). Yields (table, column, Workload)."""
+    out = []
+    for name, spec in (("table1", PAPER_TABLE1), ("table2", PAPER_TABLE2), ("table6", PAPER_TABLE6)):
+        if name not in tables:
+            continue
+        for k, n in spec:
+            if n > max_n:
+                continue
+            if name == "table6":
+                kf = wedge_k(n, k, SEED_BASE + 6, PAPER_WEDGE_FACTORS)
+                rhs = point_source_rhs(n, [(n // 2, n)], 1.0)
+                meta = {"medium": "wedge k_ref*{1,1.5,2}", "rhs": "unit source at (0.5, 1)"}
+            else:
+                kf = constant_k(n, k)
+                rhs = centre_source_rhs(n, 1.0)
+                meta = {"medium": "constant k", "rhs": "unit source at (0.5, 0.5)"}
+            col = f"k_ref={k:g}" if name == "table6" else f"k={k:g},h=1/{n}"
+            out.append((name, col, Workload(f"{name}_n{n}_k{k:g}", n, k, kf, rhs, variant=variant, levels=0,
+                                             tol=1e-7, meta=meta)))
+    return out
+
+
 BATCH_SPECS = ((50.0, 96), (100.0, 192), (200.0, 384), (300.0, 576))
 
 

@@ -214,3 +214,25 @@ def test_paper_trends():
     assert counts[(40, "hyb")] <= counts[(40, "sl")]
     assert counts[(80, "hyb")] <= counts[(80, "sl")]
     assert counts[(80, "sl")] > counts[(40, "sl")] and counts[(80, "hyb")] > counts[(40, "hyb")]
+
+
+def test_paper_table_workloads():
+    """The runs behind Tables 1, 2 and 6: kh = 0.625 (Table 1), k = 40 (Table 2), k_ref h = 15/64
+    with k between k_ref and 2 k_ref (Table 6), unit sources at the centre or at (0.5, 1)."""
+    runs = I.paper_table_workloads(max_n=256)
+    assert [c for t, c, _ in runs if t == "table1"] == ["k=40,h=1/64", "k=50,h=1/80", "k=80,h=1/128",
+                                                       "k=100,h=1/160", "k=150,h=1/240"]
+    for table, _, wl in runs:
+        assert wl.tol == 1e-7 and wl.rhs.sum() == 1.0
+        (j, i), = np.argwhere(wl.rhs != 0)
+        if table == "table6":
+            assert (i, j) == (wl.n // 2, wl.n)
+            assert abs(wl.k_ref / wl.n - 15.0 / 64) < 1e-12
+            assert wl.kfield.min() == wl.k_ref and wl.kfield.max() == 2 * wl.k_ref
+        else:
+            assert (i, j) == (wl.n // 2, wl.n // 2)
+            assert np.all(wl.kfield == wl.k_ref)
+            if table == "table1":
+                assert abs(wl.k_ref / wl.n - 0.625) < 1e-12
+            else:
+                assert wl.k_ref == 40.0
