@@ -115,6 +115,7 @@ struct TailArgs {
   int count;  // levels in the tail, the last the coarsest
   TailLevel lv[TAIL_MAX_LEVELS];
   unsigned off_r;    // residual scratch
+  unsigned off_ainv; // coarsest inverse staged in shared memory when it fits (0: read from global)
   const void* ainvT; // coarsest inverse (transposed)
   const void* f_in;  // right-hand side of the first tail level (pitch pf)
   int pf;

@@ -259,18 +259,12 @@ __device__ __forceinline__ void gs_black(c2<T>* u, const c2<T>* f, const T* k, i
   });
   __syncthreads();
 }
-// Red nodes from a zero guess, then black nodes.
-template <class T>
-__device__ __forceinline__ void gs_pre(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
-  gs_red<T>(u, f, k, n, bA);
-  __syncthreads();
-  gs_black<T>(u, f, k, n, bA);
-}
 // Correction u += P e (e: layout le) and the post-sweep, black nodes then red, in two phases. A
 // Gauss-Seidel update does not read the node's own value, so the corrected values are needed
 // only at red nodes, as neighbours of the black update: the black phase forms them on the fly
 // (the same cadd of u and the bilinear value that a separate correction pass would store) and
-// the red phase reads the new black values. Same results as correction, then gs_post.
+// the red phase reads the new black values. Same results as a correction pass followed by the
+// black and red updates.
 template <class T, class LE>
 __device__ __forceinline__ void gs_post_corrected(c2<T>* u, const c2<T>* f, const T* k, int n, T bA, const c2<T>* e,
                                                   LE le) {
@@ -291,20 +285,6 @@ __device__ __forceinline__ void gs_post_corrected(c2<T>* u, const c2<T>* f, cons
   });
   __syncthreads();
 }
-// Black nodes, then red nodes (the post-sweep on u + P e).
-template <class T>
-__device__ __forceinline__ void gs_post(c2<T>* u, const c2<T>* f, const T* k, int n, T bA) {
-  const int w = n + 1;
-#pragma unroll 1
-  for (int c = 1; c >= 0; --c) {
-    for_colour<T>(n, c, [&](int i, int j) {
-      const int p = j * w + i;
-      u[p] = xr::gs<T>(f[p], nb_at<T>(u, i, j, n), xr::diag<T>(k[p], sides_at(i, j, n), bA));
-    });
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------------ residual and transfers
 // r (natural, pitch n + 1) = f~ - B u, u and f~ stored with layout lu, k H from `k` (pitch pk;
 // shared or global).

@@ -22,8 +22,6 @@ constexpr int TAIL_THREADS = 1024;
 
 template <class T>
 __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, const int* __restrict__ stop, Inst bi) {
-  pdl_enter();
-  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const c2<T>* fin = reinterpret_cast<const c2<T>*>(A.f_in) + blockIdx.z * bi.sf;
   c2<T>* uout = reinterpret_cast<c2<T>*>(A.u_out) + blockIdx.z * bi.so;
@@ -44,39 +42,60 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
       fn(lvl::Natural{nl + 1});
   };
 
-  // Right-hand side of the first level and k H of every relaxation level, all copied at once
-  // (cp.async, one wait for all of them): k H into K(l) on Gauss-Seidel levels, into the cells of
-  // 1/|a|^2 on Kaczmarz levels, where the row constants replace it below; zero guess of the
-  // Kaczmarz levels.
+  // Before the wait for the preceding kernel, everything that does not depend on it, so that with
+  // programmatic dependent launch it overlaps that kernel: k H of every relaxation level (set up
+  // once per problem), copied at once (cp.async, one wait) into K(l) on Gauss-Seidel levels and
+  // into the cells of 1/|a|^2 on Kaczmarz levels, where the row constants replace it; the zero
+  // guess of the Kaczmarz levels.
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
-    const int w = L.n + 1;
     const T* kh = reinterpret_cast<const T*>(L.kh);
-    if (L.kind == TAIL_KACZ)
-      for (int q = threadIdx.x; q < lvl::blocked_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
     if (L.kind == TAIL_KACZ) {
+      for (int q = threadIdx.x; q < lvl::blocked_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
       lvl::for_blocked(L.n, [&](int i, int j, int p) {
         lvl::cp_async<sizeof(T)>(&V(l)[p], kh + (long long)j * L.pk + i);
-        if (l == 0) lvl::cp_async<sizeof(c2<T>)>(&F(0)[p], fin + (long long)j * A.pf + i);
       });
     } else {
+      const int w = L.n + 1;
       lvl::for_nodes(w, w * w, [&](int q, int i, int j) {
         lvl::cp_async<sizeof(T)>(&K(l)[q], kh + (long long)j * L.pk + i);
-        if (l == 0) lvl::cp_async<sizeof(c2<T>)>(&F(0)[q], fin + (long long)j * A.pf + i);
       });
     }
   }
+  const int mc = (A.lv[last].n + 1) * (A.lv[last].n + 1);
+  if (A.off_ainv) {  // the coarsest inverse, when it fits
+    const c2<T>* src = reinterpret_cast<const c2<T>*>(A.ainvT);
+    c2<T>* dst = reinterpret_cast<c2<T>*>(smem + A.off_ainv);
+    for (int q = threadIdx.x; q < mc * mc; q += TAIL_THREADS) lvl::cp_async<sizeof(c2<T>)>(dst + q, src + q);
+  }
   lvl::cp_async_wait_all();
   __syncthreads();
-  // row constants of the Kaczmarz levels; the first level's red nodes if it is a Gauss-Seidel level
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
     if (L.kind == TAIL_KACZ)
       lvl::for_blocked(L.n, [&](int i, int j, int p) {
         lvl::row_consts<T>(V(l)[p], i, j, L.n, (T)L.bA, &D(l)[p], &V(l)[p]);
       });
-    else if (l == 0)
-      lvl::gs_red<T>(U(0), F(0), K(0), L.n, (T)L.bA);
+  }
+
+  pdl_enter();
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;  // the whole block
+  // the first level's right-hand side (the preceding kernel's output), and its red nodes if it is
+  // a Gauss-Seidel level
+  {
+    const TailLevel& L = A.lv[0];
+    const int w = L.n + 1;
+    if (L.kind == TAIL_KACZ)
+      lvl::for_blocked(L.n, [&](int i, int j, int p) {
+        lvl::cp_async<sizeof(c2<T>)>(&F(0)[p], fin + (long long)j * A.pf + i);
+      });
+    else
+      lvl::for_nodes(w, w * w, [&](int q, int i, int j) {
+        lvl::cp_async<sizeof(c2<T>)>(&F(0)[q], fin + (long long)j * A.pf + i);
+      });
+    lvl::cp_async_wait_all();
+    __syncthreads();
+    if (L.kind == TAIL_GS) lvl::gs_red<T>(U(0), F(0), K(0), L.n, (T)L.bA);
   }
   __syncthreads();
 
@@ -103,7 +122,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   // coarsest: u = A^-1 f
   {
     const int m = (A.lv[last].n + 1) * (A.lv[last].n + 1);
-    const c2<T>* ainvT = reinterpret_cast<const c2<T>*>(A.ainvT);
+    const c2<T>* ainvT = A.off_ainv ? reinterpret_cast<const c2<T>*>(smem + A.off_ainv)
+                                    : reinterpret_cast<const c2<T>*>(A.ainvT);
     for (int r = threadIdx.x; r < m; r += TAIL_THREADS) U(last)[r] = lvl::coarse_row<T>(ainvT, F(last), m, r);
     __syncthreads();
   }
@@ -152,6 +172,9 @@ size_t tail_layout(bool fp32, TailArgs* A) {
     if (L.kind != TAIL_COARSE) rmax = std::max(rmax, Nn);
   }
   A->off_r = take(rmax * c);
+  const size_t m = (size_t)(A->lv[A->count - 1].n + 1) * (A->lv[A->count - 1].n + 1);
+  A->off_ainv = 0;
+  if (off + m * m * c <= (size_t)TAIL_MAX_SMEM) A->off_ainv = take(m * m * c);
   return off;
 }
 
