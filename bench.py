@@ -488,6 +488,7 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(results["fp32"]["ms"], 3),
+        "per_step_ms": results["fp32"]["per_step_ms"],
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
