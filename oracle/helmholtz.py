@@ -47,7 +47,8 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "grid_index", "helmholtz_matrix", "full_weighting", "bilinear_prolongation", "inject",
     "red_black_colours", "kaczmarz_colours", "gs_update_rows", "rb_gs_sweep", "lex_gs_sweep",
-    "kaczmarz_update_rows", "kaczmarz_sweep", "level_policy", "OracleLevel", "OracleHierarchy",
+    "kaczmarz_update_rows", "kaczmarz_sweep", "jacobi_sweep", "rb_sor_sweep", "level_policy", "OracleLevel",
+    "OracleHierarchy", "DEFAULT_OMEGA",
     "build_hierarchy", "vcycle", "bicgstab", "BicgstabResult", "true_relres",
     "BIN_EDGES", "GUARD_BAND", "shadow_residual", "splitmix64_u01",
 ]
@@ -183,6 +184,15 @@ def kaczmarz_update_rows(A_rows: sp.csr_matrix, A_rows_H: sp.csr_matrix, rownorm
     return u + A_rows_H @ delta
 
 
+def sor_update_rows(A_off_rows: sp.csr_matrix, diag_rows: np.ndarray, f: np.ndarray, u: np.ndarray,
+                    rows: np.ndarray, omega: float) -> np.ndarray:
+    """Over-relaxed Gauss-Seidel update of uncoupled unknowns: ``(1 - omega) u + omega g`` with g the
+    Gauss-Seidel value (omega = 1 is Gauss-Seidel)."""
+    u = u.copy()
+    u[rows] = (1.0 - omega) * u[rows] + omega * ((f[rows] - A_off_rows @ u) / diag_rows)
+    return u
+
+
 def lex_gs_sweep(A: sp.csr_matrix, f: np.ndarray, u: np.ndarray, order: np.ndarray | None = None) -> np.ndarray:
     """One Gauss-Seidel sweep over the unknowns in ``order`` (lexicographic by default):
     ``u <- (D + L)^{-1} (f - U u)`` with D, L, U taken in that ordering. A general triangular
@@ -248,13 +258,14 @@ class OracleLevel:
     H: float
     k: np.ndarray
     relax_op: str
-    smoother: str  # gs | kaczmarz | direct
+    smoother: str  # gs | jacobi | sor | kaczmarz | direct
     resid_op: str
     nu: int
     A: sp.csr_matrix  # relaxation operator (or the direct-solve operator on the coarsest level)
     B: sp.csr_matrix | None = None  # residual operator
     R: sp.csr_matrix | None = None  # full weighting to the next level
     P: sp.csr_matrix | None = None  # bilinear interpolation from the next level
+    omega: float = 1.0  # relaxation factor of a jacobi or sor level
     cache: dict = field(default_factory=dict)
 
 
@@ -267,14 +278,21 @@ class OracleHierarchy:
     levels: list
 
 
+# Default relaxation factors of the alternative smoothers: damped Jacobi at the usual 4/5 of
+# two-dimensional 5-point smoothing; SOR at 1, i.e. Gauss-Seidel.
+DEFAULT_OMEGA = {"jacobi": 0.8, "sor": 1.0}
+
+
 def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hyb", levels: int = 0,
                     beta: float = 0.5, nu_gs: int = 1, nu_kacz: int = 4, guard: bool = True,
-                    ops: list | None = None) -> OracleHierarchy:
+                    ops: list | None = None, gs_smoother: str = "gs", omega: float | None = None) -> OracleHierarchy:
     """Grids n, n/2, ... with rediscretised operators and the per-level roles of :func:`level_policy`.
 
     ``levels = 0`` coarsens while the grid count is even and larger than 8. The coarsest level is
     solved directly with L (HYB, HLM) or M (SL variants). ``ops`` optionally overrides
-    (relax_op, smoother, resid_op) per non-coarsest level.
+    (relax_op, smoother, resid_op) per non-coarsest level. ``gs_smoother`` replaces red-black
+    Gauss-Seidel on the levels that use it by damped Jacobi ("jacobi") or red-black SOR ("sor")
+    with relaxation factor ``omega`` (the alternatives the remark of Sec. 4 names).
     """
     if levels <= 0:
         levels, m = 1, n
@@ -297,9 +315,13 @@ def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hy
             lv.cache["lu"] = sla.lu_factor(lv.A.toarray())
         else:
             relax, smoother, resid = level_policy(variant, k_ref * H, k * H, guard) if ops is None else ops[l]
+            if smoother == "gs" and gs_smoother != "gs":
+                smoother = gs_smoother
             nu = nu_kacz if smoother == "kaczmarz" else nu_gs
             lv = OracleLevel(nl, H, k, relax, smoother, resid, nu, M if relax == "M" else L,
                              M if resid == "M" else L, full_weighting(nl), bilinear_prolongation(nl))
+            if smoother in DEFAULT_OMEGA:
+                lv.omega = DEFAULT_OMEGA[smoother] if omega is None else float(omega)
             _prepare_relaxation(lv)
         out.append(lv)
     return OracleHierarchy(n, beta, variant, k_ref, out)
@@ -307,7 +329,9 @@ def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hy
 
 def _prepare_relaxation(lv: OracleLevel) -> None:
     A = lv.A
-    if lv.smoother == "gs":
+    if lv.smoother == "jacobi":
+        lv.cache["diag"] = A.diagonal()
+    elif lv.smoother in ("gs", "sor"):
         diag = A.diagonal()
         A_off = (A - sp.diags(diag)).tocsr()
         col = red_black_colours(lv.n)
@@ -331,6 +355,19 @@ def rb_gs_sweep(lv: OracleLevel, f: np.ndarray, u: np.ndarray, first: int = 0) -
     return u
 
 
+def rb_sor_sweep(lv: OracleLevel, f: np.ndarray, u: np.ndarray, first: int = 0) -> np.ndarray:
+    """One red-black SOR sweep with the level's relaxation operator and factor ``lv.omega``."""
+    for c in (first, 1 - first):
+        rows, A_off_rows, diag_rows = lv.cache[("gs", c)]
+        u = sor_update_rows(A_off_rows, diag_rows, f, u, rows, lv.omega)
+    return u
+
+
+def jacobi_sweep(lv: OracleLevel, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """One damped Jacobi sweep, every unknown at once: ``u + omega D^-1 (f - A u)``."""
+    return u + lv.omega * (f - lv.A @ u) / lv.cache["diag"]
+
+
 def kaczmarz_sweep(lv: OracleLevel, f: np.ndarray, u: np.ndarray, order=(0, 1, 2, 3, 4)) -> np.ndarray:
     """One Kaczmarz sweep over the five colours in ``order`` with the level's relaxation operator."""
     for c in order:
@@ -344,6 +381,10 @@ def relax(lv: OracleLevel, f: np.ndarray, u: np.ndarray, post: bool) -> np.ndarr
     for _ in range(lv.nu):
         if lv.smoother == "gs":
             u = rb_gs_sweep(lv, f, u, first=1 if post else 0)
+        elif lv.smoother == "sor":
+            u = rb_sor_sweep(lv, f, u, first=1 if post else 0)
+        elif lv.smoother == "jacobi":
+            u = jacobi_sweep(lv, f, u)
         else:
             u = kaczmarz_sweep(lv, f, u, order=(4, 3, 2, 1, 0) if post else (0, 1, 2, 3, 4))
     return u

@@ -934,7 +934,7 @@ void plan_tail(hz_problem* P) {
 
 // ------------------------------------------------------------------ tile autotuner
 // Every fused Gauss-Seidel level of the FP32 form runs each candidate variant of its two passes
-// (shared-memory tiles, or register streaming with 8 .. 256 rows per warp) on its own arrays,
+// (shared-memory tiles, or register streaming with 2 .. 256 rows per warp) on its own arrays,
 // with all right-hand sides of the batch: one untimed launch, then the best of three timings of
 // five back-to-back launches with CUDA events on the library stream. The fastest is kept, and cached per
 // (n_l, batch, pass, finest level or not) for later problems of the same shape.

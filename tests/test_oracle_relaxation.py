@@ -228,3 +228,81 @@ def test_kaczmarz_error_is_monotone_on_consistent_systems():
     res = f - lv.A @ u
     last = o.kaczmarz_colours(n) == 4
     assert np.abs(res[last]).max() < 1e-9 * np.abs(f).max()
+
+
+# --------------------------------------------------------------------------- Jacobi and SOR
+# The alternatives the remark of Sec. 4 names: damped Jacobi and (red-black) SOR.
+
+
+def _periodic_level(m, kH, beta, smoother, omega):
+    """An m x m periodic grid with the h^2-scaled 5-point row (neighbours 1, diagonal
+    -4 + (kH)^2 (1 + i beta)) wrapped in an OracleLevel, so the oracle's own sweeps run on it."""
+    N = m * m
+    idx = np.arange(N).reshape(m, m)
+    d = -4 + kH * kH * (1 + 1j * beta)
+    rows, cols, vals = [], [], []
+    for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+        rows.append(idx.ravel()); cols.append(np.roll(np.roll(idx, -dj, 0), -di, 1).ravel()); vals.append(np.ones(N))
+    rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(np.full(N, d))
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N)).tocsr()
+    lv = o.OracleLevel(m - 1, 1.0, np.zeros((m, m)), "L", smoother, "L", 1, A, omega=omega)
+    o.helmholtz._prepare_relaxation(lv)
+    J, I = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    return lv, I, J
+
+
+@pytest.mark.parametrize("kH,beta,omega", [(0.3125, 0.0, 0.8), (1.25, 0.5, 0.8), (2.5, 0.0, 0.6), (5.0, 0.5, 1.0)])
+def test_jacobi_sweep_multiplies_each_fourier_mode(kH, beta, omega):
+    from oracle import lfa
+
+    m = 16
+    lv, I, J = _periodic_level(m, kH, beta, "jacobi", omega)
+    for th in ((2 * np.pi * 3 / m, 2 * np.pi * 1 / m), (2 * np.pi * 7 / m, 2 * np.pi * 6 / m)):
+        e = np.exp(1j * (th[0] * I + th[1] * J)).ravel()
+        out = o.jacobi_sweep(lv, np.zeros_like(e), e)
+        d = -4 + kH * kH * (1 + 1j * beta)
+        g = 1 - omega * (2 * math.cos(th[0]) + 2 * math.cos(th[1]) + d) / d
+        np.testing.assert_allclose(out, g * e, rtol=0, atol=1e-12)
+        assert abs(abs(g) - lfa.jacobi_amplification(th[0], th[1], kH, beta, omega)) < 1e-13
+
+
+@pytest.mark.parametrize("kH,beta,omega", [(0.3, 0.0, 1.0), (1.25, 0.5, 1.2), (2.5, 0.0, 0.7), (3.2, 0.5, 1.0)])
+def test_red_black_sor_sweep_is_the_two_harmonic_matrix(kH, beta, omega):
+    """One red-black SOR sweep of the oracle maps span{e_th, e_(th+(pi,pi))} into itself by exactly the
+    2 x 2 matrix derived in lfa.rb_sor_two_harmonic (omega = 1: the Gauss-Seidel analysis above)."""
+    from oracle import lfa
+
+    m = 16
+    lv, I, J = _periodic_level(m, kH, beta, "sor", omega)
+    th = (2 * np.pi * 3 / m, 2 * np.pi * 2 / m)
+    e1 = np.exp(1j * (th[0] * I + th[1] * J)).ravel()
+    e2 = np.exp(1j * ((th[0] + np.pi) * I + (th[1] + np.pi) * J)).ravel()
+    G = np.zeros((2, 2), complex)
+    for c, e in enumerate((e1, e2)):
+        out = o.rb_sor_sweep(lv, np.zeros_like(e), e, first=0)
+        coef = np.linalg.lstsq(np.stack([e1, e2], 1), out, rcond=None)[0]
+        assert np.linalg.norm(np.stack([e1, e2], 1) @ coef - out) < 1e-10
+        G[:, c] = coef
+    np.testing.assert_allclose(G, lfa.rb_sor_two_harmonic(th[0], th[1], kH, beta, omega), atol=1e-12)
+
+
+def test_textbook_smoothing_factors_of_the_laplacian():
+    """kH = 0 is the Poisson 5-point stencil, whose factors are textbook values: damped Jacobi with
+    omega = 4/5 smooths by 3/5, red-black Gauss-Seidel by 1/4."""
+    from oracle import lfa
+
+    assert abs(lfa.jacobi_smoothing_factor(0.0, 0.0, 0.8) - 0.6) < 1e-12
+    assert abs(lfa.rb_smoothing_factor(0.0, 0.0, 1.0) - 0.25) < 1e-12
+
+
+def test_sor_with_omega_one_is_gauss_seidel():
+    n, k = 32, 12.0
+    kf = np.full((n + 1, n + 1), k)
+    f = np.random.default_rng(3).standard_normal((n + 1) ** 2) + 0j
+    z_gs = o.vcycle(o.build_hierarchy(n, kf, k, "hyb"), f)
+    z_sor = o.vcycle(o.build_hierarchy(n, kf, k, "hyb", gs_smoother="sor", omega=1.0), f)
+    assert np.array_equal(z_gs, z_sor)
+    H = o.build_hierarchy(n, kf, k, "hyb", gs_smoother="jacobi")
+    assert [lv.smoother for lv in H.levels] == ["jacobi" if s == "gs" else s
+                                                for s in (lv.smoother for lv in o.build_hierarchy(n, kf, k, "hyb").levels)]
+    assert all(lv.omega == 0.8 for lv in H.levels if lv.smoother == "jacobi")
