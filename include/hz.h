@@ -59,7 +59,8 @@ typedef enum { HZ_VAR_HYB = 0, HZ_VAR_SL = 1, HZ_VAR_HLM = 2, HZ_VAR_SL_PLAIN = 
 typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_FP32 = 1 } hz_prec;
 
 typedef enum { HZ_OP_L = 0, HZ_OP_M = 1 } hz_op;
-typedef enum { HZ_SMOOTH_GS = 0, HZ_SMOOTH_KACZMARZ = 1, HZ_SMOOTH_DIRECT = 2 } hz_smoother;
+typedef enum { HZ_SMOOTH_GS = 0, HZ_SMOOTH_KACZMARZ = 1, HZ_SMOOTH_DIRECT = 2, HZ_SMOOTH_JACOBI = 3,
+               HZ_SMOOTH_SOR = 4 } hz_smoother;
 
 /* Kernel forms of a Kaczmarz level (Sec. 4): one launch per colour; the whole level (sweeps,
    residual and full weighting, or correction and sweeps) in one block's shared memory; one launch
@@ -94,6 +95,12 @@ typedef struct {
                        tiles (even sweep counts), else colour launches in the FP32 form; a cluster,
                        else colour launches in the FP64 form. A form that does not apply to a level
                        falls back to that default. */
+  int gs_smoother;  /* smoother of the levels the rules of Sec. 5 give Gauss-Seidel: HZ_SMOOTH_GS
+                       (default, red-black), HZ_SMOOTH_JACOBI (damped) or HZ_SMOOTH_SOR (red-black,
+                       over-relaxed) -- the alternatives the remark of Sec. 4 names. Jacobi and SOR
+                       levels run unfused, one launch per sweep or colour, outside the coarse tail. */
+  double omega;     /* relaxation factor of Jacobi or SOR in [0, 2); 0 (default) = 0.8 for Jacobi,
+                       1 for SOR (then SOR is Gauss-Seidel) */
 } hz_hierarchy_opts;
 
 typedef struct {
@@ -259,6 +266,7 @@ typedef enum {
   HZ_K_KACZ_SWEEP,     /* one five-colour Kaczmarz sweep over halo tiles */
   HZ_K_TAIL,           /* coarse tail: every level from hz_level_info.in_tail down, in one block */
   HZ_K_KACZ_CLUSTER,   /* whole Kaczmarz level over a thread-block cluster (pre or post, as HZ_K_KACZ_LEVEL) */
+  HZ_K_JACOBI,         /* one damped Jacobi sweep, out of place */
   HZ_K_COUNT
 } hz_kernel;
 

@@ -45,6 +45,7 @@ struct Level {
   void* u2 = nullptr; // result of the fused post-smoothing pass (levels >= 1)
   int var_down = 0, var_up = 0;  // fused-pass variants (FP32 form; picked by the tile autotuner)
   int kform = 0;                 // hz_kacz_form of a Kaczmarz level (set up by plan_kaczmarz)
+  double omega = 1.0;            // relaxation factor of a Jacobi or SOR level
 };
 
 struct Plan {
@@ -115,6 +116,9 @@ bool make_plan(int n, const hz_hierarchy_opts& o, Plan* P, std::string* err) {
       P->off_f[l] = off;
       off = align256(off + cells * ce * B);
       P->off_u2[l] = off;  // out-of-place result of the fused post-smoothing pass
+      off = align256(off + cells * ce * B);
+    } else if (o.gs_smoother == HZ_SMOOTH_JACOBI) {
+      P->off_u2[0] = off;  // the other half of the finest level's Jacobi sweeps
       off = align256(off + cells * ce * B);
     }
   }
@@ -365,6 +369,34 @@ cudaError_t kacz_tile_sweeps(hz_problem* P, int l, Src f, const void* first_in, 
   return cudaSuccess;
 }
 
+// `sweeps` damped Jacobi sweeps on level l ending in lv[l].u, from a zero guess or from lv[l].u;
+// ping-pong between u and u2 (from u with an odd count, u is first copied to u2).
+cudaError_t jacobi_sweeps(hz_problem* P, int l, Src f, bool from_zero, int sweeps, const int* stop, const Inst& bi) {
+  const Level& L = P->lv[l];
+  const bool fp32 = P->plan.fp32;
+  int pk;
+  const void* kh = kh_of(P, l, &pk);
+  cudaError_t e;
+  const void* src = from_zero ? nullptr : L.u;
+  if (!from_zero && sweeps % 2 == 1) {
+    const size_t es = fp32 ? sizeof(float2) : sizeof(double2);
+    if ((e = mark(P, cudaMemcpy2DAsync(L.u2, (size_t)L.pitch * es, L.u, (size_t)L.pitch * es, (size_t)(L.n + 1) * es,
+                                       (L.n + 1) * bi.count, cudaMemcpyDeviceToDevice, P->stream),
+                  HZ_K_JACOBI, l)))
+      return e;
+    src = L.u2;
+  }
+  for (int k = 0; k < sweeps; ++k) {
+    void* dst = ((sweeps - 1 - k) % 2 == 0) ? L.u : L.u2;
+    if ((e = mark(P, launch_jacobi(fp32, dst, L.pitch, src, L.pitch, f.f, f.pf, f.f64, kh, pk, L.n,
+                                   op_beta(P, L.relax_op), L.omega, stop, P->stream, bi),
+                  HZ_K_JACOBI, l)))
+      return e;
+    src = dst;
+  }
+  return cudaSuccess;
+}
+
 // Where level l's result after post-relaxation lives (what level l-1 interpolates).
 void* final_u(const hz_problem* P, int l) {
   return (l > 0 && fused(P, l)) ? P->lv[l].u2 : P->lv[l].u;
@@ -400,12 +432,15 @@ cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop, bool all = 
     return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s, bi),
                 HZ_K_RESTRICT, l);
   }
-  if (L.smoother == HZ_SMOOTH_GS) {
-    if ((e = mark(P, launch_gs_first(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 0, bA, stop, s, bi), HZ_K_GS_FIRST, l))) return e;
-    if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 1, bA, stop, s, bi), HZ_K_GS_COLOUR, l))) return e;
+  if (L.smoother == HZ_SMOOTH_JACOBI) {
+    if ((e = jacobi_sweeps(P, l, f, true, L.nu, stop, bi))) return e;
+  } else if (L.smoother == HZ_SMOOTH_GS || L.smoother == HZ_SMOOTH_SOR) {
+    const double w = L.omega;
+    if ((e = mark(P, launch_gs_first(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 0, bA, stop, s, bi, w), HZ_K_GS_FIRST, l))) return e;
+    if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, 1, bA, stop, s, bi, w), HZ_K_GS_COLOUR, l))) return e;
     for (int it = 1; it < L.nu; ++it)
       for (int c = 0; c < 2; ++c)
-        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s, bi), HZ_K_GS_COLOUR, l))) return e;
+        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, c, bA, stop, s, bi, w), HZ_K_GS_COLOUR, l))) return e;
   } else {
     size_t ce = fp32 ? 8 : 16;
     if ((e = mark(P, cudaMemset2DAsync(u, (size_t)pu * ce, 0, (size_t)(L.n + 1) * ce, (L.n + 1) * bi.count, s),
@@ -430,10 +465,12 @@ cudaError_t level_sweeps(hz_problem* P, int l, Src f, int sweeps, bool post, con
   void* u = L.u;
   int pu = L.pitch;
   cudaError_t e;
+  if (L.smoother == HZ_SMOOTH_JACOBI) return jacobi_sweeps(P, l, f, false, sweeps, stop, bi);
   for (int it = 0; it < sweeps; ++it) {
-    if (L.smoother == HZ_SMOOTH_GS) {
+    if (L.smoother == HZ_SMOOTH_GS || L.smoother == HZ_SMOOTH_SOR) {
       for (int q = 0; q < 2; ++q)
-        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 1 - q : q, bA, stop, s, bi),
+        if ((e = mark(P, launch_gs_colour(fp32, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, post ? 1 - q : q, bA, stop, s, bi,
+                                          L.omega),
                       HZ_K_GS_COLOUR, l)))
           return e;
     } else {
@@ -874,6 +911,10 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
           c_local.push_back(P->k_host[(size_t)stride * j * (n + 1) + (size_t)stride * i] * L.H);
       level_roles(o.variant, k_ref * L.H, c_local, o.guard != 0, &L);
       L.nu = L.smoother == HZ_SMOOTH_KACZMARZ ? o.nu_kacz : o.nu_gs;
+      if (L.smoother == HZ_SMOOTH_GS && o.gs_smoother != HZ_SMOOTH_GS) {
+        L.smoother = o.gs_smoother;
+        L.omega = o.omega > 0 ? o.omega : (o.gs_smoother == HZ_SMOOTH_JACOBI ? 0.8 : 1.0);
+      }
     }
   }
   return true;
@@ -883,7 +924,9 @@ bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
            o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024 ||
            o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1 ||
-           o.kacz_form < -1 || o.kacz_form > HZ_KACZ_CLUSTER);
+           o.kacz_form < -1 || o.kacz_form > HZ_KACZ_CLUSTER ||
+           (o.gs_smoother != HZ_SMOOTH_GS && o.gs_smoother != HZ_SMOOTH_JACOBI && o.gs_smoother != HZ_SMOOTH_SOR) ||
+           !(o.omega >= 0.0 && o.omega < 2.0));
 }
 
 // ------------------------------------------------------------------ coarse tail
@@ -1047,6 +1090,8 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->pass_variant = -1;
   o->coarse_tail = 1;
   o->kacz_form = -1;
+  o->gs_smoother = HZ_SMOOTH_GS;
+  o->omega = 0.0;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {
@@ -1149,7 +1194,7 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
     L.kh = (l > 0 || fp32) ? (void*)(A + pl.off_kh[l]) : nullptr;
     L.u = A + pl.off_u[l];
     L.f = l > 0 ? (void*)(A + pl.off_f[l]) : nullptr;
-    L.u2 = l > 0 ? (void*)(A + pl.off_u2[l]) : nullptr;
+    L.u2 = (l > 0 || pl.off_u2[0]) ? (void*)(A + pl.off_u2[l]) : nullptr;
     int stride = 1 << l;
     if (L.kh) CK(launch_inject_kh(fp32, L.kh, L.pk, P->kh64, n, stride, L.n, (double)stride, s));
   }
@@ -1686,7 +1731,7 @@ const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s",
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
-                                "kacz_sweep", "coarse_tail", "kacz_cluster"};
+                                "kacz_sweep", "coarse_tail", "kacz_cluster", "jacobi"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

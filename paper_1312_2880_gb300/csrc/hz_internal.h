@@ -47,10 +47,17 @@ struct Inst {
 // `stop` is an optional device flag: when it is non-zero the kernel returns at once (used to
 // turn the queued iterations after convergence into no-ops).
 
+// omega != 1: red-black SOR (the relaxed value (1 - omega) u + omega u_GS).
 cudaError_t launch_gs_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
-                             int pk, int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
+                             int pk, int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst(),
+                             double omega = 1.0);
 cudaError_t launch_gs_first(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
+                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst(),
+                            double omega = 1.0);
+// One damped Jacobi sweep out of place (in == nullptr: from a zero guess).
+cudaError_t launch_jacobi(bool fp32, void* out, int po, const void* in, int pu, const void* f, int pf, bool f64_src,
+                          const void* kh, int pk, int n, double beta, double omega, const int* stop, cudaStream_t s,
+                          const Inst& bi = Inst());
 cudaError_t launch_kacz_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh,
                                int pk, int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi = Inst());
 cudaError_t launch_restrict_residual(bool fp32, void* fc, int pc, const void* u, int pu, const void* f, int pf,

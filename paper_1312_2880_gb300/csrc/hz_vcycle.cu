@@ -24,9 +24,10 @@ inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1
 
 // One colour of a red-black sweep: every node with (i + j) % 2 == colour solves its own row
 // with its neighbours (all of the other colour) held fixed: u_p = (f~_p - sum_nb u_q) / d_p.
+// omega != 1: over-relaxed (SOR), u_p <- (1 - omega) u_p + omega (f~_p - sum_nb u_q) / d_p.
 template <class T, class F2>
 __global__ void gs_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
-                                 const T* __restrict__ kh, int pk, int n, int colour, T beta,
+                                 const T* __restrict__ kh, int pk, int n, int colour, T beta, T omega,
                                  const int* __restrict__ stop, Inst bi) {
   pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
@@ -42,14 +43,16 @@ __global__ void gs_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __rest
                      cadd<T>(u[(long long)b.js * pu + i], u[(long long)b.jn * pu + i]));
   c2<T> d = row_diag<T>(kh[(long long)j * pk + i], b.sides, beta);
   c2<T> fv = ldc<T>(f, (long long)j * pf + i);
-  u[(long long)j * pu + i] = cdiv<T>(csub<T>(fv, nb), d);
+  c2<T> g = cdiv<T>(csub<T>(fv, nb), d);
+  if (omega != (T)1) g = xr::cadd<T>(xr::cscale<T>(u[(long long)j * pu + i], (T)1 - omega), xr::cscale<T>(g, omega));
+  u[(long long)j * pu + i] = g;
 }
 
-// First half-sweep from a zero guess: nodes of `colour` get f~/d (their neighbours are zero),
-// nodes of the other colour are set to zero. Replaces zero-fill + first colour.
+// First half-sweep from a zero guess: nodes of `colour` get f~/d (their neighbours are zero;
+// omega f~/d for SOR), nodes of the other colour are set to zero. Replaces zero-fill + first colour.
 template <class T, class F2>
 __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restrict__ f, int pf,
-                                const T* __restrict__ kh, int pk, int n, int colour, T beta,
+                                const T* __restrict__ kh, int pk, int n, int colour, T beta, T omega,
                                 const int* __restrict__ stop, Inst bi) {
   pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
@@ -62,8 +65,41 @@ __global__ void gs_first_kernel(c2<T>* __restrict__ u, int pu, const F2* __restr
   if (((i + j) & 1) == colour) {
     int sides = (i == 0) + (i == n) + (j == 0) + (j == n);
     out = cdiv<T>(ldc<T>(f, (long long)j * pf + i), row_diag<T>(kh[(long long)j * pk + i], sides, beta));
+    if (omega != (T)1) out = xr::cscale<T>(out, omega);
   }
   u[(long long)j * pu + i] = out;
+}
+
+// ---------------------------------------------------------------- damped Jacobi (Sec. 4, remark)
+
+// One damped Jacobi sweep, every node at once, out of place: out = in + omega (f~ - A in) / d;
+// from a zero guess (in == nullptr) out = omega f~ / d.
+template <class T, class F2>
+__global__ void jacobi_kernel(c2<T>* __restrict__ out, int po, const c2<T>* __restrict__ in, int pu,
+                              const F2* __restrict__ f, int pf, const T* __restrict__ kh, int pk, int n, T beta,
+                              T omega, const int* __restrict__ stop, Inst bi) {
+  pdl_enter();
+  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  out += blockIdx.z * bi.su;
+  f += blockIdx.z * bi.sf;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n || j > n) return;
+  const c2<T> d = xr::diag<T>(kh[(long long)j * pk + i], lvl::sides_at(i, j, n), beta);
+  const c2<T> fv = ldc<T>(f, (long long)j * pf + i);
+  c2<T> v;
+  if (!in) {
+    v = xr::cscale<T>(xr::cdiv<T>(fv, d), omega);
+  } else {
+    in += blockIdx.z * bi.su;
+    const Nbr b = neighbours(i, j, n);
+    const c2<T>* row = in + (long long)j * pu;
+    const c2<T> up = row[i];
+    const c2<T> r = xr::resid<T>(fv, up, xr::nb4<T>(row[b.iw], row[b.ie], in[(long long)b.js * pu + i],
+                                                   in[(long long)b.jn * pu + i]), d);
+    v = xr::cadd<T>(up, xr::cscale<T>(xr::cdiv<T>(r, d), omega));
+  }
+  out[(long long)j * po + i] = v;
 }
 
 // ---------------------------------------------------------------- Kaczmarz (Sec. 4-5)
@@ -302,20 +338,29 @@ __global__ void inject_kh_kernel(T* __restrict__ kh, int pk, const double* __res
 
 template <class T, class F2>
 cudaError_t gs_colour_t(void* u, int pu, const void* f, int pf, const void* kh, int pk, int n, int colour, double beta,
-                        const int* stop, cudaStream_t s, const Inst& bi) {
+                        const int* stop, cudaStream_t s, const Inst& bi, double omega) {
   dim3 g = grid2((n + 2) / 2, n + 1);
   g.z = bi.count;
   pdl_launch(gs_colour_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
-                                                     (T)beta, stop, bi);
+                                                     (T)beta, (T)omega, stop, bi);
   return cudaGetLastError();
 }
 template <class T, class F2>
 cudaError_t gs_first_t(void* u, int pu, const void* f, int pf, const void* kh, int pk, int n, int colour, double beta,
-                       const int* stop, cudaStream_t s, const Inst& bi) {
+                       const int* stop, cudaStream_t s, const Inst& bi, double omega) {
   dim3 g = grid2(n + 1, n + 1);
   g.z = bi.count;
   pdl_launch(gs_first_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)u, pu, (const F2*)f, pf, (const T*)kh, pk, n, colour,
-                                                    (T)beta, stop, bi);
+                                                    (T)beta, (T)omega, stop, bi);
+  return cudaGetLastError();
+}
+template <class T, class F2>
+cudaError_t jacobi_t(void* out, int po, const void* in, int pu, const void* f, int pf, const void* kh, int pk, int n,
+                     double beta, double omega, const int* stop, cudaStream_t s, const Inst& bi) {
+  dim3 g = grid2(n + 1, n + 1);
+  g.z = bi.count;
+  pdl_launch(jacobi_kernel<T, F2>, g, dim3(BX, BY), 0, s, (c2<T>*)out, po, (const c2<T>*)in, pu, (const F2*)f, pf,
+             (const T*)kh, pk, n, (T)beta, (T)omega, stop, bi);
   return cudaGetLastError();
 }
 template <class T, class F2>
@@ -340,17 +385,27 @@ cudaError_t restrict_t(void* fc, int pc, const void* u, int pu, const void* f, i
 }  // namespace
 
 cudaError_t launch_gs_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                             int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi) {
-  if (!fp32) return gs_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
-  if (f64_src) return gs_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
-  return gs_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+                             int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi,
+                             double omega) {
+  if (!fp32) return gs_colour_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
+  if (f64_src) return gs_colour_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
+  return gs_colour_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
 }
 
 cudaError_t launch_gs_first(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,
-                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi) {
-  if (!fp32) return gs_first_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
-  if (f64_src) return gs_first_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
-  return gs_first_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi);
+                            int n, int colour, double beta, const int* stop, cudaStream_t s, const Inst& bi,
+                            double omega) {
+  if (!fp32) return gs_first_t<double, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
+  if (f64_src) return gs_first_t<float, double2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
+  return gs_first_t<float, float2>(u, pu, f, pf, kh, pk, n, colour, beta, stop, s, bi, omega);
+}
+
+cudaError_t launch_jacobi(bool fp32, void* out, int po, const void* in, int pu, const void* f, int pf, bool f64_src,
+                          const void* kh, int pk, int n, double beta, double omega, const int* stop, cudaStream_t s,
+                          const Inst& bi) {
+  if (!fp32) return jacobi_t<double, double2>(out, po, in, pu, f, pf, kh, pk, n, beta, omega, stop, s, bi);
+  if (f64_src) return jacobi_t<float, double2>(out, po, in, pu, f, pf, kh, pk, n, beta, omega, stop, s, bi);
+  return jacobi_t<float, float2>(out, po, in, pu, f, pf, kh, pk, n, beta, omega, stop, s, bi);
 }
 
 cudaError_t launch_kacz_colour(bool fp32, void* u, int pu, const void* f, int pf, bool f64_src, const void* kh, int pk,

@@ -21,7 +21,8 @@ HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ENOTSETUP, HZ_EBREAKDOWN, HZ_EMAXIT, H
 VARIANTS = {"hyb": 0, "sl": 1, "hlm": 2, "sl_plain": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 OPS = {"L": 0, "M": 1}
-SMOOTHERS = {0: "gs", 1: "kaczmarz", 2: "direct"}
+SMOOTHERS = {0: "gs", 1: "kaczmarz", 2: "direct", 3: "jacobi", 4: "sor"}
+GS_SMOOTHERS = {"gs": 0, "jacobi": 3, "sor": 4}
 
 
 class HzError(RuntimeError):
@@ -33,7 +34,8 @@ class HzError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
                 ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int),
-                ("pass_variant", c_int), ("coarse_tail", c_int), ("kacz_form", c_int)]
+                ("pass_variant", c_int), ("coarse_tail", c_int), ("kacz_form", c_int),
+                ("gs_smoother", c_int), ("omega", c_double)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -126,11 +128,13 @@ KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3}
 
 
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
-              pass_variant=-1, coarse_tail=True, kacz_form="auto") -> Opts:
+              pass_variant=-1, coarse_tail=True, kacz_form="auto", gs_smoother="gs", omega=0.0) -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
     memory tiles; 1..8 = register streaming with 2**v rows per warp (FP32 form).
     kacz_form: kernel form of the Kaczmarz levels below the finest (one of KACZ_FORMS); a form that
-    does not apply to a level falls back to the default."""
+    does not apply to a level falls back to the default.
+    gs_smoother: "gs" (red-black Gauss-Seidel), "jacobi" (damped) or "sor" (red-black, over-relaxed)
+    on the levels the rules give Gauss-Seidel; omega: their factor (0 = 0.8 Jacobi, 1 SOR)."""
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
@@ -138,6 +142,8 @@ def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, gua
     o.pass_variant = int(pass_variant)
     o.coarse_tail = int(bool(coarse_tail))
     o.kacz_form = KACZ_FORMS[kacz_form]
+    o.gs_smoother = GS_SMOOTHERS[gs_smoother]
+    o.omega = float(omega)
     return o
 
 
@@ -181,7 +187,7 @@ class Problem:
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
                  nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1, coarse_tail=True,
-                 kacz_form="auto"):
+                 kacz_form="auto", gs_smoother="gs", omega=0.0):
         import torch
 
         L = lib()
@@ -195,7 +201,7 @@ class Problem:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
         self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant,
-                              coarse_tail, kacz_form)
+                              coarse_tail, kacz_form, gs_smoother, omega)
         self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))
