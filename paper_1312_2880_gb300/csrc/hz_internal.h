@@ -117,6 +117,9 @@ struct TailLevel {
   const void* kh;    // k H of the level (device, working precision, pitch pk)
   int pk;
   unsigned off_u, off_f, off_k, off_d, off_inv;  // shared-memory byte offsets (tail_layout)
+  // Kaczmarz levels: a row-major copy of k H for the residual, kept in the next level's u and f
+  // cells (unused until the restriction writes them); 0: the residual reads k H from global memory
+  unsigned off_kres;
 };
 struct TailArgs {
   int count;  // levels in the tail, the last the coarsest

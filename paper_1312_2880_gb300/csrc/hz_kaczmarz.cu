@@ -75,27 +75,49 @@ struct LevelSmem {
   }
 };
 
+// Global <-> shared copies visit the level in row-major order (coalesced on the global side) and
+// go through cp.async, one wait for all of them: a load per node at a time would put one memory
+// latency per node a thread holds on the launch's critical path. k H (fixed per problem) and the
+// zero guess are issued before the wait for the preceding kernel. The row constants then replace
+// k H in place.
+template <class T>
+__device__ __forceinline__ void level_kh_async(const LevelSmem<T>& S, const T* kh, int pk, int n) {
+  lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) {
+    lvl::cp_async<sizeof(T)>(&S.sinv[p], kh + (long long)j * pk + i);
+  });
+}
+template <class T>
+__device__ __forceinline__ void level_row_consts(const LevelSmem<T>& S, int n, T bA) {
+  lvl::for_blocked(n, [&](int i, int j, int p) { lvl::row_consts<T>(S.sinv[p], i, j, n, bA, &S.sd[p], &S.sinv[p]); });
+}
+
 template <class T>
 __global__ void __launch_bounds__(LB) kacz_level_pre_kernel(c2<T>* __restrict__ u, int pu, c2<T>* __restrict__ fc,
                                                              int pc, const c2<T>* __restrict__ f, int pf,
                                                              const T* __restrict__ kh, int pk, int n, T bA, T bB,
                                                              int nu, const int* __restrict__ stop, Inst bi) {
-  pdl_enter();
-  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
-  u += blockIdx.z * bi.su;
-  fc += blockIdx.z * bi.sc;
-  f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   const int Np = lvl::blocked_cells(n);
   LevelSmem<T> S(smem, Np);
   for (int q = threadIdx.x; q < Np; q += LB) S.su[q] = mk<T>(0, 0);
-  lvl::for_blocked(n, [&](int i, int j, int p) {
-    S.sf[p] = f[(long long)j * pf + i];
-    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
+  level_kh_async<T>(S, kh, pk, n);
+  pdl_enter();
+  if (stop && stop[blockIdx.z * bi.stop_stride]) {
+    lvl::cp_async_wait_all();
+    return;
+  }
+  u += blockIdx.z * bi.su;
+  fc += blockIdx.z * bi.sc;
+  f += blockIdx.z * bi.sf;
+  lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) {
+    lvl::cp_async<sizeof(c2<T>)>(&S.sf[p], f + (long long)j * pf + i);
   });
+  lvl::cp_async_wait_all();
+  __syncthreads();
+  level_row_consts<T>(S, n, bA);
   __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, false);
-  lvl::for_blocked(n, [&](int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
+  lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
   lvl::residual_blocked<T>(S.sd, S.su, S.sf, kh, pk, n, bB);  // the residual (natural) replaces the diagonals
   __syncthreads();
   lvl::restrict_fw<T>(fc, lvl::Natural{pc}, S.sd, n);
@@ -107,22 +129,37 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
                                                               const c2<T>* __restrict__ f, int pf,
                                                               const T* __restrict__ kh, int pk, int n, T bA, int nu,
                                                               const int* __restrict__ stop, Inst bi) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  LevelSmem<T> S(smem, lvl::blocked_cells(n));
+  level_kh_async<T>(S, kh, pk, n);
   pdl_enter();
-  if (stop && stop[blockIdx.z * bi.stop_stride]) return;
+  if (stop && stop[blockIdx.z * bi.stop_stride]) {
+    lvl::cp_async_wait_all();
+    return;
+  }
   u += blockIdx.z * bi.su;
   ec += blockIdx.z * bi.sc;
   f += blockIdx.z * bi.sf;
-  extern __shared__ __align__(16) unsigned char smem[];
-  LevelSmem<T> S(smem, lvl::blocked_cells(n));
+  // u and f into their cells, the coarse correction row-major (pitch wc) into the diagonals' cells
+  const int wc = n / 2 + 1;
+  lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) {
+    lvl::cp_async<sizeof(c2<T>)>(&S.su[p], u + (long long)j * pu + i);
+    lvl::cp_async<sizeof(c2<T>)>(&S.sf[p], f + (long long)j * pf + i);
+  });
+  lvl::for_nodes(wc, wc * wc, [&](int q, int I, int J) {
+    lvl::cp_async<sizeof(c2<T>)>(&S.sd[q], ec + (long long)J * pc + I);
+  });
+  lvl::cp_async_wait_all();
+  __syncthreads();
   lvl::for_blocked(n, [&](int i, int j, int p) {
-    const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
-    S.su[p] = xr::cadd<T>(u[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
-    S.sf[p] = f[(long long)j * pf + i];
-    lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, bA, &S.sd[p], &S.sinv[p]);
+    const c2<T>* e0 = S.sd + (j >> 1) * wc;
+    S.su[p] = xr::cadd<T>(S.su[p], xr::bilinear<T>(e0, e0 + wc, i >> 1, i & 1, j & 1));
   });
   __syncthreads();
+  level_row_consts<T>(S, n, bA);
+  __syncthreads();
   lvl::kacz_sweeps<T>(S.su, S.sf, S.sd, S.sinv, n, nu, true);
-  lvl::for_blocked(n, [&](int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
+  lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
 }
 
 template <class T, class F2>

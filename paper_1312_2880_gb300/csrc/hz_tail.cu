@@ -45,15 +45,18 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
   // Before the wait for the preceding kernel, everything that does not depend on it, so that with
   // programmatic dependent launch it overlaps that kernel: k H of every relaxation level (set up
   // once per problem), copied at once (cp.async, one wait) into K(l) on Gauss-Seidel levels and
-  // into the cells of 1/|a|^2 on Kaczmarz levels, where the row constants replace it; the zero
-  // guess of the Kaczmarz levels.
+  // into the cells of 1/|a|^2 on Kaczmarz levels, where the row constants replace it (plus a
+  // row-major copy for the residual when there is room); the zero guess of the Kaczmarz levels.
   for (int l = 0; l < last; ++l) {
     const TailLevel& L = A.lv[l];
     const T* kh = reinterpret_cast<const T*>(L.kh);
     if (L.kind == TAIL_KACZ) {
       for (int q = threadIdx.x; q < lvl::blocked_cells(L.n); q += TAIL_THREADS) U(l)[q] = mk<T>(0, 0);
-      lvl::for_blocked(L.n, [&](int i, int j, int p) {
-        lvl::cp_async<sizeof(T)>(&V(l)[p], kh + (long long)j * L.pk + i);
+      T* kres = L.off_kres ? reinterpret_cast<T*>(smem + L.off_kres) : nullptr;
+      lvl::for_nodes_blocked(L.n, [&](int q, int i, int j, int p) {
+        const T* src = kh + (long long)j * L.pk + i;
+        lvl::cp_async<sizeof(T)>(&V(l)[p], src);
+        if (kres) lvl::cp_async<sizeof(T)>(&kres[q], src);
       });
     } else {
       const int w = L.n + 1;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
     const TailLevel& L = A.lv[0];
     const int w = L.n + 1;
     if (L.kind == TAIL_KACZ)
-      lvl::for_blocked(L.n, [&](int i, int j, int p) {
+      lvl::for_nodes_blocked(L.n, [&](int, int i, int j, int p) {
         lvl::cp_async<sizeof(c2<T>)>(&F(0)[p], fin + (long long)j * A.pf + i);
       });
     else
@@ -108,7 +111,10 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
       lvl::residual<T>(R, U(l), F(l), lvl::Natural{L.n + 1}, K(l), L.n + 1, L.n, (T)L.bB);
     } else {
       lvl::kacz_sweeps<T>(U(l), F(l), D(l), V(l), L.n, L.nu, false);
-      lvl::residual_blocked<T>(R, U(l), F(l), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
+      if (L.off_kres)
+        lvl::residual_blocked<T>(R, U(l), F(l), reinterpret_cast<const T*>(smem + L.off_kres), L.n + 1, L.n, (T)L.bB);
+      else
+        lvl::residual_blocked<T>(R, U(l), F(l), reinterpret_cast<const T*>(L.kh), L.pk, L.n, (T)L.bB);
     }
     __syncthreads();
     const TailLevel& C = A.lv[l + 1];
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
 
   const int w = A.lv[0].n + 1;
   if (A.lv[0].kind == TAIL_KACZ)
-    lvl::for_blocked(A.lv[0].n, [&](int i, int j, int p) { uout[(long long)j * A.po + i] = U(0)[p]; });
+    lvl::for_nodes_blocked(A.lv[0].n, [&](int, int i, int j, int p) { uout[(long long)j * A.po + i] = U(0)[p]; });
   else
     lvl::for_nodes(w, w * w, [&](int q, int i, int j) { uout[(long long)j * A.po + i] = U(0)[q]; });
 }
@@ -171,6 +177,16 @@ size_t tail_layout(bool fp32, TailArgs* A) {
     }
     if (L.kind != TAIL_COARSE) rmax = std::max(rmax, Nn);
   }
+  for (int l = 0; l + 1 < A->count; ++l) {
+    TailLevel& L = A->lv[l];
+    const TailLevel& C = A->lv[l + 1];
+    L.off_kres = 0;
+    // the next level's u and f cells are contiguous; a Kaczmarz next level needs its zeroed u
+    const size_t need = (size_t)(L.n + 1) * (L.n + 1) * r;
+    const size_t nc = C.kind == TAIL_KACZ ? (size_t)lvl::blocked_cells(C.n) : (size_t)(C.n + 1) * (C.n + 1);
+    if (L.kind == TAIL_KACZ && C.kind != TAIL_KACZ && need <= (size_t)(C.off_f - C.off_u) + nc * c) L.off_kres = C.off_u;
+  }
+  A->lv[A->count - 1].off_kres = 0;
   A->off_r = take(rmax * c);
   const size_t m = (size_t)(A->lv[A->count - 1].n + 1) * (A->lv[A->count - 1].n + 1);
   A->off_ainv = 0;

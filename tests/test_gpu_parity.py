@@ -234,6 +234,29 @@ def test_solve_fp32_preconditioner(name):
     assert rel(xs, ref.x) <= 1e-3
 
 
+def test_solve_fp32_wedge_n512_timed_configuration():
+    """The timed workload in full (n = 512 wedge, k = 100, 8 sources, HYB, 8 levels) in the timed
+    configuration: FP32 V-cycle, fused-pass forms picked by the tile autotuner, coarse tail. A
+    full-size V-cycle is within the FP32 tolerance of the FP64 oracle's, and the solve reaches
+    relres 1e-6 on the oracle's true residual in at most 1.5x the oracle's iterations."""
+    wl = I.wedge_n512()
+    A, ref = _oracle_solve(wl, 1e-6)
+    P, H = pair(wl, precision="fp32")
+    try:
+        assert any(d["in_tail"] for d in P.schedule())
+        r = rand_c((wl.n + 1) ** 2, 82)
+        err = rel(P.vcycle(dev(r, wl.n)), o.vcycle(H, r))
+        x, info, hist = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+    finally:
+        P.close()
+    xs = x.cpu().numpy().ravel()
+    assert err <= 2e-5, err  # measured 2.9e-7
+    assert info["status"] == 0 and o.true_relres(A, wl.rhs.ravel(), xs) <= 1e-6
+    assert info["iterations"] <= 1.5 * ref.iterations + 2  # measured 161.5 against 149.5
+    # both iterates have relres <= 1e-6; measured difference 2.7e-6 of the largest entry
+    assert rel(xs, ref.x) <= 1e-4
+
+
 def test_host_buffer_solve_equals_device_solve():
     wl = I.plain_n64()
     P, _ = pair(wl)
