@@ -143,7 +143,10 @@ def workload(name: str):
     raise ValueError(name)
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str = "nccl"):
+    """Rank, world size and local GPU from the torchrun environment. One process per GPU; the
+    process group only carries the barriers and the max over ranks of the timings (each rank
+    solves its own replica). backend="gloo" runs the same path on host cores (no GPU)."""
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -152,23 +155,33 @@ def dist_setup(n_gpus: int):
     if world > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    elif backend == "nccl":
         torch.cuda.set_device(0)
     return world, rank, local
 
 
 def barrier_max(value: float, world: int) -> float:
+    """The maximum of `value` over all ranks, after a barrier (the slowest replica's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], device=dev, dtype=torch.float64)
     dist.barrier()
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_fields(world: int, ms: float) -> dict:
+    """Whole-job figures of N replicas (weak scaling): every rank completes one solve per step, so
+    the job completes `world` solves in the slowest rank's time `ms`."""
+    return {"n_gpus": world, "solves_per_s": round(world * 1e3 / ms, 3),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def l2_flush_buffer():
@@ -480,6 +493,7 @@ def run_ours(args):
     big_iter_ms = sum(sum(v) for v in per_big.values()) / 2
     Pr.close()
     del rrhs
+    replica = replica_fields(world, results["fp32"]["ms"])
     line = {
         "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
         "value": round(results["fp32"]["ms"], 3),
@@ -497,10 +511,10 @@ def run_ours(args):
         "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "medium": wl.meta.get("medium", ""),
                    "levels": wl.levels, "variant": wl.variant, "tol": tol, "rhs": wl.meta.get("rhs", ""),
                    "l2": "flushed before every timed solve (512 MB write); HBM rates measured on the roofline workload, larger than L2",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": replica["parallelism"]},
         "iterations": it32,
         "relres_true": results["fp32"]["relres_true"],
-        "solves_per_s": round(world * 1e3 / results["fp32"]["ms"], 3),
+        "solves_per_s": replica["solves_per_s"],
         "fp64_form": {"ms": round(results["fp64"]["ms"], 3), "iterations": results["fp64"]["iterations"],
                       "relres_true": results["fp64"]["relres_true"],
                       "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3)},

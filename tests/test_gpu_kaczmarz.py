@@ -5,7 +5,7 @@ All four forms take the same fixed-rounding row actions in the same colour order
 with any of them give the same bits, in FP32 and in FP64. The FP64 cluster form is also checked
 against the oracle per level step (1e-12) and per V-cycle (1e-11). Kaczmarz levels of
 n = 48 (49 rows: ragged bands), 64, 128 and 256, the coarse tail off so that the level runs in
-the form under test; batches retire instances inside a cluster launch.
+the form under test; batches retire instances inside every form's launches.
 """
 import numpy as np
 import pytest
@@ -149,21 +149,26 @@ def test_fp64_form_defaults_to_the_cluster():
         P.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batched_cluster_solves_equal_single_solves(precision):
+@pytest.mark.parametrize("form,precision", [("cluster", "fp32"), ("cluster", "fp64"), ("level", "fp32"),
+                                            ("level", "fp64"), ("tile", "fp32"), ("colour", "fp64")])
+def test_batched_solves_equal_single_solves(form, precision):
+    """Instances of a batch converge at different iterations; a retired instance's blocks leave each
+    Kaczmarz launch at its stop flag while the others go on, and every instance keeps the bits of
+    its single solve."""
     hz = hzmod()
     wl = wedge(256, 50.0)  # Kaczmarz on n = 32, outside the tail when the tail is off
     n = wl.n
     rhs = np.stack([I.point_source_rhs(n, I.random_interior_nodes(n, 2, s)) for s in (4, 5, 6)])
-    P = problem(wl, precision, "cluster", batch=3)
+    P = problem(wl, precision, form, batch=3)
     try:
-        assert P.schedule()[kacz_level(P.schedule(), 32)]["kacz_form"] == "cluster"
+        assert P.schedule()[kacz_level(P.schedule(), 32)]["kacz_form"] == form
         xb, infos = P.solve_batch(torch.from_numpy(rhs).cuda(), tol=1e-6, maxit=1000)
         xb = xb.cpu().numpy()
     finally:
         P.close()
+    assert len({i["iterations"] for i in infos}) > 1, infos
     for q in range(3):
-        S = problem(wl, precision, "cluster")
+        S = problem(wl, precision, form)
         try:
             x, info, _ = S.solve(torch.from_numpy(rhs[q]).cuda(), tol=1e-6, maxit=1000)
         finally:
