@@ -1,0 +1,146 @@
+"""Finest-level fused passes at full size (n = 4096, k = 1000, Gaussian random field: the grid the
+bench measures HBM rates on), in the launch configuration the solve uses (FP32 form, fused-pass
+form picked by the tile autotuner), checked against the oracle on sampled outputs.
+
+A pass's output at a node depends only on nearby data: the pre-pass (red-black Gauss-Seidel from
+a zero guess, residual, full weighting) reaches 3 fine nodes, the post-pass (bilinear correction,
+black then red) 2. So the oracle recomputes each sample on a window of 25 x 25 fine nodes cut from
+the full grid, as a grid of its own whose k is scaled to keep k h (the rows then equal the full
+grid's rows times a constant, which the right-hand side carries too). Window edges inside the
+square are artificial boundaries; only nodes at least 6 fine nodes from them are compared, and
+windows on the square's edges and corners check the Sommerfeld rows. Tolerance 1e-5 of the
+largest sampled value (FP32 arithmetic through one pass); the FP64 operator apply at 1e-13.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1312_2880_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NW = 24  # window intervals (even: the window's coarse grid is part of the full coarse grid)
+MARGIN = 6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1312_2880_gb300 import build
+
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_1312_2880_gb300 import hz
+
+    wl = I.grf_n4096()
+    P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision="fp32", levels=wl.levels, k_ref=wl.k_ref)
+    yield wl, P
+    P.close()
+
+
+def rand_c(shape, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def windows(n):
+    """Window origins (even): the four corners, edge midpoints, strip and segment seams of the
+    streaming form, and seeded interior positions."""
+    last = n - NW
+    pts = [(0, 0), (last, 0), (0, last), (last, last), (n // 2, 0), (0, n // 2), (last, n // 2), (n // 2, last)]
+    pts += [(58 * s - 14, 64 * s - 12) for s in (3, 17, 40)]
+    g = np.random.default_rng(2024)
+    pts += [(2 * int(a), 2 * int(b)) for a, b in g.integers(1, last // 2, size=(6, 2))]
+    return pts
+
+
+def mask(i0, j0, n, m):
+    """Nodes (step m apart, m = 1 fine, 2 coarse) of the window that its artificial edges do not reach."""
+    idx = np.arange(0, NW + 1, m)
+    lo_i = 0 if i0 == 0 else MARGIN
+    hi_i = NW if i0 + NW == n else NW - MARGIN
+    lo_j = 0 if j0 == 0 else MARGIN
+    hi_j = NW if j0 + NW == n else NW - MARGIN
+    oki = (idx >= lo_i) & (idx <= hi_i)
+    okj = (idx >= lo_j) & (idx <= hi_j)
+    return okj[:, None] & oki[None, :]
+
+
+def window_level(wl, P, i0, j0):
+    h, hw = 1.0 / wl.n, 1.0 / NW
+    kw = wl.kfield[j0:j0 + NW + 1, i0:i0 + NW + 1] * (h / hw)
+    d = P.schedule()[0]
+    H = o.build_hierarchy(NW, kw, wl.k_ref * h / hw, wl.variant, 2, ops=[(d["relax_op"], "gs", d["resid_op"])])
+    return H.levels[0], (h / hw) ** 2  # rows of the window = rows of the full grid x s; s = (h / hw)^2
+
+
+def cut(a, i0, j0, m=1):
+    return a[j0 // m:(j0 + NW) // m + 1, i0 // m:(i0 + NW) // m + 1]
+
+
+def test_presmooth_and_restriction_at_full_size(case):
+    wl, P = case
+    n = wl.n
+    f = rand_c((n + 1, n + 1), 41)
+    u, fc = P.level_presmooth(0, torch.from_numpy(f).cuda())
+    u, fc = u.cpu().numpy(), fc.cpu().numpy()
+    diffs = []
+    for i0, j0 in windows(n):
+        lv, s = window_level(wl, P, i0, j0)
+        fw = (cut(f, i0, j0) * s).ravel()
+        uw = o.helmholtz.relax(lv, fw, np.zeros_like(fw), post=False)
+        fcw = lv.R @ (fw - lv.B @ uw)
+        mf, mc = mask(i0, j0, n, 1), mask(i0, j0, n, 2)
+        ref_u, ref_c = uw.reshape(NW + 1, NW + 1)[mf], fcw.reshape(NW // 2 + 1, NW // 2 + 1)[mc] / s
+        diffs += [np.abs(cut(u, i0, j0)[mf] - ref_u).max() / np.abs(ref_u).max(),
+                  np.abs(cut(fc, i0, j0, 2)[mc] - ref_c).max() / np.abs(ref_c).max()]
+    assert max(diffs) <= 1e-5, max(diffs)
+
+
+def test_correction_and_postsmooth_at_full_size(case):
+    wl, P = case
+    n, nc = wl.n, wl.n // 2
+    f, u0, ec = rand_c((n + 1, n + 1), 42), rand_c((n + 1, n + 1), 43), rand_c((nc + 1, nc + 1), 44)
+    dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    u = P.level_postsmooth(0, dev(f), dev(u0), dev(ec)).cpu().numpy()
+    diffs = []
+    for i0, j0 in windows(n):
+        lv, s = window_level(wl, P, i0, j0)
+        fw = (cut(f, i0, j0) * s).ravel()
+        start = cut(u0, i0, j0).ravel() + lv.P @ cut(ec, i0, j0, 2).ravel()
+        uw = o.helmholtz.relax(lv, fw, start, post=True)
+        mf = mask(i0, j0, n, 1)
+        ref = uw.reshape(NW + 1, NW + 1)[mf]
+        diffs.append(np.abs(cut(u, i0, j0)[mf] - ref).max() / np.abs(ref).max())
+    assert max(diffs) <= 1e-5, max(diffs)
+
+
+@pytest.mark.parametrize("op", ["L", "M"])
+def test_operator_apply_at_full_size(case, op):
+    """A u in FP64 (the operator of the Krylov kernels) at every node of each window: the stencil
+    reaches one node, so only the artificial edges' own rows are left out (tolerance 1e-13)."""
+    wl, P = case
+    n = wl.n
+    u = rand_c((n + 1, n + 1), 45)
+    v = P.apply(torch.from_numpy(u).cuda(), op).cpu().numpy()
+    h, hw = 1.0 / n, 1.0 / NW
+    diffs = []
+    for i0, j0 in windows(n):
+        kw = cut(wl.kfield, i0, j0) * (h / hw)
+        A = o.helmholtz_matrix(NW, kw, 0.5 if op == "M" else 0.0)
+        ref = (A @ cut(u, i0, j0).ravel()).reshape(NW + 1, NW + 1) / (h / hw) ** 2
+        m = np.ones((NW + 1, NW + 1), dtype=bool)
+        if i0 > 0:
+            m[:, 0] = False
+        if i0 + NW < n:
+            m[:, NW] = False
+        if j0 > 0:
+            m[0, :] = False
+        if j0 + NW < n:
+            m[NW, :] = False
+        diffs.append(np.abs(cut(v, i0, j0)[m] - ref[m]).max() / np.abs(ref[m]).max())
+    assert max(diffs) <= 1e-13, max(diffs)
