@@ -517,7 +517,8 @@ def run_ours(args):
         "solves_per_s": replica["solves_per_s"],
         "fp64_form": {"ms": round(results["fp64"]["ms"], 3), "iterations": results["fp64"]["iterations"],
                       "relres_true": results["fp64"]["relres_true"],
-                      "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3)},
+                      "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3),
+                      "tile_autotuner": results["fp64"]["forms"]},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "batched": batched,
         "serving": serving,

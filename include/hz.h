@@ -82,10 +82,11 @@ typedef struct {
   double k_ref;  /* wavenumber that sets each level's scale c = k_ref H; 0 = mean of k(x) */
   int batch;     /* right-hand sides solved together by hz_solve_batch (1..1024, default 1); every
                     kernel launch then covers all of them and finished ones retire individually */
-  int pass_variant; /* kernel form of the two fused passes of each Gauss-Seidel level in the FP32 form
-                       (the FP64 form always uses 0): -1 (default) = chosen per level at setup by
-                       timing every form on the level's arrays (tile autotuner); 0 = shared-memory
-                       tiles; 1..8 = register streaming with 2^v rows per warp */
+  int pass_variant; /* kernel form of the two fused passes of each Gauss-Seidel level, in either
+                       precision: -1 (default) = chosen per level at setup by timing every form on
+                       the level's arrays (tile autotuner; the FP64 form keeps tiles); 0 =
+                       shared-memory tiles; 1..8 = register streaming with 2^v rows per warp. Every
+                       form gives the same bits. */
   int coarse_tail;  /* 1 (default): the smallest levels, from the first whose whole V-cycle below it
                        fits one block's shared memory down to the coarsest, run as one launch (same
                        operations, same results as the per-level kernels for one-sweep Gauss-Seidel

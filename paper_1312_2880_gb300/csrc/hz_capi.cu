@@ -43,7 +43,7 @@ struct Level {
   void* u = nullptr;  // working precision complex
   void* f = nullptr;  // working precision complex (levels >= 1)
   void* u2 = nullptr; // result of the fused post-smoothing pass (levels >= 1)
-  int var_down = 0, var_up = 0;  // fused-pass variants (FP32 form; picked by the tile autotuner)
+  int var_down = 0, var_up = 0;  // fused-pass variants (picked by the tile autotuner)
   int kform = 0;                 // hz_kacz_form of a Kaczmarz level (set up by plan_kaczmarz)
   double omega = 1.0;            // relaxation factor of a Jacobi or SOR level
 };
@@ -976,13 +976,13 @@ void plan_tail(hz_problem* P) {
 }
 
 // ------------------------------------------------------------------ tile autotuner
-// Every fused Gauss-Seidel level of the FP32 form runs each candidate variant of its two passes
+// Every fused Gauss-Seidel level runs each candidate variant of its two passes
 // (shared-memory tiles, or register streaming with 2 .. 256 rows per warp) on its own arrays,
 // with all right-hand sides of the batch: one untimed launch, then the best of three timings of
 // five back-to-back launches with CUDA events on the library stream. The fastest is kept, and cached per
-// (n_l, batch, pass, finest level or not) for later problems of the same shape.
+// (n_l, batch, pass, finest level or not, precision) for later problems of the same shape.
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
 
 // Candidates for a level of n_l intervals: streaming needs n_l >= 4; segments longer than the
 // level add nothing over the one that covers it.
@@ -1034,18 +1034,22 @@ cudaError_t autotune(hz_problem* P) {
   for (int l = 0; l < P->plan.levels - 1; ++l) {
     Level& L = P->lv[l];
     if (!fused(P, l) || (P->tail_start > 0 && l >= P->tail_start)) continue;  // tail levels run in hz_tail.cu
-    if (!P->plan.fp32) {
-      L.var_down = L.var_up = 0;
-      continue;
-    }
     if (P->opts.pass_variant >= 0) {
       const bool ok = P->opts.pass_variant == 0 || L.n >= 4;
       L.var_down = L.var_up = ok ? P->opts.pass_variant : 0;
       continue;
     }
+    if (!P->plan.fp32) {
+      // FP64 levels keep the tiles: the passes are bound by the FP64 pipe, the streaming forms
+      // recompute halo rows (more FP64 work), and timed in the solve they were slower at the
+      // finest level (n = 512: 80 us against 60 us per pre-pass), although isolated launches
+      // ranked them ahead.
+      L.var_down = L.var_up = 0;
+      continue;
+    }
     for (int up = 0; up < 2; ++up) {
       int& var = up ? L.var_up : L.var_down;
-      const auto key = std::make_tuple(L.n, B, up, l == 0 ? 1 : 0);
+      const auto key = std::make_tuple(L.n, B, up, l == 0 ? 1 : 0, P->plan.fp32 ? 1 : 0);
       {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);

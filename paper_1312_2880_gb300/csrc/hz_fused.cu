@@ -362,21 +362,22 @@ cudaError_t ps_t(void* out, int po, const void* upre, int pu, const void* ec, in
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
                                    const void* kh, int pk, int n, double bA, double bB, const int* stop,
                                    cudaStream_t s, const Inst& bi, int variant) {
-  if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
-  if (f64_src) return cudaErrorInvalidValue;  // the FP32 form's inputs are FP32
+  if (fp32 && f64_src) return cudaErrorInvalidValue;  // the FP32 form's inputs are FP32
   if (variant >= 1 && variant < FUSED_VARIANTS)
-    return launch_smooth_restrict_stream(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stream_rows(variant), stop, s, bi);
+    return launch_smooth_restrict_stream(fp32, u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stream_rows(variant), stop, s,
+                                         bi);
+  if (!fp32) return sr_t<double, double2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
   return sr_t<float, float2>(u, pu, fc, pc, f, pf, kh, pk, n, bA, bB, stop, s, bi);
 }
 
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
                                   const int* stop, cudaStream_t s, const Inst& bi, int variant) {
-  if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
-  if (f64_src || out_f64) return cudaErrorInvalidValue;  // the FP32 form's inputs and outputs are FP32
+  if (fp32 && (f64_src || out_f64)) return cudaErrorInvalidValue;  // the FP32 form's inputs and outputs are FP32
   if (variant >= 1 && variant < FUSED_VARIANTS)
-    return launch_prolong_smooth_stream(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stream_rows(variant), stop, s,
-                                        bi);
+    return launch_prolong_smooth_stream(fp32, out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stream_rows(variant),
+                                        stop, s, bi);
+  if (!fp32) return ps_t<double, double2, double2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
   return ps_t<float, float2, float2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, n, bA, stop, s, bi);
 }
 

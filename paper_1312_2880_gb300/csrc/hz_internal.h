@@ -70,8 +70,9 @@ cudaError_t launch_coarse_solve(bool fp32, void* u, int pu, const void* f, int p
 // Fused passes for a Gauss-Seidel level with one sweep each way (hz_fused.cu). smooth_restrict
 // writes u (pre-sweep from a zero guess) and fc (coarse right-hand side, h^2-scaled for the
 // coarse level); prolong_smooth writes out = post-sweep(upre + P ec), as double2 when out_f64.
-// variant (FP32 form only): 0 = shared-memory tiles; 1 .. FUSED_VARIANTS-1 = register streaming
-// (hz_stream.cu) with stream_rows(variant) rows per warp. The FP64 form always uses tiles.
+// variant: 0 = shared-memory tiles; 1 .. FUSED_VARIANTS-1 = register streaming (hz_stream.cu)
+// with stream_rows(variant) rows per warp, in either form (inputs and outputs of the level's own
+// precision).
 constexpr int FUSED_VARIANTS = 9;
 inline int stream_rows(int variant) { return 1 << variant; }
 cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, bool f64_src,
@@ -80,11 +81,11 @@ cudaError_t launch_smooth_restrict(bool fp32, void* u, int pu, void* fc, int pc,
 cudaError_t launch_prolong_smooth(bool fp32, void* out, int po, bool out_f64, const void* upre, int pu, const void* ec,
                                   int pc, const void* f, int pf, bool f64_src, const void* kh, int pk, int n, double bA,
                                   const int* stop, cudaStream_t s, const Inst& bi = Inst(), int variant = 0);
-// Register-streaming forms (FP32; n >= 4; u / upre and kh rows 16-byte aligned).
-cudaError_t launch_smooth_restrict_stream(void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
-                                          int pk, int n, double bA, double bB, int seg_rows, const int* stop,
-                                          cudaStream_t s, const Inst& bi);
-cudaError_t launch_prolong_smooth_stream(void* out, int po, const void* upre, int pu, const void* ec, int pc,
+// Register-streaming forms (FP32 or FP64; n >= 4; u / upre and kh rows 16-byte aligned).
+cudaError_t launch_smooth_restrict_stream(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf,
+                                          const void* kh, int pk, int n, double bA, double bB, int seg_rows,
+                                          const int* stop, cudaStream_t s, const Inst& bi);
+cudaError_t launch_prolong_smooth_stream(bool fp32, void* out, int po, const void* upre, int pu, const void* ec, int pc,
                                          const void* f, int pf, const void* kh, int pk, int n, double bA, int seg_rows,
                                          const int* stop, cudaStream_t s, const Inst& bi);
 // Kaczmarz level kernels (hz_kaczmarz.cu). The whole-level pair keeps the level in one block's
