@@ -45,8 +45,14 @@ __device__ __forceinline__ c2<T> nb_sum(const c2<T>* s, int rw, int c, int r, in
 
 // ---------------------------------------------------------------- interior tiles
 // Tiles whose region lies strictly inside the square (no boundary rows, no mirrors, every node
-// present) run these paths: a 32 x 8 thread layout walks rows and columns with fixed strides,
-// so there is no index division and no per-node bounds or boundary logic.
+// present) run these paths in FP32: a 32 x 8 thread layout walks rows and columns with fixed
+// strides, so there is no index division and no per-node bounds or boundary logic. Their rows do
+// not fill whole warps (a region row of 69 nodes takes a full warp pass plus one of 2-5 lanes).
+// GB300 issues an FP64 warp instruction at the same cost however few lanes are active, so FP64
+// tiles take the general path below, whose flat index walk keeps warps full (measured: the FP64
+// solve of the n = 512 wedge 138 -> 117 ms, the same bits).
+template <class T>
+__host__ __device__ constexpr bool interior_path() { return sizeof(T) == 4; }
 
 constexpr int TXN = 32, TYN = 8;
 
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(FT) smooth_restrict_kernel(c2<T>* __restrict__
   T* sk = reinterpret_cast<T*>(sf + RN);
   const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
   const int gx = x0 - 3, gy = y0 - 3;
-  if (gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
+  if (interior_path<T>() && gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
     smooth_restrict_inner<T, F2>(u, pu, fc, pc, f, pf, kh, pk, bA, bB, su, sf, sk, gx, gy);
     return;
   }
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   T* sk = reinterpret_cast<T*>(sf + RN);
   const int x0 = blockIdx.x * W, y0 = blockIdx.y * HH;
   const int gx = x0 - 2, gy = y0 - 2;
-  if (gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
+  if (interior_path<T>() && gx >= 1 && gy >= 1 && gx + RW <= n && gy + RH <= n) {
     prolong_smooth_inner<T, F2, O2>(out, po, upre, pu, ec, pc, f, pf, kh, pk, bA, su, sf, sk, gx, gy);
     return;
   }
