@@ -275,19 +275,33 @@ __device__ __forceinline__ void gs_black(c2<T>* u, const c2<T>* f, const T* k, i
 // (the same cadd of u and the bilinear value that a separate correction pass would store) and
 // the red phase reads the new black values. Same results as a correction pass followed by the
 // black and red updates.
+// The red neighbours of a black node are coincident with coarse nodes (both indices even) or at
+// coarse cell centres (both odd): on an even row the west and east ones are coincident and the
+// south and north ones centres, on an odd row the reverse (mirror neighbours keep the parity, n
+// being even). The black nodes of the even rows come first in the walk and those of the odd rows
+// after, so a warp rarely mixes the two cases; the corrected values are the ones bilinear_at
+// gives (same operations).
 template <class T, class LE>
 __device__ __forceinline__ void gs_post_corrected(c2<T>* u, const c2<T>* f, const T* k, int n, T bA, const c2<T>* e,
                                                   LE le) {
-  const int w = n + 1;
-  auto corrected = [&](int i, int j) {
-    return xr::cadd<T>(u[j * w + i], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
+  const int w = n + 1, HW = (w + 1) / 2, even_slots = (n / 2 + 1) * HW;
+  auto coinc = [&](int i, int j) { return xr::cadd<T>(u[j * w + i], e[le.at(i >> 1, j >> 1)]); };
+  auto centre = [&](int i, int j) {
+    const int I = i >> 1, J = j >> 1;
+    return xr::cadd<T>(u[j * w + i], xr::cscale<T>(xr::cadd<T>(xr::cadd<T>(e[le.at(I, J)], e[le.at(I, J + 1)]),
+                                                                xr::cadd<T>(e[le.at(I + 1, J)], e[le.at(I + 1, J + 1)])),
+                                                    (T)0.25));
   };
-  for_colour<T>(n, 1, [&](int i, int j) {
+  for (int q = threadIdx.x; q < even_slots + (n / 2) * HW; q += blockDim.x) {
+    const int odd = q >= even_slots, r = odd ? q - even_slots : q;
+    const int jj = r / HW, h = r - jj * HW, j = 2 * jj + odd, i = 2 * h + ((1 + j) & 1);
+    if (i > n) continue;
     const Nbr b = neighbours(i, j, n);
     const int p = j * w + i;
-    const c2<T> nb = xr::nb4<T>(corrected(b.iw, j), corrected(b.ie, j), corrected(i, b.js), corrected(i, b.jn));
+    const c2<T> nb = odd ? xr::nb4<T>(centre(b.iw, j), centre(b.ie, j), coinc(i, b.js), coinc(i, b.jn))
+                         : xr::nb4<T>(coinc(b.iw, j), coinc(b.ie, j), centre(i, b.js), centre(i, b.jn));
     u[p] = xr::gs<T>(f[p], nb, xr::diag<T>(k[p], sides_at(i, j, n), bA));
-  });
+  }
   __syncthreads();
   for_colour<T>(n, 0, [&](int i, int j) {
     const int p = j * w + i;
@@ -349,15 +363,24 @@ __device__ __forceinline__ void restrict_fw(c2<T>* fc, LC lc, const c2<T>* r, in
     for_nodes(wc, wc * wc, [&](int, int I, int J) { fc[lc.at(I, J)] = xr::fw_node<T>(r, n + 1, n, I, J); });
 }
 // u (layout lu) += P e (e: (n/2 + 1)^2 grid, layout le).
+// On a Blocked level the nodes are walked one parity class (i mod 2, j mod 2) at a time, so the
+// threads of a warp take the same interpolation case.
 template <class T, class LU, class LE>
 __device__ __forceinline__ void prolong_add(c2<T>* u, LU lu, const c2<T>* e, LE le, int n) {
-  auto add = [&](int i, int j, int p) {
-    u[p] = xr::cadd<T>(u[p], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
-  };
-  if constexpr (LU::blocked)
-    for_blocked(n, add);
-  else
-    for_nodes(n + 1, (n + 1) * (n + 1), [&](int q, int i, int j) { add(i, j, q); });
+  if constexpr (LU::blocked) {
+#pragma unroll
+    for (int cls = 0; cls < 4; ++cls) {
+      const int oi = cls & 1, oj = cls >> 1, wi = (n - oi) / 2 + 1, wj = (n - oj) / 2 + 1;
+      for_nodes(wi, wi * wj, [&](int, int I, int J) {
+        const int p = lu.at(2 * I + oi, 2 * J + oj);
+        u[p] = xr::cadd<T>(u[p], bilinear_at<T>(e, le, I, J, oi, oj));
+      });
+    }
+  } else {
+    for_nodes(n + 1, (n + 1) * (n + 1), [&](int q, int i, int j) {
+      u[q] = xr::cadd<T>(u[q], bilinear_at<T>(e, le, i >> 1, j >> 1, i & 1, j & 1));
+    });
+  }
 }
 // Row r of the coarsest solve u = A^-1 f (inverse stored transposed, m x m), accumulated in column
 // order. The inverse is read from global memory eight columns at a time before they are summed,
