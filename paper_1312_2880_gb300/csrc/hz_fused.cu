@@ -281,11 +281,24 @@ __global__ void __launch_bounds__(FT) prolong_smooth_kernel(O2* __restrict__ out
   for (int q = tid; q < RN; q += FT) {
     int r = q / RW, c = q - r * RW, i = gx + c, j = gy + r;
     if (in_grid(i, j, n)) {
-      const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
-      const c2<T>* e0 = ec + (long long)J * pc;
-      su[q] = xr::cadd<T>(upre[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, I, oi, oj));
       sf[q] = ldc<T>(f, (long long)j * pf + i);
       sk[q] = kh[(long long)j * pk + i];
+    }
+  }
+  // u_pre + P e, one parity class (i mod 2, j mod 2) after the other (gx and gy are even), so that
+  // a warp takes one interpolation case: a warp mixing the four cases would issue all of them
+  constexpr int CE = (RW + 1) / 2, CO = RW / 2, RE = (RH + 1) / 2, RO = RH / 2;
+  for (int q = tid; q < RN; q += FT) {
+    int oi, oj, t;
+    if (q < CE * RE) { oi = 0; oj = 0; t = q; }
+    else if (q < CE * RE + CO * RE) { oi = 1; oj = 0; t = q - CE * RE; }
+    else if (q < CE * RE + CO * RE + CE * RO) { oi = 0; oj = 1; t = q - CE * RE - CO * RE; }
+    else { oi = 1; oj = 1; t = q - CE * RE - CO * RE - CE * RO; }
+    const int wcls = oi ? CO : CE, mr = t / wcls, mc = t - mr * wcls;
+    const int r = 2 * mr + oj, c = 2 * mc + oi, i = gx + c, j = gy + r;
+    if (in_grid(i, j, n)) {
+      const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
+      su[r * RW + c] = xr::cadd<T>(upre[(long long)j * pu + i], xr::bilinear<T>(e0, e0 + pc, i >> 1, oi, oj));
     }
   }
   __syncthreads();
