@@ -319,8 +319,9 @@ const char* hz_kernel_name(int kernel);
  * v = A u on the (n+1)^2 grid (A = L^h for beta = 0, M^h = L^h + i k^2 beta otherwise; physical
  * units, as hz_apply) and dot = <w, v> = sum_p conj(w_p) v_p, in one pass; no problem object.
  *  kh      : device, (n+1)^2 doubles, k(x) h at each node.
- *  u, w, v : device, (n+1)^2 complex128; v must not alias u or w.
- *  dot     : device, one complex128.
+ *  u, w, v : device, (n+1)^2 complex128; u and w may be the same array; v shares no byte with
+ *            u, w or kh.
+ *  dot     : device, one complex128, sharing no byte with v, u, w or kh.
  *  stream  : a cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
  * Allocates nothing: its only scratch (per-block partial sums and a counter, about 33 KB) is a
  * fixed array in the library's device memory, present on every device that loads the library
@@ -328,7 +329,7 @@ const char* hz_kernel_name(int kernel);
  * address (cudaGetSymbolAddress): make it before any stream capture. Every call shares the array
  * and clears its counter, so calls that overlap on the GPU (other streams or host threads) race
  * and give wrong results: order them. Returns HZ_EINVAL for n outside [2, HZ_NOALLOC_MAX_N], a
- * null pointer or aliasing (nothing launched), HZ_ECUDA if a launch fails. */
+ * null pointer or overlapping output and input ranges (nothing launched), HZ_ECUDA if a launch fails. */
 #define HZ_NOALLOC_MAX_N 32768
 hz_status hz_apply_dot_noalloc(int n, const double* kh, double beta, const double* u, const double* w, double* v,
                                double* dot, void* stream);

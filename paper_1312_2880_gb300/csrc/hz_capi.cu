@@ -802,6 +802,9 @@ hz_status instance_status(const KState& hs, int maxit, double* iters) {
     *iters = (double)maxit;
     return HZ_EMAXIT;
   }
+  // The recurrence converged but the true residual b - A x (the quantity that stops the solve)
+  // did not follow, and the restarts from it are used up or maxit was reached.
+  if (hs.bnorm2 > 0 && !(hs.trr <= hs.tol2)) return HZ_EMAXIT;
   return HZ_OK;
 }
 

@@ -10,6 +10,7 @@
 // process exits.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "hz_common.cuh"
@@ -102,13 +103,28 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
 }  // namespace
 }  // namespace hz
 
 extern "C" hz_status hz_apply_dot_noalloc(int n, const double* kh, double beta, const double* u, const double* w,
                                           double* v, double* dot, void* stream) {
   if (n < 2 || n > HZ_NOALLOC_MAX_N || !kh || !u || !w || !v || !dot) return HZ_EINVAL;
-  if ((const double*)v == u || (const double*)v == w) return HZ_EINVAL;
+  {
+    // v and dot are written while u, w and kh are still being read (by other blocks): no output
+    // may share a byte with an input or with the other output.
+    const size_t N = (size_t)(n + 1) * (size_t)(n + 1);
+    const size_t cb = sizeof(double2) * N, rb = sizeof(double) * N, db = sizeof(double2);
+    if (hz::overlaps(v, cb, u, cb) || hz::overlaps(v, cb, w, cb) || hz::overlaps(v, cb, kh, rb) ||
+        hz::overlaps(dot, db, v, cb) || hz::overlaps(dot, db, u, cb) || hz::overlaps(dot, db, w, cb) ||
+        hz::overlaps(dot, db, kh, rb))
+      return HZ_EINVAL;
+  }
   void* scratch = nullptr;
   if (hz::scratch_address(&scratch) != cudaSuccess) return HZ_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;

@@ -46,6 +46,8 @@ def device_io(n: int, source: tuple):
 
 
 class Server:
+    ENOMEM = 2  # hz_status of a request whose hierarchy can never fit the budget
+
     def __init__(self, hbm_budget: int, precision: str = "fp32", tol: float = 1e-6, maxit: int = 4000,
                  max_active: int = 32, variant: str = "hyb", keep_solutions: bool = False, backend=None,
                  make_io=device_io):
@@ -109,9 +111,19 @@ class Server:
     def submit(self, job: Job):
         self.queue.append(job)
 
+    def _reject(self, job: Job, now: float, status: int, why: str):
+        job.start = job.end = now
+        job.result = {"status": status, "error": why, "iterations": 0.0}
+        self.done.append(job)
+
     def _admit(self, now: float):
         while self.queue and len(self.active) < self.max_active:
             job = self.queue[0]
+            if job.key not in self.idle and self.footprint(job.n) > self.budget:
+                # no amount of eviction makes room: fail the request instead of waiting forever
+                self.queue.popleft()
+                self._reject(job, now, self.ENOMEM, "footprint exceeds the device-memory budget")
+                continue
             prob = self._acquire(job)
             if prob is None:
                 break  # memory full: wait for a solve to finish

@@ -79,3 +79,27 @@ def test_schedule_of_table1_setting(L):
     sch = hz.describe_hierarchy(64, kf, variant="hyb", levels=4, k_ref=40.0)
     assert [(d["relax_op"], d["smoother"], d["nu"]) for d in sch] == [
         ("M", "gs", 1), ("M", "kaczmarz", 4), ("M", "gs", 1), ("L", "direct", 0)]
+
+
+def test_noalloc_rejects_overlapping_outputs_before_any_device_call(L):
+    """The allocation-free entry point checks byte ranges on the host: an output that shares a byte
+    with an input, or with the other output, is refused before anything touches the device (the
+    addresses below are never dereferenced)."""
+    from ctypes import c_void_p
+
+    n = 8
+    cb = 16 * (n + 1) ** 2  # bytes of one complex128 grid vector
+    base = 1 << 40
+    kh, u, w, v, dot = base, base + 4 * cb, base + 6 * cb, base + 8 * cb, base + 10 * cb
+
+    def call(kh_, u_, w_, v_, dot_):
+        return L.hz_apply_dot_noalloc(n, c_void_p(kh_), 0.5, c_void_p(u_), c_void_p(w_), c_void_p(v_),
+                                      c_void_p(dot_), None)
+
+    assert call(kh, u, w, u + 16, dot) == hz.HZ_EINVAL  # v starts inside u
+    assert call(kh, u, w, w - cb + 16, dot) == hz.HZ_EINVAL  # v ends inside w
+    assert call(kh, u, w, kh + 8, dot) == hz.HZ_EINVAL  # v inside kh
+    assert call(kh, u, w, v, v + cb - 16) == hz.HZ_EINVAL  # dot is v's last element
+    assert call(kh, u, w, v, u) == hz.HZ_EINVAL  # dot inside u
+    assert call(kh, u, w, v, w + 8) == hz.HZ_EINVAL  # dot straddles w
+    assert call(kh, u, w, v, kh) == hz.HZ_EINVAL  # dot inside kh

@@ -73,3 +73,15 @@ def test_latency_counts_from_arrival(server):
     assert out["completed"] == 2 and out["p50_ms"] is not None
     for j in s.done:
         assert j.end >= j.arrival and j.start >= j.arrival
+
+
+def test_request_larger_than_the_budget_is_rejected_not_queued_forever(server):
+    FakeProblem.built = 0
+    foot64 = 1000 * 64 + 2 * 16 * 65 ** 2
+    s = server(budget=foot64, max_active=4)
+    jobs = [_job(0, 64, ("a",)), _job(1, 512, ("big",)), _job(2, 64, ("a",))]
+    out = s.run(jobs, realtime=False, time_limit=30.0)
+    assert out["completed"] == 3 and out["converged"] == 2
+    assert out["statuses"] == {0: 2, serve.Server.ENOMEM: 1}
+    big = [j for j in s.done if j.rid == 1][0]
+    assert big.result["status"] == serve.Server.ENOMEM and "budget" in big.result["error"]
