@@ -84,9 +84,9 @@ typedef struct {
                     kernel launch then covers all of them and finished ones retire individually */
   int pass_variant; /* kernel form of the two fused passes of each Gauss-Seidel level, in either
                        precision: -1 (default) = chosen per level at setup by timing every form on
-                       the level's arrays (tile autotuner; the FP64 form keeps tiles); 0 =
-                       shared-memory tiles; 1..8 = register streaming with 2^v rows per warp. Every
-                       form gives the same bits. */
+                       the level's arrays (tile autotuner; FP64 levels below n_l = 2048 keep
+                       tiles); 0 = shared-memory tiles; 1..8 = register streaming with 2^v rows
+                       per warp. Every form gives the same bits. */
   int coarse_tail;  /* 1 (default): the smallest levels, from the first whose whole V-cycle below it
                        fits one block's shared memory down to the coarsest, run as one launch (same
                        operations, same results as the per-level kernels for one-sweep Gauss-Seidel
@@ -102,7 +102,16 @@ typedef struct {
                        levels run unfused, one launch per sweep or colour, outside the coarse tail. */
   double omega;     /* relaxation factor of Jacobi or SOR in [0, 2); 0 (default) = 0.8 for Jacobi,
                        1 for SOR (then SOR is Gauss-Seidel) */
+  int kacz_rule;    /* which levels relax by Kaczmarz, the normal-equation relaxation Sec. 4 brings in
+                       where Gauss-Seidel is no smoother (hz_kacz_rule): HZ_KACZ_RULE_BAND (default)
+                       = every level with some node whose k(x) H lies in [0.625 sqrt 2, 2 sqrt 2)
+                       (in a heterogeneous medium one level spans k_min H .. k_max H, so several
+                       levels can qualify); HZ_KACZ_RULE_BINS = only the levels whose scale
+                       c = k_ref H is in the kH ~ 1.25 bin [0.625 sqrt 2, 1.25 sqrt 2). Kaczmarz
+                       levels relax with M (HYB, SL) or L (HLM). */
 } hz_hierarchy_opts;
+
+typedef enum { HZ_KACZ_RULE_BAND = 0, HZ_KACZ_RULE_BINS = 1 } hz_kacz_rule;
 
 typedef struct {
   int n;        /* n_l */

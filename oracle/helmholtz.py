@@ -22,10 +22,14 @@ Readings of points the paper leaves open (each one also listed in the design not
 * Gauss-Seidel is red-black ((i+j) even first on the way down, odd first on the
   way up); "GS on the normal equations" (Sec. 4-5) is row-action Kaczmarz with
   colours ``(i + 2j) mod 5`` (0..4 on the way down, 4..0 on the way up).
-* Level roles (Sec. 5) are binned by ``c = k_ref H`` around the paper's scales
-  0.3125, 0.625, 1.25, 2.5 with geometric-midpoint edges, plus a guard that
-  relaxes with M where red-black GS on L would amplify oscillatory error
-  (any node with ``1 < k H < 2 sqrt 2``).
+* Level roles (Sec. 5): a level relaxes by Kaczmarz (GS on the normal equations)
+  when the local scales ``k(x) H`` of its nodes reach into the band
+  ``[0.625 sqrt 2, 2 sqrt 2)`` where red-black GS fails as a smoother (Sec. 4);
+  other levels use GS, with the operator binned by ``c = k_ref H`` around the
+  paper's scales 0.3125, 0.625, 1.25, 2.5 (geometric-midpoint edges), plus a
+  guard that relaxes with M where red-black GS on L would amplify oscillatory
+  error (any node with ``1 < k H < 2 sqrt 2``). The earlier reading, Kaczmarz
+  on the ``c ~ 1.25`` bin only, is kept as ``rule="bins"``.
 * Bi-CGSTAB is right-preconditioned, x0 = 0, shadow residual r^_0 a fixed
   pseudo-random vector (r^_0 = b degenerates: after a final red-black sweep
   with the Krylov operator itself, ``(A K v)_p = v_p`` on the last colour, so a
@@ -50,7 +54,7 @@ __all__ = [
     "kaczmarz_update_rows", "kaczmarz_sweep", "jacobi_sweep", "rb_sor_sweep", "level_policy", "OracleLevel",
     "OracleHierarchy", "DEFAULT_OMEGA",
     "build_hierarchy", "vcycle", "bicgstab", "BicgstabResult", "true_relres",
-    "BIN_EDGES", "GUARD_BAND", "shadow_residual", "splitmix64_u01",
+    "BIN_EDGES", "GUARD_BAND", "KACZ_BAND", "level_count", "schedule", "shadow_residual", "splitmix64_u01",
 ]
 
 # --------------------------------------------------------------------------- grid and operator (Sec. 1)
@@ -214,9 +218,12 @@ def lex_gs_sweep(A: sp.csr_matrix, f: np.ndarray, u: np.ndarray, order: np.ndarr
 BIN_EDGES = (0.625 / math.sqrt(2.0), 0.625 * math.sqrt(2.0), 1.25 * math.sqrt(2.0))
 # Guard band in local k H where red-black Gauss-Seidel on L is not a usable smoother (see level_policy).
 GUARD_BAND = (1.0, 2.0 * math.sqrt(2.0))
+# Band of local k H where Gauss-Seidel is replaced by Kaczmarz (rule "band" of level_policy): from the
+# geometric midpoint of the paper's 0.625 and 1.25 scales up to the end of the guard band.
+KACZ_BAND = (0.625 * math.sqrt(2.0), 2.0 * math.sqrt(2.0))
 
 
-def level_policy(variant: str, c: float, c_local: np.ndarray, guard: bool = True):
+def level_policy(variant: str, c: float, c_local: np.ndarray, guard: bool = True, rule: str = "band"):
     """(relaxation operator, smoother, residual operator) for a non-coarsest level.
 
     ``c = k_ref H`` picks the scale bin; ``c_local`` holds ``k(x) H`` at the level's nodes.
@@ -224,6 +231,16 @@ def level_policy(variant: str, c: float, c_local: np.ndarray, guard: bool = True
     GS on the normal equations (Kaczmarz) are used; HLM-V uses L for relaxation (A) and for the
     residual (B); SL-V uses M for both; HYB-V uses L for (B) always and for (A) except on
     ``0.625 <~ kH <~ 1.25``, where M replaces it. ``sl_plain`` is M with GS on every level.
+
+    Which levels count as the ``kH ~ 1.25`` scale (reading): Sec. 4 finds GS a good smoother for
+    ``kH <~ 0.625`` and ``kH >~ 2.5`` only, and brings in GS on the normal equations where it is not.
+    With ``rule="band"`` (default) a level is such a scale when any node's ``k(x) H`` lies in
+    :data:`KACZ_BAND`, ``[0.625 sqrt 2, 2 sqrt 2)``: the lower edge is the bin edge between the
+    paper's 0.625 and 1.25 scales, the upper edge the ``kH`` below which one red-black sweep
+    still amplifies some oscillatory Fourier pair (the guard analysis below). In a heterogeneous
+    medium one level spans the scales ``k_min H .. k_max H``, so several levels can reach the band.
+    Kaczmarz relaxes with M (HYB, SL) or L (HLM). With ``rule="bins"`` only levels with
+    ``c = k_ref H`` in ``[0.625 sqrt 2, 1.25 sqrt 2)`` do.
 
     Guard (reading): HYB relaxes with L on coarse scales because Gauss-Seidel converges fast
     there (Sec. 5). For red-black GS one sweep maps the Fourier pair {theta, theta + (pi, pi)}
@@ -236,7 +253,13 @@ def level_policy(variant: str, c: float, c_local: np.ndarray, guard: bool = True
     lo, mid, hi = BIN_EDGES
     if variant == "sl_plain":
         return "M", "gs", "M"
-    kacz = mid <= c < hi
+    if rule == "band":
+        c_local = np.asarray(c_local)
+        kacz = bool(np.any((c_local >= KACZ_BAND[0]) & (c_local < KACZ_BAND[1])))
+    elif rule == "bins":
+        kacz = mid <= c < hi
+    else:
+        raise ValueError(rule)
     smoother = "kaczmarz" if kacz else "gs"
     if variant == "sl":
         return "M", smoother, "M"
@@ -244,7 +267,7 @@ def level_policy(variant: str, c: float, c_local: np.ndarray, guard: bool = True
         return "L", smoother, "L"
     if variant != "hyb":
         raise ValueError(variant)
-    op = "M" if lo <= c < hi else "L"
+    op = "M" if (lo <= c < hi or kacz) else "L"
     if op == "L" and guard:
         c_local = np.asarray(c_local)
         if np.any((c_local > GUARD_BAND[0]) & (c_local < GUARD_BAND[1])):
@@ -283,23 +306,50 @@ class OracleHierarchy:
 DEFAULT_OMEGA = {"jacobi": 0.8, "sor": 1.0}
 
 
-def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hyb", levels: int = 0,
-                    beta: float = 0.5, nu_gs: int = 1, nu_kacz: int = 4, guard: bool = True,
-                    ops: list | None = None, gs_smoother: str = "gs", omega: float | None = None) -> OracleHierarchy:
-    """Grids n, n/2, ... with rediscretised operators and the per-level roles of :func:`level_policy`.
-
-    ``levels = 0`` coarsens while the grid count is even and larger than 8. The coarsest level is
-    solved directly with L (HYB, HLM) or M (SL variants). ``ops`` optionally overrides
-    (relax_op, smoother, resid_op) per non-coarsest level. ``gs_smoother`` replaces red-black
-    Gauss-Seidel on the levels that use it by damped Jacobi ("jacobi") or red-black SOR ("sor")
-    with relaxation factor ``omega`` (the alternatives the remark of Sec. 4 names).
-    """
+def level_count(n: int, levels: int = 0) -> int:
+    """Number of grids: ``levels``, or (0) coarsen while the grid count is even and larger than 8."""
     if levels <= 0:
         levels, m = 1, n
         while m % 2 == 0 and m > 8:
             m //= 2
             levels += 1
     assert n % (1 << (levels - 1)) == 0 and n >> (levels - 1) >= 2, "grid not divisible for the requested levels"
+    return levels
+
+
+def schedule(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hyb", levels: int = 0, guard: bool = True,
+             rule: str = "band") -> list:
+    """(n_l, relax_op, smoother, resid_op) of every level, as :func:`build_hierarchy` assigns them,
+    without building any operator (k injected level by level, Sec. 5)."""
+    levels = level_count(n, levels)
+    out = []
+    k = np.asarray(kfield, dtype=np.float64)
+    for l in range(levels):
+        nl = n >> l
+        if l > 0:
+            k = inject(k)
+        if l == levels - 1:
+            op = "M" if variant in ("sl", "sl_plain") else "L"
+            out.append((nl, op, "direct", op))
+        else:
+            out.append((nl,) + tuple(level_policy(variant, k_ref / nl, k / nl, guard, rule)))
+    return out
+
+
+def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hyb", levels: int = 0,
+                    beta: float = 0.5, nu_gs: int = 1, nu_kacz: int = 4, guard: bool = True,
+                    ops: list | None = None, gs_smoother: str = "gs", omega: float | None = None,
+                    rule: str = "band") -> OracleHierarchy:
+    """Grids n, n/2, ... with rediscretised operators and the per-level roles of :func:`level_policy`.
+
+    ``levels = 0`` coarsens while the grid count is even and larger than 8. The coarsest level is
+    solved directly with L (HYB, HLM) or M (SL variants). ``ops`` optionally overrides
+    (relax_op, smoother, resid_op) per non-coarsest level; ``rule`` selects which levels relax by
+    Kaczmarz (see :func:`level_policy`). ``gs_smoother`` replaces red-black
+    Gauss-Seidel on the levels that use it by damped Jacobi ("jacobi") or red-black SOR ("sor")
+    with relaxation factor ``omega`` (the alternatives the remark of Sec. 4 names).
+    """
+    levels = level_count(n, levels)
     out = []
     k = np.asarray(kfield, dtype=np.float64)
     for l in range(levels):
@@ -314,7 +364,7 @@ def build_hierarchy(n: int, kfield: np.ndarray, k_ref: float, variant: str = "hy
             lv = OracleLevel(nl, H, k, op, "direct", op, 0, M if op == "M" else L)
             lv.cache["lu"] = sla.lu_factor(lv.A.toarray())
         else:
-            relax, smoother, resid = level_policy(variant, k_ref * H, k * H, guard) if ops is None else ops[l]
+            relax, smoother, resid = level_policy(variant, k_ref * H, k * H, guard, rule) if ops is None else ops[l]
             if smoother == "gs" and gs_smoother != "gs":
                 smoother = gs_smoother
             nu = nu_kacz if smoother == "kaczmarz" else nu_gs

@@ -31,6 +31,8 @@ const double BIN_MID = 0.625 * std::sqrt(2.0);
 const double BIN_HI = 1.25 * std::sqrt(2.0);
 const double GUARD_LO = 1.0;
 const double GUARD_HI = 2.0 * std::sqrt(2.0);
+const double KACZ_BAND_LO = 0.625 * std::sqrt(2.0);
+const double KACZ_BAND_HI = 2.0 * std::sqrt(2.0);
 
 constexpr int PIPELINE = 3;  // polled mode: iterations queued ahead of the convergence poll
 
@@ -254,8 +256,17 @@ cudaError_t mark(hz_problem* P, cudaError_t e, int kernel, int level) {
 }
 
 // Relaxation/residual roles of Sec. 5 for a non-coarsest level (the oracle's level_policy).
-void level_roles(int variant, double c, const std::vector<double>& c_local, bool guard, Level* L) {
-  bool kacz = (c >= BIN_MID && c < BIN_HI);
+void level_roles(int variant, double c, const std::vector<double>& c_local, bool guard, int rule, Level* L) {
+  // Kaczmarz levels (Sec. 4-5): with the band rule, every level with some node whose k(x) H lies
+  // in [KACZ_BAND_LO, KACZ_BAND_HI), where red-black Gauss-Seidel is no smoother; with the bins
+  // rule, the levels whose scale c = k_ref H is in the kH ~ 1.25 bin.
+  bool kacz = false;
+  if (rule == HZ_KACZ_RULE_BAND) {
+    for (double v : c_local)
+      if (v >= KACZ_BAND_LO && v < KACZ_BAND_HI) { kacz = true; break; }
+  } else {
+    kacz = (c >= BIN_MID && c < BIN_HI);
+  }
   L->smoother = kacz ? HZ_SMOOTH_KACZMARZ : HZ_SMOOTH_GS;
   if (variant == HZ_VAR_SL_PLAIN) {
     L->relax_op = HZ_OP_M; L->smoother = HZ_SMOOTH_GS; L->resid_op = HZ_OP_M;
@@ -264,7 +275,7 @@ void level_roles(int variant, double c, const std::vector<double>& c_local, bool
   if (variant == HZ_VAR_SL) { L->relax_op = HZ_OP_M; L->resid_op = HZ_OP_M; return; }
   if (variant == HZ_VAR_HLM) { L->relax_op = HZ_OP_L; L->resid_op = HZ_OP_L; return; }
   L->resid_op = HZ_OP_L;
-  L->relax_op = (c >= BIN_LO && c < BIN_HI) ? HZ_OP_M : HZ_OP_L;
+  L->relax_op = ((c >= BIN_LO && c < BIN_HI) || kacz) ? HZ_OP_M : HZ_OP_L;
   if (L->relax_op == HZ_OP_L && guard) {
     for (double v : c_local)
       if (v > GUARD_LO && v < GUARD_HI) { L->relax_op = HZ_OP_M; break; }
@@ -322,16 +333,16 @@ bool kform_ok(const hz_problem* P, int l, int form) {
   switch (form) {
     case HZ_KACZ_COLOUR: return true;
     case HZ_KACZ_LEVEL: return l > 0 && kacz_level_fits(fp32, L.n);
-    case HZ_KACZ_TILE: return l > 0 && fp32 && L.nu % 2 == 0;
+    case HZ_KACZ_TILE: return l > 0 && L.nu % 2 == 0;
     case HZ_KACZ_CLUSTER: return l > 0 && kacz_cluster_fits(fp32, L.n);
   }
   return false;
 }
 // Default form: FP32 - one block if the level fits, else a cluster, else tiles; FP64 - a cluster
-// (the FP64 pipe of one SM bounds the one-block form, and the tiles' halo adds FP64 work), else
-// colour launches. Measured per Bi-CGSTAB iteration (four level launches): FP32 n_l = 128 cluster
-// 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64 cluster 206 us,
-// colour launches 820 us.
+// (the FP64 pipe of one SM bounds the one-block form), else colour launches (the tiles' 2.6x halo
+// recomputation is FP64 work). Measured per Bi-CGSTAB iteration (four level launches): FP32
+// n_l = 128 cluster 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64
+// cluster 206 us, colour launches 820 us; FP64 n_l = 1024 tiles 4.49 ms, colour launches 2.39 ms.
 int default_kform(const hz_problem* P, int l) {
   const int order32[] = {HZ_KACZ_LEVEL, HZ_KACZ_CLUSTER, HZ_KACZ_TILE}, order64[] = {HZ_KACZ_CLUSTER};
   const int* o = P->plan.fp32 ? order32 : order64;
@@ -360,7 +371,7 @@ cudaError_t kacz_tile_sweeps(hz_problem* P, int l, Src f, const void* first_in, 
   cudaError_t e;
   for (int k = 0; k < L.nu; ++k) {
     void* out = ((L.nu - 1 - k) % 2 == 0) ? L.u : L.u2;
-    if ((e = mark(P, launch_kacz_sweep_tile(true, out, L.pitch, in, L.pitch, f.f, f.pf, f.f64, kh, pk, L.n,
+    if ((e = mark(P, launch_kacz_sweep_tile(P->plan.fp32, out, L.pitch, in, L.pitch, f.f, f.pf, f.f64, kh, pk, L.n,
                                             op_beta(P, L.relax_op), post, stop, P->stream, bi),
                   HZ_K_KACZ_SWEEP, l)))
       return e;
@@ -912,7 +923,7 @@ bool schedule(const hz_problem* P, const hz_hierarchy_opts& o, const Plan& pl, s
       for (int j = 0; j <= L.n; ++j)
         for (int i = 0; i <= L.n; ++i)
           c_local.push_back(P->k_host[(size_t)stride * j * (n + 1) + (size_t)stride * i] * L.H);
-      level_roles(o.variant, k_ref * L.H, c_local, o.guard != 0, &L);
+      level_roles(o.variant, k_ref * L.H, c_local, o.guard != 0, o.kacz_rule, &L);
       L.nu = L.smoother == HZ_SMOOTH_KACZMARZ ? o.nu_kacz : o.nu_gs;
       if (L.smoother == HZ_SMOOTH_GS && o.gs_smoother != HZ_SMOOTH_GS) {
         L.smoother = o.gs_smoother;
@@ -929,7 +940,7 @@ bool opts_ok(const hz_hierarchy_opts& o) {
            o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1 ||
            o.kacz_form < -1 || o.kacz_form > HZ_KACZ_CLUSTER ||
            (o.gs_smoother != HZ_SMOOTH_GS && o.gs_smoother != HZ_SMOOTH_JACOBI && o.gs_smoother != HZ_SMOOTH_SOR) ||
-           !(o.omega >= 0.0 && o.omega < 2.0));
+           !(o.omega >= 0.0 && o.omega < 2.0) || (o.kacz_rule != HZ_KACZ_RULE_BAND && o.kacz_rule != HZ_KACZ_RULE_BINS));
 }
 
 // ------------------------------------------------------------------ coarse tail
@@ -1032,6 +1043,8 @@ cudaError_t time_pass(hz_problem* P, int l, bool up, float* best_ms) {
   return e;
 }
 
+constexpr int FP64_TUNE_MIN_N = 2048;  // smallest FP64 level whose fused-pass form is tuned
+
 cudaError_t autotune(hz_problem* P) {
   const int B = P->plan.batch;
   for (int l = 0; l < P->plan.levels - 1; ++l) {
@@ -1042,11 +1055,13 @@ cudaError_t autotune(hz_problem* P) {
       L.var_down = L.var_up = ok ? P->opts.pass_variant : 0;
       continue;
     }
-    if (!P->plan.fp32) {
-      // FP64 levels keep the tiles: the passes are bound by the FP64 pipe, the streaming forms
-      // recompute halo rows (more FP64 work), and timed in the solve they were slower at the
-      // finest level (n = 512: 80 us against 60 us per pre-pass), although isolated launches
-      // ranked them ahead.
+    if (!P->plan.fp32 && L.n < FP64_TUNE_MIN_N) {
+      // FP64 levels that fit L2 keep the tiles: the passes are bound by the FP64 pipe, the
+      // streaming forms recompute halo rows (more FP64 work), and timed in the solve they were
+      // slower at the finest level (n = 512: 80 us against 60 us per pre-pass), although
+      // isolated launches ranked them ahead. Larger levels are tuned like FP32 ones (n = 4096,
+      // per iteration in the solve's graph: pre-passes 4.79 ms with tiles, 3.82 ms with 32-row
+      // streaming; post-passes 3.96 and 2.51 ms).
       L.var_down = L.var_up = 0;
       continue;
     }
@@ -1107,6 +1122,7 @@ void hz_default_opts(hz_hierarchy_opts* o) {
   o->kacz_form = -1;
   o->gs_smoother = HZ_SMOOTH_GS;
   o->omega = 0.0;
+  o->kacz_rule = HZ_KACZ_RULE_BAND;
 }
 
 hz_status hz_create_problem(int n, const double* k_field, double beta, int bc, hz_problem** out) {

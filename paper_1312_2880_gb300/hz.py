@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("levels", c_int), ("variant", c_int), ("precision", c_int), ("nu_gs", c_int),
                 ("nu_kacz", c_int), ("guard", c_int), ("k_ref", c_double), ("batch", c_int),
                 ("pass_variant", c_int), ("coarse_tail", c_int), ("kacz_form", c_int),
-                ("gs_smoother", c_int), ("omega", c_double)]
+                ("gs_smoother", c_int), ("omega", c_double), ("kacz_rule", c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -125,16 +125,20 @@ def _ptr(t) -> c_void_p:
 
 
 KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3}
+KACZ_RULES = {"band": 0, "bins": 1}
 
 
 def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, guard=True, k_ref=0.0, batch=1,
-              pass_variant=-1, coarse_tail=True, kacz_form="auto", gs_smoother="gs", omega=0.0) -> Opts:
+              pass_variant=-1, coarse_tail=True, kacz_form="auto", gs_smoother="gs", omega=0.0,
+              kacz_rule="band") -> Opts:
     """pass_variant: -1 = fused-pass form picked per level by the tile autotuner at setup; 0 = shared-
     memory tiles; 1..8 = register streaming with 2**v rows per warp (FP32 form).
     kacz_form: kernel form of the Kaczmarz levels below the finest (one of KACZ_FORMS); a form that
     does not apply to a level falls back to the default.
     gs_smoother: "gs" (red-black Gauss-Seidel), "jacobi" (damped) or "sor" (red-black, over-relaxed)
-    on the levels the rules give Gauss-Seidel; omega: their factor (0 = 0.8 Jacobi, 1 SOR)."""
+    on the levels the rules give Gauss-Seidel; omega: their factor (0 = 0.8 Jacobi, 1 SOR).
+    kacz_rule: "band" (every level with some node's k(x) H in [0.625 sqrt 2, 2 sqrt 2) relaxes by
+    Kaczmarz) or "bins" (only the level whose k_ref H is in the kH ~ 1.25 bin)."""
     o = Opts()
     lib().hz_default_opts(byref(o))
     o.levels, o.variant, o.precision = levels, VARIANTS[variant], PRECISIONS[precision]
@@ -144,6 +148,7 @@ def make_opts(variant="hyb", precision="fp64", levels=0, nu_gs=1, nu_kacz=4, gua
     o.kacz_form = KACZ_FORMS[kacz_form]
     o.gs_smoother = GS_SMOOTHERS[gs_smoother]
     o.omega = float(omega)
+    o.kacz_rule = KACZ_RULES[kacz_rule]
     return o
 
 
@@ -187,7 +192,7 @@ class Problem:
 
     def __init__(self, n: int, kfield, beta: float = 0.5, *, variant="hyb", precision="fp64", levels=0, nu_gs=1,
                  nu_kacz=4, guard=True, k_ref=0.0, batch=1, arena=None, pass_variant=-1, coarse_tail=True,
-                 kacz_form="auto", gs_smoother="gs", omega=0.0):
+                 kacz_form="auto", gs_smoother="gs", omega=0.0, kacz_rule="band"):
         import torch
 
         L = lib()
@@ -201,7 +206,7 @@ class Problem:
             raise HzError(st, "hz_create_problem failed")
         self._h = h
         self.opts = make_opts(variant, precision, levels, nu_gs, nu_kacz, guard, k_ref, batch, pass_variant,
-                              coarse_tail, kacz_form, gs_smoother, omega)
+                              coarse_tail, kacz_form, gs_smoother, omega, kacz_rule)
         self.batch = int(batch)
         self.precision = precision
         self.bytes = int(L.hz_footprint_bytes(self.n, byref(self.opts)))

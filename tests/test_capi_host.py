@@ -53,30 +53,42 @@ def test_footprint(L):
     assert hz.footprint_bytes(100, levels=2) == 0  # coarsest 51^2 > 1089 unknowns
 
 
-def _oracle_schedule(wl, variant=None, levels=None, k_ref=None):
-    h = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref if k_ref is None else k_ref, variant or wl.variant,
-                          wl.levels if levels is None else levels)
-    return [(lv.n, lv.relax_op, {"gs": "gs", "kaczmarz": "kaczmarz", "direct": "direct"}[lv.smoother], lv.resid_op)
-            for lv in h.levels]
+def _oracle_schedule(wl, variant=None, rule="band"):
+    return o.schedule(wl.n, wl.kfield, wl.k_ref, variant or wl.variant, wl.levels, rule=rule)
 
 
-def _lib_schedule(wl, variant=None, levels=None):
+def _lib_schedule(wl, variant=None, levels=None, rule="band"):
     sch = hz.describe_hierarchy(wl.n, wl.kfield, variant=variant or wl.variant,
-                                levels=wl.levels if levels is None else levels, k_ref=wl.k_ref)
+                                levels=wl.levels if levels is None else levels, k_ref=wl.k_ref, kacz_rule=rule)
     return [(d["n"], d["relax_op"], d["smoother"], d["resid_op"]) for d in sch]
 
 
+@pytest.mark.parametrize("rule", ["band", "bins"])
 @pytest.mark.parametrize("variant", ["hyb", "sl", "hlm", "sl_plain"])
-def test_schedule_matches_oracle_policy(L, variant):
+def test_schedule_matches_oracle_policy(L, variant, rule):
     cases = [I.plain_n64(), I.wedge_n512(), I.grf_n4096(n=512, k=125.0)]
     cases += I.batch_problems(rhs_per_k=1)
+    cases += [wl for _, _, wl in I.paper_table_workloads(max_n=256)]
     for wl in cases:
-        assert _lib_schedule(wl, variant) == _oracle_schedule(wl, variant), (wl.name, variant)
+        assert _lib_schedule(wl, variant, rule=rule) == _oracle_schedule(wl, variant, rule), (wl.name, variant)
+
+
+def test_schedule_of_the_n4096_random_field(L):
+    """n = 4096, k = 1000, k (1 + 0.3 g): local k H spans 0.7 .. 1.3 times k_ref H, so with the band
+    rule the levels n_l = 1024, 512 and 256 (k_ref H = 0.98, 1.95, 3.9) relax by Kaczmarz."""
+    wl = I.grf_n4096()
+    for rule in ("band", "bins"):
+        assert _lib_schedule(wl, rule=rule) == _oracle_schedule(wl, rule=rule)
+    kacz = [s[0] for s in _oracle_schedule(wl) if s[2] == "kaczmarz"]
+    assert kacz == [1024, 512, 256]
 
 
 def test_schedule_of_table1_setting(L):
     kf = I.constant_k(64, 40.0)
     sch = hz.describe_hierarchy(64, kf, variant="hyb", levels=4, k_ref=40.0)
+    assert [(d["relax_op"], d["smoother"], d["nu"]) for d in sch] == [
+        ("M", "gs", 1), ("M", "kaczmarz", 4), ("M", "kaczmarz", 4), ("L", "direct", 0)]
+    sch = hz.describe_hierarchy(64, kf, variant="hyb", levels=4, k_ref=40.0, kacz_rule="bins")
     assert [(d["relax_op"], d["smoother"], d["nu"]) for d in sch] == [
         ("M", "gs", 1), ("M", "kaczmarz", 4), ("M", "gs", 1), ("L", "direct", 0)]
 

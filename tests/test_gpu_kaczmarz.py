@@ -61,8 +61,9 @@ def problem(wl, precision, form, batch=1):
 
 
 def kacz_level(sched, nk):
-    ls = [l for l, d in enumerate(sched) if d["smoother"] == "kaczmarz"]
-    assert ls and sched[ls[0]]["n"] == nk, sched
+    """Index of the Kaczmarz level of n_l = nk (the band rule can make further levels Kaczmarz)."""
+    ls = [l for l, d in enumerate(sched) if d["smoother"] == "kaczmarz" and d["n"] == nk]
+    assert len(ls) == 1, sched
     return ls[0]
 
 

@@ -107,24 +107,80 @@ def _sched(h):
 
 def test_policy_table1_setting():
     """k = 40, h = 1/64 (Table 1): scales kH = 0.625, 1.25, 2.5, 5. HYB relaxes M at 0.625 and 1.25
-    (Kaczmarz at 1.25), L residuals everywhere, L on the coarsest; SL is M throughout; HLM is L."""
+    (Kaczmarz at 1.25, and with the band rule also at 2.5 < 2 sqrt 2), L residuals everywhere, L on
+    the coarsest; SL is M throughout; HLM is L."""
     kf = I.constant_k(64, 40.0)
     hyb = _sched(o.build_hierarchy(64, kf, 40.0, "hyb", 4))
     assert hyb[0] == ("M", "gs", "L") and hyb[1] == ("M", "kaczmarz", "L")
-    assert hyb[2] == ("M", "gs", "L")  # guard: 1 < kH = 2.5 < 2 sqrt 2
+    assert hyb[2] == ("M", "kaczmarz", "L")  # band: kH = 2.5 in [0.625 sqrt 2, 2 sqrt 2)
     assert hyb[3] == ("L", "direct", "L")
-    assert _sched(o.build_hierarchy(64, kf, 40.0, "sl", 4)) == [("M", "gs", "M"), ("M", "kaczmarz", "M"), ("M", "gs", "M"), ("M", "direct", "M")]
-    assert _sched(o.build_hierarchy(64, kf, 40.0, "hlm", 4)) == [("L", "gs", "L"), ("L", "kaczmarz", "L"), ("L", "gs", "L"), ("L", "direct", "L")]
-    assert o.build_hierarchy(64, kf, 40.0, "hyb", 4, guard=False).levels[2].relax_op == "L"
+    assert _sched(o.build_hierarchy(64, kf, 40.0, "sl", 4)) == [("M", "gs", "M"), ("M", "kaczmarz", "M"), ("M", "kaczmarz", "M"), ("M", "direct", "M")]
+    assert _sched(o.build_hierarchy(64, kf, 40.0, "hlm", 4)) == [("L", "gs", "L"), ("L", "kaczmarz", "L"), ("L", "kaczmarz", "L"), ("L", "direct", "L")]
+    bins = _sched(o.build_hierarchy(64, kf, 40.0, "hyb", 4, rule="bins"))
+    assert bins[2] == ("M", "gs", "L")  # bins: Gauss-Seidel, guard 1 < kH = 2.5 < 2 sqrt 2 gives M
+    assert o.build_hierarchy(64, kf, 40.0, "hyb", 4, guard=False, rule="bins").levels[2].relax_op == "L"
 
 
 def test_policy_wedge_n512():
+    """Layers k * {1.0, 1.5, 0.75}: level l spans k H from 75/n_l to 150/n_l. Band rule: Kaczmarz on
+    n_l = 128 (0.59 .. 1.17), 64 (1.17 .. 2.34) and 32 (2.34 .. 4.69); bins: on n_l = 64 only."""
     wl = I.wedge_n512()
     h = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
     assert [lv.n for lv in h.levels] == [512, 256, 128, 64, 32, 16, 8, 4]
     ops = [(a[0] + ("k" if a[1] == "kaczmarz" else "")) for a in _sched(h)]
-    assert ops == ["L", "L", "M", "Mk", "M", "L", "L", "L"]
+    assert ops == ["L", "L", "Mk", "Mk", "Mk", "L", "L", "L"]
     assert all(lv.resid_op == "L" for lv in h.levels)
+    sch = o.schedule(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels, rule="bins")
+    assert [a[1] + ("k" if a[2] == "kaczmarz" else "") for a in sch] == ["L", "L", "M", "Mk", "M", "L", "L", "L"]
+
+
+def test_kaczmarz_band_edges_follow_the_red_black_analysis():
+    """The band rule's upper edge: one red-black sweep on L maps the Fourier pair {theta, theta+(pi,pi)}
+    with eigenvalue (S/d)^2, d = -4 + (kH)^2, |S| <= 4 reached by the smoothest pair and its
+    oscillatory partner; it exceeds 1 for some pair exactly when |d| < 4, i.e. kH < 2 sqrt 2 (for
+    kH > 0). The lower edge is the geometric midpoint of the paper's 0.625 and 1.25 scales. A level
+    relaxes by Kaczmarz exactly when some node's k H lies in [lower, upper)."""
+    lo, hi = o.KACZ_BAND
+    assert lo == pytest.approx(math.sqrt(0.625 * 1.25)) and hi == pytest.approx(2 * math.sqrt(2))
+    # measured: growth per red-black sweep (f = 0) of a random error on a periodic 16 x 16 grid,
+    # whose Fourier pairs include S = 4 and -4; the analysis gives the rate (4/d)^2
+    m, N = 16, 256
+    idx = np.arange(N).reshape(m, m)
+    J, Ii = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    col = ((Ii + J) % 2).ravel()
+    order = np.concatenate([np.nonzero(col == 0)[0], np.nonzero(col == 1)[0]])
+    for kH in (2.6, 2.75, 2.9, 3.2):
+        d = -4 + kH * kH
+        rows, cols, vals = [], [], []
+        for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            rows.append(idx.ravel()); cols.append(np.roll(np.roll(idx, -dj, 0), -di, 1).ravel()); vals.append(np.ones(N))
+        rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(np.full(N, d))
+        import scipy.sparse as sp
+        A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N)).tocsr()
+        e = np.random.default_rng(1).standard_normal(N) + 0j
+        for _ in range(400):
+            e = o.lex_gs_sweep(A, np.zeros(N, complex), e, order)
+            e /= np.linalg.norm(e)
+        rate = np.linalg.norm(o.lex_gs_sweep(A, np.zeros(N, complex), e, order))
+        assert rate == pytest.approx((4 / d) ** 2, rel=1e-6)
+        assert (rate > 1.0) == (kH < hi)
+    rng = np.random.default_rng(3)
+    for variant in ("hyb", "sl", "hlm"):
+        for _ in range(200):
+            c = float(rng.uniform(0.05, 6.0))
+            c_local = c * rng.uniform(0.6, 1.4, size=7)
+            expect = bool(np.any((c_local >= lo) & (c_local < hi)))
+            assert (o.level_policy(variant, c, c_local)[1] == "kaczmarz") == expect
+            if variant == "hyb" and expect:
+                assert o.level_policy(variant, c, c_local)[0] == "M"
+
+
+def test_schedule_matches_built_hierarchy():
+    for wl in (I.wedge_n512(), I.grf_n4096(n=256, k=62.5), I.plain_n64()):
+        for rule in ("band", "bins"):
+            h = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels, rule=rule)
+            assert o.schedule(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels, rule=rule) == [
+                (lv.n, lv.relax_op, lv.smoother, lv.resid_op) for lv in h.levels]
 
 
 def test_policy_fine_hyb_uses_l():
