@@ -319,6 +319,16 @@ hz_status hz_set_stall_detection(hz_problem* p, double cos2, double step2, int m
 /* Name of an hz_kernel. */
 const char* hz_kernel_name(int kernel);
 
+/* Measured FP64 FMA throughput of the current device (the paper has no counterpart; it sets the
+ * roofline of the FP64 Krylov kernels, which GB300's FP64 pipe bounds before HBM): full warps of
+ * independent DFMA chains on every SM, `iters` FMAs per chain, timed with CUDA events on `stream`
+ * (a cudaStream_t, NULL = legacy default stream), each launch shape (4 or 8 blocks of 256 threads
+ * per SM, 8 or 16 chains a thread) after an untimed warm-up launch; the best shape counts. Writes the rate
+ * in TFLOP/s (an FMA counts 2 flops) to *tflops (host) and the launch time to *ms (host, may be
+ * NULL). Synchronises the stream. Returns HZ_EINVAL for iters outside [1, 2^24] or a null tflops,
+ * HZ_ECUDA if a launch or event fails. */
+hz_status hz_measure_fp64_rate(int iters, void* stream, double* tflops, double* ms);
+
 /* ---- Allocation-free variant (the paper has no counterpart to this entry point) ----
  * For callers that cannot allocate device memory when they call: hosts whose own pool owns every
  * byte of the device (a framework's caching allocator, a serving runtime's memory budget), where

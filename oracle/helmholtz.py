@@ -54,7 +54,8 @@ __all__ = [
     "kaczmarz_update_rows", "kaczmarz_sweep", "jacobi_sweep", "rb_sor_sweep", "level_policy", "OracleLevel",
     "OracleHierarchy", "DEFAULT_OMEGA",
     "build_hierarchy", "vcycle", "bicgstab", "BicgstabResult", "true_relres",
-    "BIN_EDGES", "GUARD_BAND", "KACZ_BAND", "level_count", "schedule", "shadow_residual", "splitmix64_u01",
+    "BIN_EDGES", "GUARD_BAND", "KACZ_BAND", "level_count", "schedule", "renewed_shadow_seed",
+    "STALL_COS2", "STALL_STEP2", "MAX_SHADOW_RESTARTS", "MAX_TRUE_RESTARTS", "shadow_residual", "splitmix64_u01",
 ]
 
 # --------------------------------------------------------------------------- grid and operator (Sec. 1)
@@ -494,74 +495,147 @@ class BicgstabResult:
     history: list  # relative residual after each half and each full step
     status: str  # converged | maxit | breakdown
     true_relres: float
+    restarts: int = 0  # restarts from the true residual (recurrence converged, b - A x did not)
+    shadow_restarts: int = 0  # renewals of the shadow residual (stalled recurrences)
 
 
 def true_relres(A, b, x) -> float:
     return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
 
 
+# Shadow-residual renewal after stalled recurrences (reading, not in the paper): seeds of the
+# renewed shadow residuals, and the default thresholds and cap.
+SHADOW_SEED_STEP = 0x2545F4914F6CDD1D
+STALL_COS2 = 1e-12
+STALL_STEP2 = 1e-8
+MAX_SHADOW_RESTARTS = 16
+# Restarts from the true residual that one solve may take.
+MAX_TRUE_RESTARTS = 8
+
+
+def renewed_shadow_seed(k: int) -> int:
+    """Seed of the k-th renewed shadow residual (k = 1, 2, ...): ``SHADOW_SEED + k * SHADOW_SEED_STEP``
+    modulo 2^64."""
+    return (SHADOW_SEED + k * SHADOW_SEED_STEP) % (1 << 64)
+
+
 def bicgstab(A, b: np.ndarray, precond=None, tol: float = 1e-6, maxit: int = 1000, callback=None,
-             rhat: np.ndarray | None = None) -> BicgstabResult:
+             rhat: np.ndarray | None = None, stall_cos2: float = STALL_COS2, stall_step2: float = STALL_STEP2,
+             max_shadow_restarts: int = MAX_SHADOW_RESTARTS,
+             max_true_restarts: int = MAX_TRUE_RESTARTS, renew_shadow=None) -> BicgstabResult:
     """Right-preconditioned Bi-CGSTAB (van der Vorst 1992) from ``x0 = 0``; the shadow residual
     ``rhat`` defaults to :func:`shadow_residual`.
 
     Each iteration applies the preconditioner twice (Sec. 6). Stops when ``|r| / |b| <= tol`` after
-    the half step (``s``) or the full step; a recurrence-converged iterate is accepted only when the
-    true residual ``b - A x`` also meets ``tol``, else the true residual replaces ``r`` and the
-    iteration goes on.
+    the half step (``s``) or the full step. Two readings complete the method where the paper is
+    silent:
+
+    * A recurrence-converged iterate is accepted only when the true residual ``b - A x`` also
+      meets ``tol``. If it does not, the iteration restarts from it: ``r = b - A x``, the next
+      direction is ``p = r`` and ``rho = <rhat, r>``; at most ``max_true_restarts`` times and
+      below ``maxit`` iterations, else the solve ends unconfirmed (status ``maxit``).
+    * Stalled recurrences: after a full step with ``|<rhat, r>|^2 < stall_cos2 |rhat|^2 |r|^2``
+      and ``|omega|^2 |t|^2 < stall_step2 |r|^2``, the next iteration renews the shadow residual
+      (:func:`shadow_residual` with seed :func:`renewed_shadow_seed` of the renewal's number),
+      takes ``p = r`` and ``rho = <rhat, r>``; at most ``max_shadow_restarts`` times.
+
+    ``callback(x)`` is called after every full step. ``renew_shadow(k, r)``, if given, supplies the
+    k-th renewed shadow residual instead of the seeded one (used to check the renewal against a
+    fresh start of an independent implementation).
     """
     K = (lambda v: v) if precond is None else precond
     x = np.zeros_like(b)
     r = b.copy()
     rhat = shadow_residual(b.size) if rhat is None else np.asarray(rhat, dtype=np.complex128)
     bnorm = np.linalg.norm(b)
+    tol2 = (tol * bnorm) ** 2
     hist = []
     p = np.zeros_like(b)
     v = np.zeros_like(b)
-    rho_old = alpha = omega = 1.0 + 0j
+    alpha = omega = beta = 1.0 + 0j
     if bnorm == 0:
         return BicgstabResult(x, 0.0, hist, "converged", 0.0)
-    for it in range(1, maxit + 1):
-        rho = np.vdot(rhat, r)
-        if rho == 0:
-            return BicgstabResult(x, it - 1, hist, "breakdown", true_relres(A, b, x))
-        if it == 1:
+    rho = np.vdot(rhat, r)
+    restarts = renewals = 0
+    first, renew = True, False
+    it = 1
+
+    def result(status, iterations, xx):
+        return BicgstabResult(xx, float(iterations), hist, status, true_relres(A, b, xx), restarts, renewals)
+
+    if rho == 0:
+        return result("breakdown", 0, x)
+    while it <= maxit:
+        if renew:  # a new shadow residual and a fresh direction
+            renewals += 1
+            rhat = (shadow_residual(b.size, renewed_shadow_seed(renewals)) if renew_shadow is None
+                    else np.asarray(renew_shadow(renewals, r), dtype=np.complex128))
+            rho = np.vdot(rhat, r)
+            p = r.copy()
+            renew = False
+            if rho == 0:
+                return result("breakdown", it - 1, x)
+        elif first:
             p = r.copy()
         else:
-            beta = (rho / rho_old) * (alpha / omega)
             p = r + beta * (p - omega * v)
         y = K(p)
         v = A @ y
         rv = np.vdot(rhat, v)
         if rv == 0:
-            return BicgstabResult(x, it - 1, hist, "breakdown", true_relres(A, b, x))
+            return result("breakdown", it - 1, x)
         alpha = rho / rv
         s = r - alpha * v
-        hist.append(np.linalg.norm(s) / bnorm)
-        if hist[-1] <= tol:
-            xh = x + alpha * y
-            trr = true_relres(A, b, xh)
-            if trr <= tol:
-                if callback:
-                    callback(xh)
-                return BicgstabResult(xh, it - 0.5, hist, "converged", trr)
-        z = K(s)
-        t = A @ z
-        tt = np.vdot(t, t)
-        if tt == 0:
-            return BicgstabResult(x + alpha * y, it - 0.5, hist, "breakdown", true_relres(A, b, x + alpha * y))
-        omega = np.vdot(t, s) / tt
-        x = x + alpha * y + omega * z
-        r = s - omega * t
-        rho_old = rho
-        hist.append(np.linalg.norm(r) / bnorm)
-        if callback:
-            callback(x)
-        if omega == 0:
-            return BicgstabResult(x, it, hist, "breakdown", true_relres(A, b, x))
-        if hist[-1] <= tol:
-            trr = true_relres(A, b, x)
-            if trr <= tol:
-                return BicgstabResult(x, float(it), hist, "converged", trr)
-            r = b - A @ x
-    return BicgstabResult(x, float(maxit), hist, "maxit", true_relres(A, b, x))
+        ss = np.vdot(s, s).real
+        hist.append(math.sqrt(ss) / bnorm)
+        stop = None
+        if ss <= tol2:  # stop after the half step
+            x = x + alpha * y
+            stop = it - 0.5
+        else:
+            z = K(s)
+            t = A @ z
+            tt = np.vdot(t, t).real
+            if tt == 0:
+                return result("breakdown", it - 1, x)
+            omega = np.vdot(t, s) / tt
+            x = x + alpha * y + omega * z
+            r = s - omega * t
+            rho_new = np.vdot(rhat, r)
+            rr = np.vdot(r, r).real
+            hist.append(math.sqrt(rr) / bnorm)
+            if callback:
+                callback(x)
+            if omega == 0:
+                return result("breakdown", it, x)
+            if rr <= tol2:
+                stop = float(it)
+            elif rho_new == 0:
+                return result("breakdown", it, x)
+            else:
+                cos2 = abs(rho_new) ** 2 / (np.vdot(rhat, rhat).real * rr)
+                step2 = abs(omega) ** 2 * tt / rr
+                if cos2 < stall_cos2 and step2 < stall_step2 and renewals < max_shadow_restarts:
+                    renew = True
+                else:
+                    beta = (rho_new / rho) * (alpha / omega)
+                    rho = rho_new
+                    first = False
+                it += 1
+                continue
+        # the recurrence says converged: confirm on the true residual b - A x
+        tr = b - A @ x
+        if np.vdot(tr, tr).real <= tol2:
+            if stop != int(stop) and callback:
+                callback(x)
+            return result("converged", stop, x)
+        if restarts >= max_true_restarts or it >= maxit:
+            return result("maxit", stop, x)
+        restarts += 1
+        r = tr
+        rho = np.vdot(rhat, r)
+        first = True
+        it += 1
+        if rho == 0:
+            return result("breakdown", it - 1, x)
+    return result("maxit", maxit, x)

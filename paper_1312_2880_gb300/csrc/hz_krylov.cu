@@ -253,6 +253,10 @@ __global__ void k_update_p_kernel(KrylovVecs k) {
   pdl_enter();
   k = instance(k);
   KState* st = k.st;
+  if (st->done == 5 && st->it > st->maxit) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 4;
+    return;
+  }
   if (st->done == 5) {
     // Near-breakdown restart: a new pseudo-random shadow residual (the next seed of the same
     // generator), p = r, rho = <r^, r>.

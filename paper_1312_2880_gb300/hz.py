@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
         "hz_group_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_double, c_int, POINTER(SolveInfo)]),
         "hz_group_last_error": (ctypes.c_char_p, [c_void_p]),
         "hz_group_destroy": (None, [c_void_p]),
+        "hz_measure_fp64_rate": (c_int, [c_int, c_void_p, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -114,6 +115,18 @@ def lib() -> ctypes.CDLL:
         fn.argtypes = args
     _LIB = L
     return L
+
+
+def measure_fp64_rate(iters: int = 1 << 16) -> dict:
+    """FP64 FMA throughput of the current device in TFLOP/s (hz_measure_fp64_rate), on torch's
+    current stream."""
+    import torch
+
+    tf, ms = c_double(), c_double()
+    st = lib().hz_measure_fp64_rate(int(iters), c_void_p(torch.cuda.current_stream().cuda_stream), byref(tf), byref(ms))
+    if st != HZ_OK:
+        raise HzError(st, "hz_measure_fp64_rate failed")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def _ptr(t) -> c_void_p:

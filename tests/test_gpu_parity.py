@@ -383,6 +383,65 @@ def test_forced_shadow_restarts_keep_the_solve_correct(precision):
     assert o.true_relres(A, wl.rhs.ravel(), x1.cpu().numpy().ravel()) <= 1e-6
 
 
+@pytest.mark.parametrize("name", ["plain64", "wedge128"])
+def test_forced_shadow_restarts_match_the_oracle_iterates(name):
+    """The renewal branch (R21) against the oracle's twin of it: with thresholds every iteration
+    meets, both renew the shadow residual (the same SplitMix64 seeds) after each of the first five
+    full steps; the first eight iterates and the residual history agree as the plain iterations do
+    (1e-10, or ten times the oracle's own one-ulp spread), and so does the whole solve."""
+    wl = WORKLOADS[name]()
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    K = lambda v: o.vcycle(H, v)  # noqa: E731
+    forced = dict(stall_cos2=2.0, stall_step2=1e300, max_shadow_restarts=5)
+    ref = o.bicgstab(A, wl.rhs.ravel(), K, tol=1e-30, maxit=8, **forced)
+    alt = o.bicgstab(A, wl.rhs.ravel() * (1 + 2.0**-52), K, tol=1e-30, maxit=8, **forced)
+    spread_x = rel(alt.x / (1 + 2.0**-52), ref.x)
+    spread_h = float(np.abs(np.array(alt.history) / np.array(ref.history) - 1).max())
+    assert ref.shadow_restarts == 5
+    P, _ = pair(wl)
+    try:
+        P.set_stall_detection(2.0, 1e300, 5)
+        x, info, hist = P.solve(dev(wl.rhs), tol=1e-30, maxit=8, allow_fail=True)
+        assert P.krylov_scalars()["shadow_restarts"] == 5 and info["iterations"] == 8
+        assert rel(x, ref.x) <= max(1e-10, 10 * spread_x)
+        np.testing.assert_allclose(hist, ref.history, rtol=max(1e-10, 10 * spread_h))
+        full = o.bicgstab(A, wl.rhs.ravel(), K, tol=1e-6, maxit=1000, **forced)
+        x, info, _ = P.solve(dev(wl.rhs), tol=1e-6, maxit=1000)
+        assert info["status"] == 0 and full.status == "converged"
+        assert abs(info["iterations"] - full.iterations) <= 1.0
+        assert info["restarts"] == full.restarts + full.shadow_restarts
+        assert o.true_relres(A, wl.rhs.ravel(), x.cpu().numpy().ravel()) <= 1e-6
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_true_residual_restart_branch(precision):
+    """A tolerance below the attainable accuracy: the recurrence residual reaches it, b - A x cannot,
+    so each recurrence stop is refused, the solve restarts from the true residual up to the cap (8)
+    and ends with HZ_EMAXIT (not HZ_OK), x at the attainable accuracy. The oracle takes the same
+    branch the same number of times, and the two solutions agree to that accuracy."""
+    hz = hzmod()
+    wl = I.plain_n64()
+    A = o.helmholtz_matrix(wl.n, wl.kfield)
+    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+    ref = o.bicgstab(A, wl.rhs.ravel(), lambda v: o.vcycle(H, v), tol=1e-18, maxit=400)
+    assert ref.restarts == o.MAX_TRUE_RESTARTS and ref.status == "maxit"
+    P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=precision, levels=wl.levels, k_ref=wl.k_ref)
+    try:
+        x, info, hist = P.solve(dev(wl.rhs), tol=1e-18, maxit=400, allow_fail=True)
+    finally:
+        P.close()
+    assert info["status"] == hz.HZ_EMAXIT, info
+    assert info["restarts"] >= o.MAX_TRUE_RESTARTS
+    xs = x.cpu().numpy().ravel()
+    assert o.true_relres(A, wl.rhs.ravel(), xs) <= 1e-13
+    assert rel(xs, ref.x) <= 1e-10
+    below = [q for q, v in enumerate(hist) if v <= 1e-18]
+    assert len(below) >= o.MAX_TRUE_RESTARTS + 1
+
+
 def test_converging_solves_never_restart_the_shadow_residual():
     hz = hzmod()
     for wl in (I.plain_n64(), small_wedge()):

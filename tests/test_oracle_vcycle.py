@@ -232,6 +232,70 @@ def test_bicgstab_iterates_match_an_independent_implementation(precond):
         np.testing.assert_allclose(a, r, rtol=1e-9, atol=1e-9 * np.abs(r).max())
 
 
+def test_shadow_renewal_is_a_fresh_start_of_an_independent_implementation():
+    """Renewing the shadow residual after a full step (forced here: every step, up to the cap) takes
+    p = r and rho = <rhat_new, r>, i.e. Bi-CGSTAB starts afresh from the current iterate. With the
+    renewed shadow residual set to the current residual (scipy's choice of r^ at a start), the
+    iterates equal a chain of one-iteration scipy solves, each started from the previous iterate."""
+    n, kf, A, b = _problem()
+    h = o.build_hierarchy(n, kf, 20.0, "sl")
+    K = lambda v: o.vcycle(h, v)  # noqa: E731
+    M = spla.LinearOperator(A.shape, matvec=K, dtype=complex)
+    mine = []
+    res = o.bicgstab(A, b, K, tol=1e-30, maxit=6, callback=lambda x: mine.append(x.copy()), rhat=b,
+                     stall_cos2=2.0, stall_step2=np.inf, max_shadow_restarts=4,
+                     renew_shadow=lambda k, r: r.copy())
+    assert res.shadow_restarts == 4 and res.status == "maxit" and len(mine) == 6
+    ref, x = [], np.zeros_like(b)
+    for it in range(6):
+        if it <= 4:  # renewed before iterations 2..5: each one a fresh start from the last iterate
+            x, _ = spla.bicgstab(A, b, x0=x, M=M, rtol=1e-30, atol=0, maxiter=1)
+            ref.append(x.copy())
+    # iteration 6 continues iteration 5's recurrence (renewals used up): two scipy iterations from x4
+    two = []
+    spla.bicgstab(A, b, x0=ref[3], M=M, rtol=1e-30, atol=0, maxiter=2, callback=lambda z: two.append(z.copy()))
+    ref[4:] = two
+    for a, r in zip(mine, ref):
+        np.testing.assert_allclose(a, r, rtol=1e-9, atol=1e-9 * np.abs(r).max())
+
+
+def test_seeded_shadow_renewals_follow_the_generator():
+    """The k-th renewed shadow residual is SplitMix64 started from SHADOW_SEED + k * step (mod 2^64)."""
+    assert o.renewed_shadow_seed(1) == (0x5EED1312 + 0x2545F4914F6CDD1D) % 2**64
+    assert o.renewed_shadow_seed(7) == (0x5EED1312 + 7 * 0x2545F4914F6CDD1D) % 2**64
+    n, kf, A, b = _problem(16, 10.0)
+    seen = []
+    o.bicgstab(A, b, None, tol=1e-30, maxit=3, stall_cos2=2.0, stall_step2=np.inf, max_shadow_restarts=2,
+               renew_shadow=lambda k, r: (seen.append(k), o.shadow_residual(b.size, o.renewed_shadow_seed(k)))[1])
+    assert seen == [1, 2]
+    a = o.bicgstab(A, b, None, tol=1e-30, maxit=3, stall_cos2=2.0, stall_step2=np.inf, max_shadow_restarts=2)
+    c = o.bicgstab(A, b, None, tol=1e-30, maxit=3, stall_cos2=2.0, stall_step2=np.inf, max_shadow_restarts=2,
+                   renew_shadow=lambda k, r: o.shadow_residual(b.size, o.renewed_shadow_seed(k)))
+    assert np.array_equal(a.x, c.x)
+
+
+def test_true_residual_restart_below_the_attainable_accuracy():
+    """A tolerance below what FP64 can reach: the recurrence residual keeps falling while b - A x
+    stalls, so every recurrence stop is refused by the true residual and the solve restarts from it
+    (r = b - A x, p = r) until the cap; it then ends unconfirmed (status maxit) with x still at the
+    attainable accuracy. After each restart the recurrence residual starts again from the true one."""
+    n, kf, A, b = _problem()
+    h = o.build_hierarchy(n, kf, 20.0, "sl")
+    res = o.bicgstab(A, b, lambda v: o.vcycle(h, v), tol=1e-18, maxit=400)
+    assert res.restarts == o.MAX_TRUE_RESTARTS and res.status == "maxit"
+    assert res.true_relres <= 1e-13
+    xs = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-10
+    # the history drops below 1e-18 once per stop (restarts + 1 times), rising again after each
+    below = [q for q, v in enumerate(res.history) if v <= 1e-18]
+    assert len(below) == o.MAX_TRUE_RESTARTS + 1
+    for q in below[:-1]:
+        assert res.history[q + 1] > 1e2 * res.history[q]
+    # with the cap at zero the first refused stop ends the solve
+    one = o.bicgstab(A, b, lambda v: o.vcycle(h, v), tol=1e-18, maxit=400, max_true_restarts=0)
+    assert one.restarts == 0 and one.status == "maxit" and one.history[-1] <= 1e-18
+
+
 def test_bicgstab_solution_matches_direct_solve():
     n, kf, A, b = _problem(48, 30.0)
     h = o.build_hierarchy(n, kf, 30.0, "hyb")
