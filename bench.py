@@ -1,24 +1,31 @@
 """Benchmark: solve time to relative residual 1e-6, FP32-preconditioned vs all-FP64 form.
 
-Timed workload (default ``wedge512``): n = 512 (513^2 nodes), k = 100, seeded three-layer wedge
-k * {1.0, 1.5, 0.75}, 8 seeded point sources of 1/h^2, hybrid (HYB-V) hierarchy of 8 levels,
-Bi-CGSTAB to relres 1e-6. A step is one complete solve (every kernel of the hot path) with the
-inputs resident in HBM. Between solves the library rewrites every Krylov vector from the
-right-hand side, so no state carries over, and L2 is flushed (a 512 MB write, untimed) before
-each timed solve. The problem (~60 MB) fits in L2, so within a solve its kernels run mostly from
-L2; the HBM roofline is therefore measured on the n = 4096 grid (``--roofline-workload``, two
-profiled iterations launched kernel by kernel, no solve): per-kernel device times from CUDA
-events on the library's stream.
+Timed workload (default ``grf4096``): n = 4096 (4097^2 nodes), k = 1000 (kh = 0.244), smooth
+random medium k (1 + 0.3 g) with g a seeded Gaussian random field of correlation length 0.05,
+a centre point source of 1/h^2, hybrid (HYB-V) hierarchy of 10 levels, Bi-CGSTAB to relres 1e-6.
+A step is one complete solve (every kernel of the hot path) with the inputs resident in HBM; the
+library rewrites every Krylov vector from the right-hand side, so no state carries over between
+solves. The problem's arrays (3.6 GB) are far larger than L2 (129 MB); L2 is also flushed (a 512 MB
+write, untimed) before each timed solve.
 
-Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead: one full oracle
-solve gives its iteration count, then each step times a bounded sample of whole iterations,
-scaled to the full solve. Multi-GPU (torchrun): every rank solves its own replica (weak
-scaling, no collective on the data path); times are the max over ranks.
+Beside the headline: the FP64 form of the same solve, the solve through host buffers (``e2e``),
+the per-kernel roofline of one profiled iteration (CUDA events on the library's stream inside
+the solve's graph), the measured FP64 FMA rate (the ceiling of the FP64 Krylov kernels), the
+batched form (64 right-hand sides over 4 grids) and a prefix of the served Poisson stream, and
+for every workload the error of each form's solution against the FP64 oracle (test
+infrastructure, run on the host beside the GPU work; the n = 4096 oracle solve takes hours, so
+its solution is read from the sampled copy that tests/golden/make_grf4096_oracle.py wrote).
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead: each step is one
+whole Bi-CGSTAB iteration of the same workload, and the solve time is that per-iteration time
+times the oracle's own iteration count. Multi-GPU (torchrun): every rank solves its own replica
+(weak scaling, no collective on the data path); times are the max over ranks.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,6 +39,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1312_2880_gb300 import inputs as I  # noqa: E402
+
+GOLDEN_GRF4096 = os.path.join(ROOT, "tests", "golden", "grf_n4096_k1000_oracle.json")
+
 
 # Algorithmic (compulsory) HBM bytes per finest-grid node of one launch of each kernel. FP32 form:
 # the V-cycle reads and writes FP32 (complex 8 B, k h 4 B) on every level including the finest,
@@ -48,6 +58,7 @@ def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
         "gs_first": c / 2 + r / 2 + c,
         "gs_colour": (c + c + r + c) / 2,
         "kacz_colour": (5 * c * 2 + c + r) / 5,
+        "kacz_sweep": c + c + r + c,               # u in, f, k h; u out
         "restrict_residual": c + c + r + c / 4,
         "prolong_add": 2 * c + c / 4,
         "export": 2 * c,
@@ -66,20 +77,12 @@ KRYLOV_FP64 = {"k_update_p": (16, 8), "k_apply_rv": (20, 13), "k_update_s": (12,
                "k_update_xr": (36, 18)}
 
 
-def kernel_fp64_flops_per_node(kernel: str) -> float:
-    return KRYLOV_FP64.get(kernel, (0, 0))[0]
-
-
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
-
-
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (probe on this pool: 1.20 TFLOP/s)
-FP64_PEAK_INSTR = FP64_PEAK_TFLOPS / 2  # FP64-pipe instructions per ps (an FMA is one instruction)
 
 
 class ClockSampler:
@@ -191,14 +194,14 @@ def l2_flush_buffer():
     return torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
 
 
-def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
+def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float, maxit: int):
     """Each step: flush L2 (untimed), then one solve bracketed by CUDA events on the caller's
     stream. Returns per-step ms, their sum and the solve infos."""
     import torch
 
     flush = l2_flush_buffer()
     for _ in range(warmup):
-        P.solve(rhs, tol=tol, maxit=5000)
+        P.solve(rhs, tol=tol, maxit=maxit)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -207,29 +210,32 @@ def time_solves(P, rhs, steps: int, warmup: int, world: int, tol: float):
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     infos = []
+    x = None
     for s in range(steps):
         flush.fill_(s & 0xFF)
         ev[s][0].record(stream)
-        _, info, _ = P.solve(rhs, tol=tol, maxit=5000)
+        x, info, _ = P.solve(rhs, tol=tol, maxit=maxit)
         ev[s][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     per = [a.elapsed_time(b) for a, b in ev]
-    return per, sum(per), infos
+    return per, sum(per), infos, x
 
 
-def time_e2e(P, rhs_host, steps: int, tol: float):
+def time_e2e(P, rhs_host, steps: int, tol: float, maxit: int):
+    """The same solve through the host-buffer entry point: the right-hand side is copied in and the
+    solution out inside every timed call."""
     import torch
 
     out = np.empty_like(rhs_host)
-    P.solve_host(rhs_host, tol=tol, maxit=5000, out=out)
+    P.solve_host(rhs_host, tol=tol, maxit=maxit, out=out)
     torch.cuda.synchronize()
     t = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        _, info, _ = P.solve_host(rhs_host, tol=tol, maxit=5000, out=out)
+        P.solve_host(rhs_host, tol=tol, maxit=maxit, out=out)
         t.append((time.perf_counter() - t0) * 1e3)
     return t, out
 
@@ -244,40 +250,48 @@ def profile(P, rhs, iterations: int = 2):
     return per
 
 
-def roofline(per, fp32: bool, hbm_peak: float, peak_kind: str, n: int, iterations: int = 2):
-    """The dominant kernel (largest total time) of a profile and its achieved rate."""
+def roofline(per, fp32: bool, hbm_peak: float, peak_kind: str, n: int, fp64_peak: dict | None):
+    """The dominant kernel (largest total time) of a profile and its achieved rate: an FP64 Krylov
+    kernel against the measured FP64 FMA rate (flops, an FMA counted 2), a V-cycle kernel against
+    the measured HBM copy rate; the HBM fraction is given beside the FP64 one."""
     total = sum(sum(v) for v in per.values())
     (name, level), times = max(per.items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
     nodes = ((n >> level) + 1) ** 2
-    if name.startswith("k_"):
-        flops = kernel_fp64_flops_per_node(name) * nodes
+    gbs = kernel_bytes_per_node(name, fp32) * nodes / (avg_ms * 1e-3) / 1e9
+    if name.startswith("k_") and fp64_peak:
+        flops = KRYLOV_FP64[name][0] * nodes
         achieved = flops / (avg_ms * 1e-3) / 1e12
-        instr = KRYLOV_FP64[name][1] * nodes / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": name, "level": level, "bound": "alu", "achieved": round(achieved, 4),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 rate (recipe table); FMA = 2 flops",
-                "fp64_pipe_frac": round(instr / FP64_PEAK_INSTR, 4),
-                "hbm_gbs": round(kernel_bytes_per_node(name, fp32) * nodes / (avg_ms * 1e-3) / 1e9, 1)}
+        peak = fp64_peak["tflops"]
+        roof = {"kernel": name, "level": level, "bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": "measured: hz_measure_fp64_rate in this run (DFMA chains on every SM, CUDA events); "
+                               "FMA = 2 flops",
+                "flops_per_node": KRYLOV_FP64[name][0], "nodes": nodes,
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4), "hbm_peak": hbm_peak}
     else:
-        byts = kernel_bytes_per_node(name, fp32) * nodes
-        achieved = byts / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": name, "level": level, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind}
+        roof = {"kernel": name, "level": level, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "peak_source": peak_kind,
+                "bytes_per_node": kernel_bytes_per_node(name, fp32), "nodes": nodes}
     roof.update({"traffic": None, "avg_launch_ms": round(avg_ms, 5), "launches": len(times),
                  "share": round(sum(times) / total, 4)})
     return roof
 
 
 def sweep_rates(per, fp32: bool, hbm_peak: float, n: int):
-    """Achieved HBM GB/s (algorithmic bytes / device time) of each finest-grid V-cycle kernel."""
+    """Achieved HBM GB/s (algorithmic bytes / device time) of each V-cycle kernel on the levels
+    larger than L2 (n_l >= 2048), and of the Kaczmarz sweeps (L2-resident levels, for reference)."""
     out = {}
     for (name, level), times in per.items():
-        if level != 0 or name.startswith("k_") or kernel_bytes_per_node(name, fp32) == 0:
+        nl = n >> level
+        if name.startswith("k_") or kernel_bytes_per_node(name, fp32) == 0:
+            continue
+        if nl < 2048 and not name.startswith("kacz"):
             continue
         avg = sum(times) / len(times)
-        gbs = kernel_bytes_per_node(name, fp32) * (n + 1) ** 2 / (avg * 1e-3) / 1e9
-        out[name] = {"gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4), "ms": round(avg, 4)}
+        gbs = kernel_bytes_per_node(name, fp32) * (nl + 1) ** 2 / (avg * 1e-3) / 1e9
+        out[f"{name}@L{level}"] = {"n_l": nl, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                                   "ms": round(avg, 4), "launches_per_iteration": len(times) // 2}
     return out
 
 
@@ -319,64 +333,98 @@ def profiled_traffic(kernel: str, level: int, workload_name: str):
     return None
 
 
-def shares(per):
+def shares(per, top: int = 12):
     total = sum(sum(v) for v in per.values())
-    top = sorted(per.items(), key=lambda kv: -sum(kv[1]))[:10]
-    return {f"{k[0]}@L{k[1]}": round(sum(v) / total, 4) for k, v in top}
+    rows = sorted(per.items(), key=lambda kv: -sum(kv[1]))[:top]
+    return {f"{k[0]}@L{k[1]}": round(sum(v) / total, 4) for k, v in rows}
 
 
-def cpu_baseline(wl, iters_full: float, sample_iters: int):
-    """Time the FP64 oracle on this host for `sample_iters` Bi-CGSTAB iterations of the workload."""
+# --------------------------------------------------------------------------- oracle side (host)
+# The oracle is test infrastructure: the benchmark runs it only to state each form's error against
+# it and to time the CPU baseline, in worker processes started with "spawn" beside the GPU work.
+
+
+def oracle_job(spec):
+    """One oracle task in a worker process. ("solve", kind, key): the oracle's own solve to relres
+    1e-6 of a workload (kind plain64 / wedge512 / batch (problem index, rhs index) / serve (request
+    id, stream length, rate)), returning its solution and iteration count. ("sample", workload,
+    iterations): the time of that many whole Bi-CGSTAB iterations of the workload (after an
+    untimed setup)."""
     import oracle as o
 
+    kind = spec[0]
+    if kind == "sample":
+        wl = workload(spec[1])
+        t0 = time.perf_counter()
+        A = o.helmholtz_matrix(wl.n, wl.kfield)
+        H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
+        setup = time.perf_counter() - t0
+        b = wl.rhs.ravel()
+        t0 = time.perf_counter()
+        o.bicgstab(A, b, lambda v: o.vcycle(H, v), tol=1e-300, maxit=spec[2])
+        dt = time.perf_counter() - t0
+        return {"per_iter_ms": dt * 1e3 / spec[2], "iterations": spec[2], "setup_s": setup}
+    wl = oracle_workload(spec[1], spec[2])
     A = o.helmholtz_matrix(wl.n, wl.kfield)
     H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
-    b = wl.rhs.ravel()
-    t0 = time.perf_counter()
-    o.bicgstab(A, b, lambda v: o.vcycle(H, v), tol=1e-300, maxit=sample_iters)
-    dt = time.perf_counter() - t0
-    per_iter_ms = dt * 1e3 / sample_iters
-    return {"value": round(per_iter_ms * iters_full, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample_iters} Bi-CGSTAB iterations of the same n={wl.n} solve ({per_iter_ms:.1f} ms each, "
-                      f"numpy/scipy, one thread), scaled by the {iters_full:g} iterations of the FP64 form"}
+    res = o.bicgstab(A, wl.rhs.ravel(), lambda v: o.vcycle(H, v), tol=wl.tol, maxit=5000)
+    return {"x": res.x, "iterations": res.iterations, "status": res.status, "true_relres": res.true_relres}
 
 
-def oracle_errors(wl, xs: dict, tol: float):
-    """max |x - x_oracle| / max |x_oracle| of each form's solution against the FP64 oracle's own
-    solve of the same system to the same tolerance (both stop at relres tol, so the difference is
-    of the order tol times the conditioning, not rounding)."""
-    import oracle as o
+def oracle_workload(kind: str, key):
+    """The single-right-hand-side workload behind an oracle task (same inputs the GPU side solves)."""
+    if kind in ("plain64", "wedge512"):
+        return workload(kind)
+    if kind == "batch":
+        wl = I.batch_problems(rhs_per_k=16)[key[0]]
+        return I.Workload(wl.name, wl.n, wl.k_ref, wl.kfield, wl.rhs[key[1]], variant=wl.variant, levels=wl.levels)
+    if kind == "serve":
+        rid, count, rate = key
+        req = I.serving_requests(count, rate)[rid]
+        return I.Workload(f"request{rid}", req.n, req.k, I.request_medium(req), I.point_source_rhs(req.n, [req.source]))
+    raise ValueError(kind)
 
-    A = o.helmholtz_matrix(wl.n, wl.kfield)
-    H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
-    ref = o.bicgstab(A, wl.rhs.ravel(), lambda v: o.vcycle(H, v), tol=tol, maxit=5000)
-    scale = np.abs(ref.x).max()
-    out = {f"{p}_form": float(np.abs(x.ravel() - ref.x).max() / scale) for p, x in xs.items()}
-    out["oracle_iterations"] = ref.iterations
+
+def rel_err(x, ref) -> float:
+    x = np.asarray(x).ravel()
+    ref = np.asarray(ref).ravel()
+    return float(np.abs(x - ref).max() / np.abs(ref).max())
+
+
+def grf4096_sampled_errors(xs: dict):
+    """max over the sampled nodes of |x - x_oracle| / max |x_oracle| of each form's n = 4096 solution,
+    against the oracle's solve stored by tests/golden/make_grf4096_oracle.py (None if absent)."""
+    if not os.path.exists(GOLDEN_GRF4096):
+        return None
+    g = json.load(open(GOLDEN_GRF4096))
+    s = np.array(g["sampled"])
+    i, j = s[:, 0].astype(int), s[:, 1].astype(int)
+    ref = s[:, 2] + 1j * s[:, 3]
+    out = {f"{p}_form": float(np.abs(x[j, i] - ref).max() / g["max_abs_x"]) for p, x in xs.items()}
+    out.update({"oracle_iterations": g["iterations"], "oracle_true_relres": g["true_relres"],
+                "sampled_nodes": int(len(ref)),
+                "sample": "every 128th node in each direction plus the 9 x 9 nodes around the source"})
     return out
 
 
-def small_case_errors(tol: float):
-    """The same comparison on the n = 64 plain workload (both forms)."""
-    import torch
-
-    from paper_1312_2880_gb300 import hz
-
-    wl = workload("plain64")
-    rhs = torch.from_numpy(wl.rhs).cuda()
-    xs = {}
-    for prec in ("fp32", "fp64"):
-        P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
-        x, _, _ = P.solve(rhs, tol=tol, maxit=5000)
-        xs[prec] = x.cpu().numpy()
-        P.close()
-    return oracle_errors(wl, xs, tol)
+def serve_sample_ids(count: int, rate: float, sizes=(128, 256, 512), per_size: int = 1):
+    """Request ids of the served prefix whose solutions are checked against the oracle: the first
+    `per_size` requests of each listed grid size (the oracle's solves of larger grids take minutes)."""
+    reqs = I.serving_requests(count, rate)
+    out = []
+    for n in sizes:
+        out += [q.rid for q in reqs if q.n == n][:per_size]
+    return out
 
 
-def run_batched(precision: str, reps: int = 3):
+# --------------------------------------------------------------------------- batched and served forms
+
+
+def run_batched(precision: str, reps: int = 3, keep=()):
     """Four constant-k problems (k, n) = (50, 96), (100, 192), (200, 384), (300, 576), 16 seeded
     point sources each, solved as one group (every right-hand side of every problem advances in
-    the same graph launch per iteration; finished ones retire). Returns timing and counts."""
+    the same graph launch per iteration; finished ones retire). Returns timing, counts and the
+    solutions of the (problem, rhs) pairs listed in `keep`."""
     import torch
 
     from paper_1312_2880_gb300 import hz
@@ -393,6 +441,7 @@ def run_batched(precision: str, reps: int = 3):
         t0 = time.perf_counter()
         xs, infos = G.solve(rhs, tol=1e-6, maxit=3000, allow_fail=True)
         t.append((time.perf_counter() - t0) * 1e3)
+    kept = {(pi, q): xs[pi][q].cpu().numpy() for pi, q in keep}
     its = [i["iterations"] for i in infos]
     conv = sum(1 for i in infos if i["status"] == 0)
     G.close()
@@ -400,46 +449,80 @@ def run_batched(precision: str, reps: int = 3):
         P.close()
     ms = statistics.median(t)
     return {"ms": round(ms, 2), "rhs": len(infos), "converged": conv, "iterations_min": min(its),
-            "iterations_max": max(its), "solves_per_s": round(len(infos) * 1e3 / ms, 1)}
+            "iterations_max": max(its), "solves_per_s": round(len(infos) * 1e3 / ms, 1)}, kept
 
 
-def run_serving(precision: str, count: int, rate: float, seed: int = I.SEED_BASE + 5):
-    """Poisson stream of single-RHS requests through the continuous-batching server."""
+def run_serving(precision: str, count: int, rate: float, keep=()):
+    """The first `count` requests of the served Poisson stream (200 requests/s, n uniform over
+    {128, ..., 2048}, kh = 2 pi / 12, wedge or random-field media, one seeded source each) through
+    the continuous-batching server. Media are generated before the clock starts."""
     import torch
 
     from paper_1312_2880_gb300.serve import Job, Server
 
-    u = I.uniform01(seed, 4 * count)
-    gaps = -np.log(1.0 - u[0::4]) / rate
-    t = np.cumsum(gaps) - gaps[0]
-    sizes = SERVE_SIZES
+    reqs = I.serving_requests(count, rate)
     media = {}
     jobs = []
-    for r in range(count):
-        n = sizes[min(len(sizes) - 1, int(u[4 * r + 1] * len(sizes)))]
-        medium = "wedge" if u[4 * r + 2] < 0.5 else "grf"
-        mseed = I.SEED_BASE + 1000 + int(u[4 * r + 3] * 2)
-        key = (n, medium, mseed)
-        k = SERVE_KH * n
+    for q in reqs:
+        key = (q.n, q.medium, q.medium_seed)
         if key not in media:
-            media[key] = I.wedge_k(n, k, mseed) if medium == "wedge" else I.grf_k(n, k, mseed)
-        src = I.random_interior_nodes(n, 1, seed + 17 * r + 3)[0]
-        jobs.append(Job(r, n, key, (lambda key=key: media[key]), k, src, arrival=float(t[r])))
+            media[key] = I.request_medium(q)
+        jobs.append(Job(q.rid, q.n, key, (lambda key=key: media[key]), q.k, q.source, arrival=q.arrival_s))
     free = torch.cuda.mem_get_info()[0]
-    srv = Server(hbm_budget=int(free * 0.6), precision=precision, max_active=32, maxit=3000)
+    srv = Server(hbm_budget=int(free * 0.6), precision=precision, max_active=32, maxit=4000, keep_solutions=set(keep))
     summ = srv.run(jobs, realtime=True)
+    kept = {j.rid: j.result["x"] for j in srv.done if "x" in j.result}
+    its = [j.result.get("iterations", 0.0) for j in srv.done]
     srv.close()
-    summ["rate_hz"] = rate
-    summ["requests"] = count
-    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in summ.items()}
+    service = sum((j.end - j.start) for j in srv.done)
+    waits = [(j.start - j.arrival) * 1e3 for j in srv.done]
+    last_arrival = reqs[-1].arrival_s if reqs else 0.0
+    summ.update({"rate_hz": rate, "requests": count, "iterations_max": max(its) if its else None,
+                 "mean_concurrency": round(service / max(summ["wall_s"], 1e-9), 2),
+                 "admission_wait_p50_ms": round(float(np.percentile(waits, 50)), 2) if waits else None,
+                 "last_arrival_s": round(last_arrival, 3),
+                 # arrivals outpace service: latency is then mostly time spent queued
+                 "queue_bound": bool(summ["wall_s"] > 1.5 * last_arrival + 0.05)})
+    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in summ.items()}, kept
 
 
-# Served stream: grid sizes and kh. The stream of the serving workload (kh = 2 pi / 12 with wedge
-# and random-field media, n up to 2048) does not converge within 4000 iterations for n >= 256 in
-# either form (measured), so the served requests use kh = 0.2, the resolution of the n = 512
-# wedge workload, and sizes up to 1024.
-SERVE_SIZES = (128, 256, 512, 1024)
-SERVE_KH = 0.2
+# --------------------------------------------------------------------------- the GPU arm
+
+
+def small_solves(names=("plain64", "wedge512"), tol: float = 1e-6):
+    """Both forms' solutions of the small workloads (for their error against the oracle)."""
+    import torch
+
+    from paper_1312_2880_gb300 import hz
+
+    out = {}
+    for name in names:
+        wl = workload(name)
+        rhs = torch.from_numpy(wl.rhs).cuda()
+        for prec in ("fp32", "fp64"):
+            P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
+            x, info, _ = P.solve(rhs, tol=tol, maxit=4000)
+            out[(name, prec)] = (x.cpu().numpy(), info["iterations"])
+            P.close()
+    return out
+
+
+def start_oracle_pool(args, serve_ids):
+    """Worker processes (spawn) for the oracle tasks, submitted before any GPU work."""
+    import concurrent.futures
+    import multiprocessing
+
+    pool = concurrent.futures.ProcessPoolExecutor(max_workers=args.oracle_workers,
+                                                  mp_context=multiprocessing.get_context("spawn"))
+    fut = {"sample": pool.submit(oracle_job, ("sample", args.workload, args.cpu_sample_iters))}
+    for name in ("plain64", "wedge512"):
+        fut[name] = pool.submit(oracle_job, ("solve", name, None))
+    if not args.skip_forms:
+        for pi in range(4):
+            fut[("batch", pi, 0)] = pool.submit(oracle_job, ("solve", "batch", (pi, 0)))
+        for rid in serve_ids:
+            fut[("serve", rid)] = pool.submit(oracle_job, ("solve", "serve", (rid, args.serve_requests, args.serve_rate)))
+    return pool, fut
 
 
 def run_ours(args):
@@ -448,94 +531,62 @@ def run_ours(args):
     from paper_1312_2880_gb300 import build, hz
 
     world, rank, local = dist_setup(args.gpus)
+    with_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    serve_ids = serve_sample_ids(args.serve_requests, args.serve_rate) if not args.skip_forms else []
+    pool, fut = start_oracle_pool(args, serve_ids) if with_oracle else (None, {})
     build.build()
     wl = workload(args.workload)
     tol = 1e-6
     rhs = torch.from_numpy(wl.rhs).cuda()
     hbm_peak, peak_kind = load_peaks()
-    results = {}
+    fp64_peak = hz.measure_fp64_rate()
+    results, probs = {}, {}
     for prec in ("fp32", "fp64"):
         P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision=prec, levels=wl.levels, k_ref=wl.k_ref)
         steps = args.steps if prec == "fp32" else max(1, min(args.steps, args.fp64_steps))
-        warm = args.warmup if prec == "fp32" else max(3, min(args.warmup, 3))
+        warm = args.warmup if prec == "fp32" else max(1, min(args.warmup, args.fp64_warmup))
         with ClockSampler(local) as clk:
-            per, total, infos = time_solves(P, rhs, steps, warm, world, tol)
-        ms = barrier_max(total / steps, world)
-        x_chk, info_chk, _ = P.solve(rhs, tol=tol, maxit=5000)
-        results[prec] = {"ms": ms, "per_step_ms": [round(x, 3) for x in per], "iterations": infos[-1]["iterations"],
-                         "relres_true": infos[-1]["relres_true"], "clocks": clk.summary(), "P": P,
-                         "forms": pass_forms(P), "x": x_chk.cpu().numpy()}
-    P32 = results["fp32"]["P"]
-    per_small = profile(P32, rhs, 2)
-    launches_per_iter = sum(len(v) for k, v in per_small.items() if k[0] != "zero") // 2
-    e2e_t, _ = time_e2e(P32, wl.rhs, max(1, min(args.steps, 3)), tol)
+            per, total, infos, x = time_solves(P, rhs, steps, warm, world, tol, args.maxit)
+        results[prec] = {"ms": barrier_max(total / steps, world), "per_step_ms": [round(v, 3) for v in per],
+                         "steps": steps, "warmup": warm, "iterations": infos[-1]["iterations"],
+                         "relres_true": infos[-1]["relres_true"], "status": infos[-1]["status"],
+                         "restarts": infos[-1]["restarts"], "clocks": clk.summary(), "forms": pass_forms(P),
+                         "x": x.cpu().numpy()}
+        probs[prec] = P
+    P32 = probs["fp32"]
+    e2e_t, _ = time_e2e(P32, wl.rhs, max(1, min(args.steps, 3)), tol, args.maxit)
     e2e_ms = barrier_max(statistics.mean(e2e_t), world)
-    nbytes = 16 * (wl.n + 1) ** 2
+    per32 = profile(P32, rhs, 2)
+    per64 = profile(probs["fp64"], rhs, 2)
+    launches_per_iter = sum(len(v) for v in per32.values()) // 2 + 1  # + the loop-control kernel
+    for P in probs.values():
+        P.close()
+    roof = roofline(per32, True, hbm_peak, peak_kind, wl.n, fp64_peak)
+    roof["workload"] = wl.name
+    roof["traffic"] = profiled_traffic(roof["kernel"], roof["level"], wl.name)
     it32 = results["fp32"]["iterations"]
-    gpu_launches = int(args.steps * ((int(np.ceil(it32)) + 3) * launches_per_iter + 4))
-    for r in results.values():
-        r["P"].close()
+    gpu_launches = int(args.steps * (math.ceil(it32) * launches_per_iter + 4))
     batched = serving = None
+    kept_b, kept_s = {}, {}
     if not args.skip_forms:
-        batched = {"fp32_form": run_batched("fp32"), "fp64_form": run_batched("fp64")}
-        serving = {"fp32_form": run_serving("fp32", args.serve_requests, args.serve_rate),
-                   "fp64_form": run_serving("fp64", args.serve_requests, args.serve_rate)}
-    # HBM roofline on a grid larger than L2: two profiled FP32-preconditioned iterations.
-    rw = workload(args.roofline_workload)
-    Pr = hz.Problem(rw.n, rw.kfield, 0.5, variant=rw.variant, precision="fp32", levels=rw.levels, k_ref=rw.k_ref)
-    rrhs = torch.from_numpy(rw.rhs).cuda()
-    per_big = profile(Pr, rrhs, 2)
-    roof = roofline(per_big, True, hbm_peak, peak_kind, rw.n)
-    roof["workload"] = rw.name
-    roof["traffic"] = profiled_traffic(roof["kernel"], roof["level"], rw.name)
-    roof_forms = pass_forms(Pr)
-    sweeps = sweep_rates(per_big, True, hbm_peak, rw.n)
-    big_iter_ms = sum(sum(v) for v in per_big.values()) / 2
-    Pr.close()
-    del rrhs
+        keep_b = [(pi, 0) for pi in range(4)]
+        b32, kb32 = run_batched("fp32", keep=keep_b)
+        b64, kb64 = run_batched("fp64", keep=keep_b)
+        batched = {"fp32_form": b32, "fp64_form": b64}
+        kept_b = {"fp32": kb32, "fp64": kb64}
+        s32, ks32 = run_serving("fp32", args.serve_requests, args.serve_rate, keep=serve_ids)
+        s64, ks64 = run_serving("fp64", args.serve_requests, args.serve_rate, keep=serve_ids)
+        serving = {"fp32_form": s32, "fp64_form": s64,
+                   "stream": f"the first {args.serve_requests} requests of the 2000-request stream "
+                             f"(Poisson, {args.serve_rate:g}/s, n in 128..2048, kh = 2 pi / 12)"}
+        kept_s = {"fp32": ks32, "fp64": ks64}
+    small = small_solves() if with_oracle else {}
     replica = replica_fields(world, results["fp32"]["ms"])
-    line = {
-        "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
-        "value": round(results["fp32"]["ms"], 3),
-        "unit": "ms",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(results["fp32"]["ms"], 3),
-        "per_step_ms": results["fp32"]["per_step_ms"],
-        "higher_is_better": False,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "c64 V-cycle / c128 Krylov",
-        "data": "synthetic",
-        "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "medium": wl.meta.get("medium", ""),
-                   "levels": wl.levels, "variant": wl.variant, "tol": tol, "rhs": wl.meta.get("rhs", ""),
-                   "l2": "flushed before every timed solve (512 MB write); HBM rates measured on the roofline workload, larger than L2",
-                   "parallelism": replica["parallelism"]},
-        "iterations": it32,
-        "relres_true": results["fp32"]["relres_true"],
-        "solves_per_s": replica["solves_per_s"],
-        "fp64_form": {"ms": round(results["fp64"]["ms"], 3), "iterations": results["fp64"]["iterations"],
-                      "relres_true": results["fp64"]["relres_true"],
-                      "speedup_of_fp32_form": round(results["fp64"]["ms"] / results["fp32"]["ms"], 3),
-                      "tile_autotuner": results["fp64"]["forms"]},
-        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "batched": batched,
-        "serving": serving,
-        "roofline": roof,
-        "sweep_hbm": {"workload": rw.name, "kernels": sweeps, "iteration_ms": round(big_iter_ms, 3),
-                      "kernel_share": shares(per_big)},
-        "kernel_share": shares(per_small),
-        "gpu_launches": gpu_launches,
-        "tile_autotuner": {wl.name: results["fp32"]["forms"], rw.name: roof_forms,
-                           "forms": "0 = shared-memory tiles; v = 1..8: register streaming, 2^v rows per warp"},
-        "clocks": results["fp32"]["clocks"],
-        "clocks_fp64_form": results["fp64"]["clocks"],
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, results["fp64"]["iterations"], args.cpu_sample_iters)
-        line["error_vs_oracle"] = {wl.name: oracle_errors(wl, {p: r["x"] for p, r in results.items()}, tol),
-                                   "plain_n64_k20": small_case_errors(tol)}
+    line = headline_line(args, wl, results, replica, e2e_ms, roof, per32, per64, hbm_peak, fp64_peak, gpu_launches,
+                         batched, serving)
+    if with_oracle:
+        line.update(oracle_fields(args, wl, results, fut, small, kept_b, kept_s, serve_ids))
+        pool.shutdown()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -545,7 +596,98 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def headline_line(args, wl, results, replica, e2e_ms, roof, per32, per64, hbm_peak, fp64_peak, gpu_launches,
+                  batched, serving):
+    r32, r64 = results["fp32"], results["fp64"]
+    nbytes = 16 * (wl.n + 1) ** 2
+    return {
+        "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
+        "value": round(r32["ms"], 3),
+        "unit": "ms",
+        "n_gpus": replica["n_gpus"],
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(r32["ms"], 3),
+        "per_step_ms": r32["per_step_ms"],
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 V-cycle / c128 Krylov",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "medium": wl.meta.get("medium", ""),
+                   "levels": wl.levels, "variant": wl.variant, "tol": wl.tol, "rhs": wl.meta.get("rhs", ""),
+                   "l2": "inputs (3.6 GB of arrays) larger than L2, and L2 flushed before every timed solve (512 MB write)",
+                   "parallelism": replica["parallelism"]},
+        "iterations": r32["iterations"],
+        "relres_true": r32["relres_true"],
+        "status": r32["status"],
+        "solves_per_s": replica["solves_per_s"],
+        "fp64_form": {"ms": round(r64["ms"], 3), "per_step_ms": r64["per_step_ms"], "steps": r64["steps"],
+                      "warmup": r64["warmup"], "iterations": r64["iterations"], "relres_true": r64["relres_true"],
+                      "status": r64["status"], "speedup_of_fp32_form": round(r64["ms"] / r32["ms"], 3),
+                      "iteration_ms": round(r64["ms"] / max(r64["iterations"], 1), 4),
+                      "kernel_share": shares(per64, 8), "clocks": r64["clocks"]},
+        "iteration_ms": round(r32["ms"] / max(r32["iterations"], 1), 4),
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "batched": batched,
+        "serving": serving,
+        "roofline": roof,
+        "fp64_peak": {"tflops": round(fp64_peak["tflops"], 4), "probe_ms": round(fp64_peak["ms"], 3)},
+        "sweep_hbm": {"workload": wl.name, "kernels": sweep_rates(per32, True, hbm_peak, wl.n),
+                      "iteration_ms_profiled": round(sum(sum(v) for v in per32.values()) / 2, 3)},
+        "kernel_share": shares(per32),
+        "gpu_launches": gpu_launches,
+        "tile_autotuner": {"fp32_form": r32["forms"], "fp64_form": r64["forms"],
+                           "forms": "0 = shared-memory tiles; v = 1..8: register streaming, 2^v rows per warp"},
+        "clocks": r32["clocks"],
+    }
+
+
+def oracle_fields(args, wl, results, fut, small, kept_b, kept_s, serve_ids):
+    """error_vs_oracle for every workload and the CPU baseline, from the oracle tasks."""
+    err = {wl.name: grf4096_sampled_errors({p: r["x"] for p, r in results.items()})
+           if wl.name == "grf_n4096_k1000" else None}
+    for name, label in (("plain64", "plain_n64_k20"), ("wedge512", "wedge_n512_k100")):
+        ref = fut[name].result()
+        err[label] = {f"{p}_form": rel_err(small[(name, p)][0], ref["x"]) for p in ("fp32", "fp64")}
+        err[label].update({"oracle_iterations": ref["iterations"],
+                           "gpu_iterations": {p: small[(name, p)][1] for p in ("fp32", "fp64")}})
+    if kept_b:
+        per = {}
+        for pi in range(4):
+            ref = fut[("batch", pi, 0)].result()
+            per[f"n={I.BATCH_SPECS[pi][1]},rhs0"] = {f"{p}_form": rel_err(kept_b[p][(pi, 0)], ref["x"])
+                                                     for p in ("fp32", "fp64")}
+        err["batched"] = {"max": {f"{p}_form": max(v[f"{p}_form"] for v in per.values()) for p in ("fp32", "fp64")},
+                          "cases": per, "sample": "right-hand side 0 of each of the 4 grids"}
+    if kept_s:
+        per = {}
+        for rid in serve_ids:
+            ref = fut[("serve", rid)].result()
+            per[f"request{rid}"] = {f"{p}_form": (rel_err(kept_s[p][rid], ref["x"]) if rid in kept_s[p] else None)
+                                    for p in ("fp32", "fp64")}
+        err["served"] = {"cases": per, "sample": "the first request of each of n = 128, 256, 512 in the served prefix"}
+    samp = fut["sample"].result()
+    g_iters = json.load(open(GOLDEN_GRF4096))["iterations"] if (os.path.exists(GOLDEN_GRF4096) and
+                                                                  wl.name == "grf_n4096_k1000") else None
+    iters_full = g_iters if g_iters is not None else results["fp64"]["iterations"]
+    cpu = {"value": round(samp["per_iter_ms"] * iters_full, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": f"{samp['iterations']} whole Bi-CGSTAB iterations of the same {wl.name} solve "
+                     f"({samp['per_iter_ms']:.0f} ms each, numpy/scipy on one host core; scipy's sparse products "
+                     f"hold the GIL, so the oracle uses one core), times the "
+                     f"{'oracle' if g_iters is not None else 'FP64 form'}'s {iters_full:g} iterations; "
+                     f"untimed setup {samp['setup_s']:.0f} s"}
+    return {"error_vs_oracle": err, "cpu_baseline": cpu}
+
+
+# --------------------------------------------------------------------------- reference arm (the oracle)
+
+
 def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: untimed setup, then `warmup` and `steps` steps of one
+    whole Bi-CGSTAB iteration each (o.bicgstab with maxit = 1, from x0 = 0); the solve time is the
+    mean step time times the oracle's own iteration count (from its stored solve of the n = 4096
+    workload, or from one full solve for the smaller workloads)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -556,36 +698,39 @@ def run_reference(args):
     H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
     b = wl.rhs.ravel()
     K = lambda v: o.vcycle(H, v)  # noqa: E731
-    # one full oracle solve gives the iteration count (and serves as warm-up)
-    full = o.bicgstab(A, b, K, tol=1e-6, maxit=5000)
-    for _ in range(max(0, args.warmup - 1)):
-        o.bicgstab(A, b, K, tol=1e-300, maxit=args.cpu_sample_iters)
+    if wl.name == "grf_n4096_k1000" and os.path.exists(GOLDEN_GRF4096):
+        iters_full, source = json.load(open(GOLDEN_GRF4096))["iterations"], "its stored solve"
+    else:
+        iters_full, source = o.bicgstab(A, b, K, tol=1e-6, maxit=5000).iterations, "one full solve in this run"
+    for _ in range(args.warmup):
+        o.bicgstab(A, b, K, tol=1e-300, maxit=1)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.bicgstab(A, b, K, tol=1e-300, maxit=args.cpu_sample_iters)
-        times.append((time.perf_counter() - t0) * 1e3 / args.cpu_sample_iters)
+        o.bicgstab(A, b, K, tol=1e-300, maxit=1)
+        times.append((time.perf_counter() - t0) * 1e3)
     per_iter = statistics.mean(times)
-    value = per_iter * full.iterations
+    value = per_iter * iters_full
     line = {
         "impl": "reference",
         "metric": "solve time to relres 1e-6 (FP32-preconditioned form; FP64 form beside it)",
         "value": round(value, 1), "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(value, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": round(per_iter, 1), "value_is": "per-step time x the oracle's iterations to relres 1e-6",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128", "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "k": wl.k_ref, "levels": wl.levels, "variant": wl.variant},
-        "iterations": full.iterations,
+        "iterations": iters_full,
         "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"each step the first {args.cpu_sample_iters} Bi-CGSTAB iterations of the n={wl.n} "
-                                   f"solve ({per_iter:.1f} ms each), scaled by the oracle's {full.iterations:g} "
-                                   f"iterations to relres 1e-6"},
+                         "sample": f"each step one whole Bi-CGSTAB iteration of the n={wl.n} solve ({per_iter:.0f} ms, "
+                                   f"numpy/scipy on one host core), times the oracle's {iters_full:g} iterations to "
+                                   f"relres 1e-6 ({source})"},
         "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_profile_case(args):
-    """One FP32-form iteration of the roofline workload launched kernel by kernel (for ncu)."""
+    """One iteration of a workload launched kernel by kernel (for ncu), in the form --profile-precision."""
     import torch
 
     from paper_1312_2880_gb300 import build, hz
@@ -599,6 +744,23 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": rw.name, "launches": len(recs)}))
     P.close()
+
+
+def run_serving_only(args):
+    """The served stream alone (both forms, or --serve-precision): a long run of the config."""
+    import torch
+
+    from paper_1312_2880_gb300 import build
+
+    torch.cuda.set_device(0)
+    build.build()
+    out = {}
+    for prec in args.serve_precision.split(","):
+        with ClockSampler(0) as clk:
+            summ, _ = run_serving(prec, args.serve_requests, args.serve_rate)
+        summ["clocks"] = clk.summary()
+        out[f"{prec}_form"] = summ
+    print(json.dumps({"serving": out, "requests": args.serve_requests, "rate_hz": args.serve_rate}), flush=True)
 
 
 def run_tables(args):
@@ -649,16 +811,20 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-warmup", type=int, default=2)
+    ap.add_argument("--maxit", type=int, default=4000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="wedge512")
-    ap.add_argument("--roofline-workload", default="grf4096")
-    ap.add_argument("--cpu-sample-iters", type=int, default=30)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="grf4096")
+    ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--oracle-workers", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip every oracle task (baseline and errors)")
     ap.add_argument("--profile-case", default=None, help="run one profiled iteration of this workload and exit")
     ap.add_argument("--skip-forms", action="store_true", help="skip the batched and serving measurements")
-    ap.add_argument("--serve-requests", type=int, default=150)
-    ap.add_argument("--serve-rate", type=float, default=15.0)
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-only", action="store_true", help="run only the served stream and exit")
+    ap.add_argument("--serve-precision", default="fp32,fp64")
     ap.add_argument("--profile-precision", default="fp32")
     ap.add_argument("--pass-variant", type=int, default=-1,
                     help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..8: streaming)")
@@ -670,6 +836,8 @@ def main():
         run_tables(args)
     elif args.profile_case:
         run_profile_case(args)
+    elif args.serve_only:
+        run_serving_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

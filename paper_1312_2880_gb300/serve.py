@@ -46,10 +46,13 @@ def device_io(n: int, source: tuple):
 
 
 class Server:
+    """The serving loop. ``keep_solutions``: True copies every solution to the host (in the job's
+    result), a set of request ids only those requests' solutions."""
+
     ENOMEM = 2  # hz_status of a request whose hierarchy can never fit the budget
 
     def __init__(self, hbm_budget: int, precision: str = "fp32", tol: float = 1e-6, maxit: int = 4000,
-                 max_active: int = 32, variant: str = "hyb", keep_solutions: bool = False, backend=None,
+                 max_active: int = 32, variant: str = "hyb", keep_solutions=False, backend=None,
                  make_io=device_io):
         if backend is None:
             from . import hz as backend
@@ -141,7 +144,7 @@ class Server:
                 x, info, _ = prob.solve_finish(history_cap=0, allow_fail=True)
                 job.end = now_fn()
                 job.result = dict(info)
-                if self.keep:
+                if self.keep is True or (self.keep and job.rid in self.keep):
                     job.result["x"] = x.cpu().numpy()
                 self.done.append(job)
                 self._release(prob)
