@@ -65,10 +65,13 @@ typedef enum { HZ_SMOOTH_GS = 0, HZ_SMOOTH_KACZMARZ = 1, HZ_SMOOTH_DIRECT = 2, H
 /* Kernel forms of a Kaczmarz level (Sec. 4): one launch per colour; the whole level (sweeps,
    residual and full weighting, or correction and sweeps) in one block's shared memory; one launch
    per sweep over halo tiles; the whole level in the shared memory of a thread-block cluster of up
-   to 16 blocks (row bands, neighbour rows through distributed shared memory). All four take the
-   same row actions in the same colour order with the same fixed-rounding arithmetic, so they give
-   the same bits; they differ in launches and parallelism only. */
-typedef enum { HZ_KACZ_COLOUR = 0, HZ_KACZ_LEVEL = 1, HZ_KACZ_TILE = 2, HZ_KACZ_CLUSTER = 3 } hz_kacz_form;
+   to 16 blocks (row bands, neighbour rows through distributed shared memory); the whole level in
+   global memory by one persistent cooperative launch per pass, with bounded grid-wide barriers
+   between the colour phases (single right-hand side only; a barrier wait that runs out ends the
+   launch and the solve returns HZ_ETIMEOUT). All five take the same row actions in the same colour
+   order with the same fixed-rounding arithmetic, so they give the same bits; they differ in
+   launches and parallelism only. */
+typedef enum { HZ_KACZ_COLOUR = 0, HZ_KACZ_LEVEL = 1, HZ_KACZ_TILE = 2, HZ_KACZ_CLUSTER = 3, HZ_KACZ_GRID = 4 } hz_kacz_form;
 
 typedef struct {
   int levels;    /* number of grids; 0 = coarsen while n_l is even and larger than 8 */
@@ -277,6 +280,7 @@ typedef enum {
   HZ_K_TAIL,           /* coarse tail: every level from hz_level_info.in_tail down, in one block */
   HZ_K_KACZ_CLUSTER,   /* whole Kaczmarz level over a thread-block cluster (pre or post, as HZ_K_KACZ_LEVEL) */
   HZ_K_JACOBI,         /* one damped Jacobi sweep, out of place */
+  HZ_K_KACZ_GRID,      /* whole Kaczmarz level by one cooperative launch (pre or post, as HZ_K_KACZ_LEVEL) */
   HZ_K_COUNT
 } hz_kernel;
 

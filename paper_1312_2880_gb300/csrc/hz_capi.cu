@@ -58,7 +58,7 @@ struct Plan {
   // offsets
   std::vector<size_t> off_kh, off_u, off_f, off_u2;
   size_t off_kh64 = 0, off_vec = 0, vec_bytes = 0, off_ainv = 0, off_work = 0, off_state = 0, off_partials = 0,
-         off_hist = 0, off_status = 0;
+         off_hist = 0, off_status = 0, off_sync = 0, sync_bytes = 0;
   int nvec = 11;
   int m_coarse = 0;
   int batch = 1;
@@ -142,8 +142,11 @@ bool make_plan(int n, const hz_hierarchy_opts& o, Plan* P, std::string* err) {
   off = align256(off + (size_t)PARTIAL_SLOTS * MAX_G * 8 * B);
   P->off_hist = off;
   off = align256(off + (size_t)HIST_CAP * 8 * B);
-  P->off_status = off;
+  P->off_status = off;  // coarse-setup status, loop counter
   off = align256(off + 256);
+  P->off_sync = off;  // error word and band counters of the grid-synchronised Kaczmarz form
+  P->sync_bytes = align256(256 + (size_t)L * KGRID_MAX_BLOCKS * sizeof(unsigned int));
+  off += P->sync_bytes;
   P->total = off;
   return true;
 }
@@ -169,6 +172,7 @@ struct hz_problem {
   void* ainvT = nullptr;
   double2* work = nullptr;
   int* status_dev = nullptr;
+  unsigned int* sync_dev = nullptr;  // grid-synchronised Kaczmarz form: error word, band counters
   KrylovVecs kv{};
   double2* b_int = nullptr;  // host-buffer solve: rhs and x on the device
   double2* x_int = nullptr;
@@ -321,7 +325,29 @@ bool fused(const hz_problem* P, int l) {
 // whole level over a thread-block cluster. The finest level keeps the colour launches (its
 // right-hand side is the FP64 Krylov vector in the FP32 form).
 enum KaczPath { KACZ_COLOUR = HZ_KACZ_COLOUR, KACZ_LEVEL = HZ_KACZ_LEVEL, KACZ_TILE = HZ_KACZ_TILE,
-                KACZ_CLUSTER = HZ_KACZ_CLUSTER };
+                KACZ_CLUSTER = HZ_KACZ_CLUSTER, KACZ_GRID = HZ_KACZ_GRID };
+// Band synchronisation of the grid-synchronised Kaczmarz form on level l (the problem's sync region:
+// the error word, then KGRID_MAX_BLOCKS counters per level).
+BandSync band_sync_of(const hz_problem* P, int l) {
+  return BandSync{P->sync_dev, P->sync_dev + 64 + (size_t)l * KGRID_MAX_BLOCKS};
+}
+bool uses_grid_form(const hz_problem* P) {
+  for (int l = 0; l + 1 < P->plan.levels; ++l)
+    if (P->lv[l].smoother == HZ_SMOOTH_KACZMARZ && P->lv[l].kform == HZ_KACZ_GRID &&
+        !(P->tail_start > 0 && l >= P->tail_start))
+      return true;
+  return false;
+}
+// After a synchronised solve: HZ_ETIMEOUT (and a reset barrier) if a grid barrier wait ran out.
+hz_status grid_sync_check(hz_problem* P) {
+  if (!uses_grid_form(P)) return HZ_OK;
+  unsigned int err = 0;
+  if (cudaMemcpy(&err, P->sync_dev, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return HZ_ECUDA;
+  if (err == 0) return HZ_OK;
+  cudaMemset(P->sync_dev, 0, P->plan.sync_bytes);  // counters back in step, error cleared
+  return HZ_ETIMEOUT;
+}
+
 KaczPath kacz_path(const hz_problem* P, int l) {
   const Level& L = P->lv[l];
   if (L.smoother != HZ_SMOOTH_KACZMARZ) return KACZ_COLOUR;
@@ -335,6 +361,7 @@ bool kform_ok(const hz_problem* P, int l, int form) {
     case HZ_KACZ_LEVEL: return l > 0 && kacz_level_fits(fp32, L.n);
     case HZ_KACZ_TILE: return l > 0 && L.nu % 2 == 0;
     case HZ_KACZ_CLUSTER: return l > 0 && kacz_cluster_fits(fp32, L.n);
+    case HZ_KACZ_GRID: return l > 0 && P->plan.batch == 1 && kacz_grid_available();
   }
   return false;
 }
@@ -438,6 +465,10 @@ cudaError_t level_down(hz_problem* P, int l, Src f, const int* stop, bool all = 
   if (kp == KACZ_CLUSTER)
     return mark(P, launch_kacz_cluster_pre(fp32, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop, s, bi),
                 HZ_K_KACZ_CLUSTER, l);
+  if (kp == KACZ_GRID)
+    return mark(P, launch_kacz_grid_pre(fp32, u, pu, C.f, C.pitch, f.f, f.pf, kh, pk, L.n, bA, bB, L.nu, stop,
+                                        band_sync_of(P, l), s),
+                HZ_K_KACZ_GRID, l);
   if (kp == KACZ_TILE) {
     if ((e = kacz_tile_sweeps(P, l, f, nullptr, false, stop, bi))) return e;
     return mark(P, launch_restrict_residual(fp32, C.f, C.pitch, u, pu, f.f, f.pf, f.f64, kh, pk, L.n, bB, stop, s, bi),
@@ -524,6 +555,13 @@ cudaError_t level_up(hz_problem* P, int l, Src f, void* out, int po, const int* 
     return mark(P, launch_kacz_cluster_post(fp32, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
                                             op_beta(P, L.relax_op), L.nu, stop, P->stream, bi),
                 HZ_K_KACZ_CLUSTER, l);
+  }
+  if (kp == KACZ_GRID) {
+    int pk;
+    const void* kh = kh_of(P, l, &pk);
+    return mark(P, launch_kacz_grid_post(fp32, L.u, L.pitch, ec, C.pitch, f.f, f.pf, kh, pk, L.n,
+                                         op_beta(P, L.relax_op), L.nu, stop, band_sync_of(P, l), P->stream),
+                HZ_K_KACZ_GRID, l);
   }
   if ((e = mark(P, launch_prolong_add(fp32, L.u, L.pitch, ec, C.pitch, L.n, stop, P->stream, bi), HZ_K_PROLONG, l))) return e;
   if (kp == KACZ_TILE) {
@@ -851,6 +889,9 @@ hz_status solve_end(hz_problem* P, double* history, int history_cap, hz_solve_in
     }
   }
   const hz_status res = B == 1 ? st : worst;
+  const hz_status gsc = grid_sync_check(P);
+  if (gsc == HZ_ETIMEOUT) return fail(P, gsc, "a grid-wide barrier wait of a Kaczmarz level ran out");
+  if (gsc != HZ_OK) return fail(P, gsc, "reading the grid barrier state failed");
   if (res == HZ_EBREAKDOWN) return fail(P, res, "Bi-CGSTAB breakdown");
   if (res == HZ_ENONFINITE) return fail(P, res, "non-finite value in the Krylov scalars");
   if (res == HZ_EMAXIT) return fail(P, res, "maximum iterations reached");
@@ -938,7 +979,7 @@ bool opts_ok(const hz_hierarchy_opts& o) {
   return !(o.variant < 0 || o.variant > 3 || (o.precision != 0 && o.precision != 1) || o.nu_gs < 1 || o.nu_gs > 8 ||
            o.nu_kacz < 1 || o.nu_kacz > 16 || o.k_ref < 0 || o.batch < 1 || o.batch > 1024 ||
            o.pass_variant < -1 || o.pass_variant >= FUSED_VARIANTS || o.coarse_tail < 0 || o.coarse_tail > 1 ||
-           o.kacz_form < -1 || o.kacz_form > HZ_KACZ_CLUSTER ||
+           o.kacz_form < -1 || o.kacz_form > HZ_KACZ_GRID ||
            (o.gs_smoother != HZ_SMOOTH_GS && o.gs_smoother != HZ_SMOOTH_JACOBI && o.gs_smoother != HZ_SMOOTH_SOR) ||
            !(o.omega >= 0.0 && o.omega < 2.0) || (o.kacz_rule != HZ_KACZ_RULE_BAND && o.kacz_rule != HZ_KACZ_RULE_BINS));
 }
@@ -1271,6 +1312,8 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   P->ainvT = A + pl.off_ainv;
   P->work = (double2*)(A + pl.off_work);
   P->status_dev = (int*)(A + pl.off_status);
+  P->sync_dev = (unsigned int*)(A + pl.off_sync);
+  CK(cudaMemsetAsync(P->sync_dev, 0, pl.sync_bytes, s));
   CK(launch_coarse_setup(fp32, P->ainvT, P->work, C.kh, C.pk, C.n, op_beta(P, C.relax_op), P->status_dev, s));
   int status = 1;
   CK(cudaMemcpyAsync(&status, P->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1762,7 +1805,7 @@ const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s",
                                 "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
-                                "kacz_sweep", "coarse_tail", "kacz_cluster", "jacobi"};
+                                "kacz_sweep", "coarse_tail", "kacz_cluster", "jacobi", "kacz_grid"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

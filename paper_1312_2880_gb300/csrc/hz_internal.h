@@ -105,6 +105,24 @@ cudaError_t launch_kacz_cluster_pre(bool fp32, void* u, int pu, void* fc, int pc
 cudaError_t launch_kacz_cluster_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
                                      const void* kh, int pk, int n, double bA, int nu, const int* stop, cudaStream_t s,
                                      const Inst& bi = Inst());
+// Whole level in global memory by one persistent cooperative launch per pass (hz_kgrid.cu); one
+// instance (batch 1). Each block owns a band of grid rows and publishes its progress (phases
+// done) in its counter; before a phase it waits, with a bounded number of polls, for the two
+// neighbouring bands to have finished the previous one. The counters are zero at setup and all
+// advance by the same amount in every launch of a level; err (shared by the levels) is set when a
+// wait runs out and stays set until the host resets the region.
+constexpr int KGRID_MAX_BLOCKS = 2048;
+struct BandSync {
+  unsigned int* err;
+  unsigned int* ctr;  // KGRID_MAX_BLOCKS counters of one level
+};
+bool kacz_grid_available();  // cooperative launches supported, and capturable into a CUDA graph
+cudaError_t launch_kacz_grid_pre(bool fp32, void* u, int pu, void* fc, int pc, const void* f, int pf, const void* kh,
+                                 int pk, int n, double bA, double bB, int nu, const int* stop, BandSync bs,
+                                 cudaStream_t s);
+cudaError_t launch_kacz_grid_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
+                                  const void* kh, int pk, int n, double bA, int nu, const int* stop, BandSync bs,
+                                  cudaStream_t s);
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
                                    bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
                                    cudaStream_t s, const Inst& bi = Inst());

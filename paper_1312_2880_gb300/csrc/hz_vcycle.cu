@@ -10,6 +10,7 @@
 
 #include "hz_common.cuh"
 #include "hz_internal.h"
+#include "hz_gnode.cuh"
 #include "hz_level.cuh"
 
 namespace hz {
@@ -121,13 +122,7 @@ __global__ void kacz_colour_kernel(c2<T>* __restrict__ u, int pu, const F2* __re
   if (j > n) return;
   int i = ((colour - 2 * j) % 5 + 5) % 5 + 5 * m;
   if (i > n) return;
-  const Nbr b = neighbours(i, j, n);
-  c2<T> d;
-  T inv;
-  lvl::row_consts<T>(kh[(long long)j * pk + i], i, j, n, beta, &d, &inv);
-  c2<T>* row = u + (long long)j * pu;
-  lvl::act_nodes<T>(row + i, row + b.iw, row + b.ie, u + (long long)b.js * pu + i, u + (long long)b.jn * pu + i,
-                    ldc<T>(f, (long long)j * pf + i), d, inv);
+  gnode::kacz_row<T, F2>(u, pu, f, pf, kh, pk, n, i, j, beta);
 }
 
 // ---------------------------------------------------------------- transfers (Sec. 5)
@@ -148,24 +143,7 @@ __global__ void restrict_residual_kernel(c2<T>* __restrict__ fc, int pc, const c
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   int nc = n / 2;
   if (I > nc || J > nc) return;
-  // the same operations and order as the whole-level forms (lvl::residual, xr::fw_node)
-  c2<T> rows[3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int j = reflect(2 * J + b - 1, n);
-    c2<T> r[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int i = reflect(2 * I + a - 1, n);
-      const Nbr nb = neighbours(i, j, n);
-      const c2<T>* row = u + (long long)j * pu;
-      r[a] = xr::resid<T>(ldc<T>(f, (long long)j * pf + i), row[i],
-                          xr::nb4<T>(row[nb.iw], row[nb.ie], u[(long long)nb.js * pu + i], u[(long long)nb.jn * pu + i]),
-                          xr::diag<T>(kh[(long long)j * pk + i], lvl::sides_at(i, j, n), beta));
-    }
-    rows[b] = xr::fw3<T>(r[0], r[1], r[2]);
-  }
-  fc[(long long)J * pc + I] = xr::cscale<T>(xr::fw3<T>(rows[0], rows[1], rows[2]), (T)0.25);
+  fc[(long long)J * pc + I] = gnode::restrict_node<T, F2>(u, pu, f, pf, kh, pk, n, beta, I, J);
 }
 
 // u += P e_c, bilinear interpolation from the (n/2+1)^2 grid.
@@ -179,9 +157,7 @@ __global__ void prolong_add_kernel(c2<T>* __restrict__ u, int pu, const c2<T>* _
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
-  const c2<T>* e0 = ec + (long long)(j >> 1) * pc;
-  const long long p = (long long)j * pu + i;
-  u[p] = xr::cadd<T>(u[p], xr::bilinear<T>(e0, e0 + pc, i >> 1, i & 1, j & 1));
+  gnode::prolong_add_node<T>(u, pu, ec, pc, i, j);
 }
 
 // ---------------------------------------------------------------- coarsest grid

@@ -137,7 +137,7 @@ def _ptr(t) -> c_void_p:
     return c_void_p(t.data_ptr())
 
 
-KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3}
+KACZ_FORMS = {"auto": -1, "colour": 0, "level": 1, "tile": 2, "cluster": 3, "grid": 4}
 KACZ_RULES = {"band": 0, "bins": 1}
 
 

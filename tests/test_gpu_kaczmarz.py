@@ -1,7 +1,8 @@
-"""Kernel forms of a Kaczmarz level (Sec. 4): colour launches, one block, halo tiles, and the
-whole level over a thread-block cluster.
+"""Kernel forms of a Kaczmarz level (Sec. 4): colour launches, one block, halo tiles, the whole
+level over a thread-block cluster, and the whole level in global memory by one cooperative launch
+with grid-wide barriers.
 
-All four forms take the same fixed-rounding row actions in the same colour order, so V-cycles run
+All five forms take the same fixed-rounding row actions in the same colour order, so V-cycles run
 with any of them give the same bits, in FP32 and in FP64. The FP64 cluster form is also checked
 against the oracle per level step (1e-12) and per V-cycle (1e-11). Kaczmarz levels of
 n = 48 (49 rows: ragged bands), 64, 128 and 256, the coarse tail off so that the level runs in
@@ -86,10 +87,10 @@ def test_kaczmarz_forms_give_the_same_bits(name, precision):
     out = {}
     # the FP64 cluster form holds levels up to n = 128 (56 bytes a node in 16 x 200 KB)
     cluster_fits = precision == "fp32" or nk <= 128
-    for form in ("colour", "level", "tile", "cluster"):
+    for form in ("colour", "level", "tile", "cluster", "grid"):
         z, s = vcycle(wl, precision, form, r)
         got = s[kacz_level(s, nk)]["kacz_form"]
-        if form == "colour" or (form == "cluster" and cluster_fits):
+        if form in ("colour", "grid") or (form == "cluster" and cluster_fits):
             assert got == form, s
         out[got] = z
     assert len(out) >= (2 if cluster_fits else 1), out.keys()
@@ -132,7 +133,7 @@ def test_fp64_cluster_vcycle_matches_the_oracle(name):
     r = rand_c((wl.n + 1) ** 2, 78)
     H = o.build_hierarchy(wl.n, wl.kfield, wl.k_ref, wl.variant, wl.levels)
     ref = o.vcycle(H, r.ravel())
-    for form in ("cluster", "colour"):
+    for form in ("cluster", "colour", "grid"):
         z, s = vcycle(wl, "fp64", form, r)
         assert s[kacz_level(s, nk)]["kacz_form"] == form
         err = np.abs(z.ravel() - ref).max() / np.abs(ref).max()
