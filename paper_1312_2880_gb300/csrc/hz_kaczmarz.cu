@@ -179,14 +179,24 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
   T* sk = reinterpret_cast<T*>(sf + KR * KR);
   const int x0 = blockIdx.x * KT, y0 = blockIdx.y * KT;
   const int gx = x0 - KH, gy = y0 - KH;
+  // the tile region's u, f~ and k H in flight at once (cp.async, one wait): a plain load per node
+  // would put one L2 latency per node a thread copies on the launch's critical path
+  constexpr bool async_f = sizeof(F2) == sizeof(c2<T>);  // f~ in the level's own precision
   for (int q = threadIdx.x; q < KR * KR; q += TB) {
     int r = q / KR, c = q - r * KR, i = gx + c, j = gy + r;
     if ((unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n) {
-      su[q] = uin ? uin[(long long)j * pu + i] : mk<T>(0, 0);
-      sf[q] = ldc<T>(f, (long long)j * pf + i);
-      sk[q] = kh[(long long)j * pk + i];
+      if (uin)
+        lvl::cp_async<sizeof(c2<T>)>(su + q, uin + (long long)j * pu + i);
+      else
+        su[q] = mk<T>(0, 0);
+      if constexpr (async_f)
+        lvl::cp_async<sizeof(c2<T>)>(sf + q, f + (long long)j * pf + i);
+      else
+        sf[q] = ldc<T>(f, (long long)j * pf + i);
+      lvl::cp_async<sizeof(T)>(sk + q, kh + (long long)j * pk + i);
     }
   }
+  lvl::cp_async_wait_all();
   __syncthreads();
   constexpr int PER_ROW = (KR + 4) / 5;
   if (gx >= 1 && gy >= 1 && gx + KR <= n && gy + KR <= n) {
