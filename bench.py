@@ -632,7 +632,8 @@ def headline_line(args, wl, results, replica, e2e_ms, roof, per32, per64, hbm_pe
         "batched": batched,
         "serving": serving,
         "roofline": roof,
-        "fp64_peak": {"tflops": round(fp64_peak["tflops"], 4), "probe_ms": round(fp64_peak["ms"], 3)},
+        "fp64_peak": {"tflops": round(fp64_peak["tflops"], 4), "probe_ms": round(fp64_peak["ms"], 3),
+                      "fmas_per_chain": fp64_peak["iters"]},
         "sweep_hbm": {"workload": wl.name, "kernels": sweep_rates(per32, True, hbm_peak, wl.n),
                       "iteration_ms_profiled": round(sum(sum(v) for v in per32.values()) / 2, 3)},
         "kernel_share": shares(per32),
