@@ -2,7 +2,8 @@
 time (hosts whose own pool owns the device; latency-critical loops where cudaMalloc may
 synchronise): its v = A u and <w, v> must equal hz_apply's result and the dot product of that
 result, within the per-step tolerance of the other GPU tests (1e-12), on two calls in a row
-(the second call reuses the shared scratch the first one left behind)."""
+(the second call reuses the shared scratch the first one left behind); hz_apply is itself checked
+against the oracle's operator at the same tolerance."""
 from ctypes import c_void_p
 
 import numpy as np
@@ -31,9 +32,14 @@ def test_noalloc_apply_dot_matches_apply_twice(n):
     w = torch.from_numpy(g.standard_normal((n + 1, n + 1)) + 1j * g.standard_normal((n + 1, n + 1))).cuda()
     kh = torch.from_numpy(np.ascontiguousarray(kf * (1.0 / n))).cuda()
     stream = c_void_p(torch.cuda.current_stream().cuda_stream)
+    import oracle as o
+
     for beta, op in ((0.0, "L"), (0.5, "M")):
         ref_v = P.apply(u, op).cpu().numpy()
         ref_dot = np.vdot(w.cpu().numpy().ravel(), ref_v.ravel())
+        # hz_apply itself against the oracle's operator (the per-step bound of the other tests)
+        oracle_v = (o.helmholtz_matrix(n, kf, beta) @ u.cpu().numpy().ravel()).reshape(n + 1, n + 1)
+        assert _rel(ref_v, oracle_v) <= 1e-12
         for _ in range(2):
             v = torch.full_like(u, complex("nan"))
             dot = torch.full((1,), complex("nan"), dtype=torch.complex128, device="cuda")
