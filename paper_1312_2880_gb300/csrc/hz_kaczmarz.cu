@@ -9,9 +9,9 @@
 //   diagonal and 1/|a_p|^2 computed once per launch (operations in hz_level.cuh). Pre mode: zero guess, nu sweeps (colours
 //   0..4), then the residual with the (B) operator and full weighting onto the coarse level. Post
 //   mode: u_pre + P e_c, then nu sweeps (colours 4..0).
-// kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a 10-node halo:
-//   a colour phase moves information two nodes (a row reads and writes its neighbours), so after
-//   five phases the tile interior holds exactly the sequential sweep's values. Out of place.
+// kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a halo that holds
+//   the dependency cone of one sweep (6 columns each side, 6 and 10 rows), so the tile interior
+//   holds exactly the sequential sweep's values. Out of place.
 // kacz_cluster_*: the kacz_level_* operations with the level split into row bands over a
 //   thread-block cluster of up to 16 blocks (distributed shared memory, one cluster barrier per
 //   colour), for levels too large for one block or, in FP64, too slow on one SM's FP64 pipe.
@@ -31,9 +31,17 @@ namespace {
 
 constexpr int LB = 1024;  // threads of the whole-level kernel
 constexpr int TB = 256;   // threads of the tile kernel
-constexpr int KT = 32;    // tile edge
-constexpr int KH = 10;    // halo: 2 nodes per colour phase
-constexpr int KR = KT + 2 * KH;
+// Tile of the one-sweep-per-launch form: KT x KT outputs. The halo is the dependency cone of one
+// five-colour sweep (found by propagating dependencies through the colour phases on an unbounded
+// grid, every residue of the colour pattern): an output after a sweep in the order 0..4 depends on
+// starting values at most 6 columns to either side, 6 rows below and 10 rows above; in the order
+// 4..0 the rows swap (10 below, 6 above).
+constexpr int KT = 32;                    // tile edge
+constexpr int KHX = 6;                    // halo columns on each side
+constexpr int KHN = 6, KHF = 10;          // halo rows on the near and the far side of the sweep order
+constexpr int KRX = KT + 2 * KHX;         // region width
+constexpr int KRY = KT + KHN + KHF;       // region height
+constexpr int KREG = KRX * KRY;
 
 // Row action on row (i, j) of a level whose values sit in shared arrays of row pitch w with
 // origin (gx, gy): the row constants come from k H as in the whole-level forms, and the action is
@@ -175,15 +183,17 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   c2<T>* su = reinterpret_cast<c2<T>*>(smem);
-  c2<T>* sf = su + KR * KR;
-  T* sk = reinterpret_cast<T*>(sf + KR * KR);
+  c2<T>* sf = su + KREG;
+  T* sk = reinterpret_cast<T*>(sf + KREG);
   const int x0 = blockIdx.x * KT, y0 = blockIdx.y * KT;
-  const int gx = x0 - KH, gy = y0 - KH;
+  // order 0..4 (pre): 6 halo rows below the tile, 10 above; order 4..0 (post): 10 below, 6 above
+  const int below = post ? KHF : KHN;
+  const int gx = x0 - KHX, gy = y0 - below;
   // the tile region's u, f~ and k H in flight at once (cp.async, one wait): a plain load per node
   // would put one L2 latency per node a thread copies on the launch's critical path
   constexpr bool async_f = sizeof(F2) == sizeof(c2<T>);  // f~ in the level's own precision
-  for (int q = threadIdx.x; q < KR * KR; q += TB) {
-    int r = q / KR, c = q - r * KR, i = gx + c, j = gy + r;
+  for (int q = threadIdx.x; q < KREG; q += TB) {
+    int r = q / KRX, c = q - r * KRX, i = gx + c, j = gy + r;
     if ((unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n) {
       if (uin)
         lvl::cp_async<sizeof(c2<T>)>(su + q, uin + (long long)j * pu + i);
@@ -198,41 +208,42 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
   }
   lvl::cp_async_wait_all();
   __syncthreads();
-  constexpr int PER_ROW = (KR + 4) / 5;
-  if (gx >= 1 && gy >= 1 && gx + KR <= n && gy + KR <= n) {
+  constexpr int PER_ROW = (KRX + 4) / 5;
+  if (gx >= 1 && gy >= 1 && gx + KRX <= n && gy + KRY <= n) {
     // region strictly inside the square: no mirrors, no boundary terms
-    __shared__ int c0tab[KR];
+    __shared__ int c0tab[KRY];
     for (int ph = 0; ph < 5; ++ph) {
       const int colour = post ? 4 - ph : ph;
-      if (threadIdx.x < KR) c0tab[threadIdx.x] = mod5(colour - 2 * (gy + (int)threadIdx.x) - gx);
+      if (threadIdx.x < KRY) c0tab[threadIdx.x] = mod5(colour - 2 * (gy + (int)threadIdx.x) - gx);
       __syncthreads();
-      for (int q = threadIdx.x; q < KR * PER_ROW; q += TB) {
+      for (int q = threadIdx.x; q < KRY * PER_ROW; q += TB) {
         const int r = q / PER_ROW, m = q - r * PER_ROW;
         const int c = c0tab[r] + 5 * m;
-        if (r < 1 || r > KR - 2 || c < 1 || c > KR - 2) continue;
-        row_action_inner<T>(su, sf, sk, KR, r * KR + c, bA);
+        if (r < 1 || r > KRY - 2 || c < 1 || c > KRX - 2) continue;
+        row_action_inner<T>(su, sf, sk, KRX, r * KRX + c, bA);
       }
       __syncthreads();
     }
   } else
   for (int ph = 0; ph < 5; ++ph) {
     const int colour = post ? 4 - ph : ph;
-    for (int q = threadIdx.x; q < KR * PER_ROW; q += TB) {
+    for (int q = threadIdx.x; q < KRY * PER_ROW; q += TB) {
       int r = q / PER_ROW, m = q - r * PER_ROW;
       int j = gy + r;
       int c = ((colour - 2 * j - gx) % 5 + 5) % 5 + 5 * m;
       int i = gx + c;
-      if (c >= KR || (unsigned)i > (unsigned)n || (unsigned)j > (unsigned)n) continue;
+      if (c >= KRX || (unsigned)i > (unsigned)n || (unsigned)j > (unsigned)n) continue;
       // the row's whole support (mirror neighbours included) must lie in the tile region
       Nbr b = neighbours(i, j, n);
-      if (b.iw < gx || b.ie >= gx + KR || b.js < gy || b.jn >= gy + KR) continue;
-      row_action<T>(su, sf, sk, KR, gx, gy, i, j, n, bA);
+      if (b.iw < gx || b.ie >= gx + KRX || b.js < gy || b.jn >= gy + KRY) continue;
+      row_action<T>(su, sf, sk, KRX, gx, gy, i, j, n, bA);
     }
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < KR * KR; q += TB) {
-    int r = q / KR, c = q - r * KR, i = gx + c, j = gy + r;
-    if (r >= KH && r < KH + KT && c >= KH && c < KH + KT && (unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n)
+  for (int q = threadIdx.x; q < KREG; q += TB) {
+    int r = q / KRX, c = q - r * KRX, i = gx + c, j = gy + r;
+    if (r >= below && r < below + KT && c >= KHX && c < KHX + KT && (unsigned)i <= (unsigned)n &&
+        (unsigned)j <= (unsigned)n)
       uout[(long long)j * po + i] = su[q];
   }
 }
@@ -494,7 +505,7 @@ cudaError_t tile_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(KR * KR * (2 * sizeof(c2<T>) + sizeof(T))));
+                                       (int)(KREG * (2 * sizeof(c2<T>) + sizeof(T))));
   if (!e) done = true;
   return e;
 }
@@ -504,7 +515,7 @@ cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* ui
                                    cudaStream_t s, const Inst& bi) {
   dim3 grid((n + KT) / KT, (n + KT) / KT, bi.count);
   cudaError_t e;
-  const size_t sm64 = KR * KR * (2 * sizeof(double2) + sizeof(double)), sm32 = KR * KR * (2 * sizeof(float2) + sizeof(float));
+  const size_t sm64 = KREG * (2 * sizeof(double2) + sizeof(double)), sm32 = KREG * (2 * sizeof(float2) + sizeof(float));
   if (!fp32) {
     if ((e = tile_attr<double, double2>())) return e;
   } else if (f64_src) {
