@@ -388,18 +388,20 @@ void plan_kaczmarz(hz_problem* P) {
   }
 }
 
-// Tiled sweeps on level l: `first_in` is the input of the first sweep (null = zero guess).
+// Tiled sweeps on level l: `first_in` is the input of the first sweep (null = zero guess). One or
+// two sweeps per launch, ping-pong between u and u2 ending in u.
 cudaError_t kacz_tile_sweeps(hz_problem* P, int l, Src f, const void* first_in, bool post, const int* stop,
                              const Inst& bi) {
   const Level& L = P->lv[l];
   int pk;
   const void* kh = kh_of(P, l, &pk);
   const void* in = first_in;
+  const int per = kacz_tile_sweeps_per_launch(P->plan.fp32, L.n, L.nu), launches = L.nu / per;
   cudaError_t e;
-  for (int k = 0; k < L.nu; ++k) {
-    void* out = ((L.nu - 1 - k) % 2 == 0) ? L.u : L.u2;
+  for (int k = 0; k < launches; ++k) {
+    void* out = ((launches - 1 - k) % 2 == 0) ? L.u : L.u2;
     if ((e = mark(P, launch_kacz_sweep_tile(P->plan.fp32, out, L.pitch, in, L.pitch, f.f, f.pf, f.f64, kh, pk, L.n,
-                                            op_beta(P, L.relax_op), post, stop, P->stream, bi),
+                                            op_beta(P, L.relax_op), post, per, stop, P->stream, bi),
                   HZ_K_KACZ_SWEEP, l)))
       return e;
     in = out;

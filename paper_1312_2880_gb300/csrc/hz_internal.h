@@ -123,9 +123,11 @@ cudaError_t launch_kacz_grid_pre(bool fp32, void* u, int pu, void* fc, int pc, c
 cudaError_t launch_kacz_grid_post(bool fp32, void* u, int pu, const void* ec, int pc, const void* f, int pf,
                                   const void* kh, int pk, int n, double bA, int nu, const int* stop, BandSync bs,
                                   cudaStream_t s);
+// `sweeps` (1 or 2, from kacz_tile_sweeps_per_launch) Kaczmarz sweeps per launch over halo tiles.
+int kacz_tile_sweeps_per_launch(bool fp32, int n, int nu);
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
-                                   bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
-                                   cudaStream_t s, const Inst& bi = Inst());
+                                   bool f64_src, const void* kh, int pk, int n, double bA, bool post, int sweeps,
+                                   const int* stop, cudaStream_t s, const Inst& bi = Inst());
 // Coarse tail (hz_tail.cu): levels lt .. L-1 of the V-cycle in one block's shared memory.
 constexpr int TAIL_MAX_LEVELS = 12;
 constexpr int TAIL_MAX_SMEM = 200 * 1024;

@@ -30,18 +30,22 @@ namespace hz {
 namespace {
 
 constexpr int LB = 1024;  // threads of the whole-level kernel
-constexpr int TB = 256;   // threads of the tile kernel
-// Tile of the one-sweep-per-launch form: KT x KT outputs. The halo is the dependency cone of one
-// five-colour sweep (found by propagating dependencies through the colour phases on an unbounded
-// grid, every residue of the colour pattern): an output after a sweep in the order 0..4 depends on
-// starting values at most 6 columns to either side, 6 rows below and 10 rows above; in the order
-// 4..0 the rows swap (10 below, 6 above).
-constexpr int KT = 32;                    // tile edge
-constexpr int KHX = 6;                    // halo columns on each side
-constexpr int KHN = 6, KHF = 10;          // halo rows on the near and the far side of the sweep order
-constexpr int KRX = KT + 2 * KHX;         // region width
-constexpr int KRY = KT + KHN + KHF;       // region height
-constexpr int KREG = KRX * KRY;
+// Tiles of the tiled form: KT x KT outputs per block after S sweeps per launch. The halo is the
+// dependency cone of S five-colour sweeps (found by propagating dependencies through the colour
+// phases on an unbounded grid, every residue of the colour pattern): after one sweep in the order
+// 0..4 an output depends on starting values at most 6 columns to either side, 6 rows below and 10
+// rows above; in the order 4..0 the rows swap (10 below, 6 above); S sweeps add up the extents.
+template <int KT_, int S_, int TB_>
+struct TileGeo {
+  static constexpr int KT = KT_, S = S_, TBK = TB_;
+  static constexpr int HX = 6 * S_;             // halo columns on each side
+  static constexpr int HN = 6 * S_, HF = 10 * S_;  // halo rows on the near and the far side
+  static constexpr int RX = KT_ + 2 * HX, RY = KT_ + HN + HF, REG = RX * RY;
+};
+using TileOne = TileGeo<32, 1, 256>;   // one sweep per launch: 44 x 48 regions
+using TileTwo = TileGeo<64, 2, 1024>;  // two sweeps per launch: 88 x 96 regions (FP32, large levels)
+template <class T, class G>
+constexpr size_t tile_smem() { return (size_t)G::REG * (2 * sizeof(c2<T>) + sizeof(T)); }
 
 // Row action on row (i, j) of a level whose values sit in shared arrays of row pitch w with
 // origin (gx, gy): the row constants come from k H as in the whole-level forms, and the action is
@@ -170,12 +174,13 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
 }
 
-template <class T, class F2>
-__global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__ uout, int po,
-                                                              const c2<T>* __restrict__ uin, int pu,
-                                                              const F2* __restrict__ f, int pf,
-                                                              const T* __restrict__ kh, int pk, int n, T bA, int post,
-                                                              const int* __restrict__ stop, Inst bi) {
+template <class T, class F2, class G>
+__global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restrict__ uout, int po,
+                                                                  const c2<T>* __restrict__ uin, int pu,
+                                                                  const F2* __restrict__ f, int pf,
+                                                                  const T* __restrict__ kh, int pk, int n, T bA,
+                                                                  int post, const int* __restrict__ stop, Inst bi) {
+  constexpr int TBK = G::TBK, RX = G::RX, RY = G::RY, REG = G::REG, KT = G::KT;
   pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
   uout += blockIdx.z * bi.su;
@@ -183,17 +188,17 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
   f += blockIdx.z * bi.sf;
   extern __shared__ __align__(16) unsigned char smem[];
   c2<T>* su = reinterpret_cast<c2<T>*>(smem);
-  c2<T>* sf = su + KREG;
-  T* sk = reinterpret_cast<T*>(sf + KREG);
+  c2<T>* sf = su + REG;
+  T* sk = reinterpret_cast<T*>(sf + REG);
   const int x0 = blockIdx.x * KT, y0 = blockIdx.y * KT;
-  // order 0..4 (pre): 6 halo rows below the tile, 10 above; order 4..0 (post): 10 below, 6 above
-  const int below = post ? KHF : KHN;
-  const int gx = x0 - KHX, gy = y0 - below;
+  // sweeps in the order 0..4 (pre) need the near halo below the tile, 4..0 (post) above it
+  const int below = post ? G::HF : G::HN;
+  const int gx = x0 - G::HX, gy = y0 - below;
   // the tile region's u, f~ and k H in flight at once (cp.async, one wait): a plain load per node
   // would put one L2 latency per node a thread copies on the launch's critical path
   constexpr bool async_f = sizeof(F2) == sizeof(c2<T>);  // f~ in the level's own precision
-  for (int q = threadIdx.x; q < KREG; q += TB) {
-    int r = q / KRX, c = q - r * KRX, i = gx + c, j = gy + r;
+  for (int q = threadIdx.x; q < REG; q += TBK) {
+    int r = q / RX, c = q - r * RX, i = gx + c, j = gy + r;
     if ((unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n) {
       if (uin)
         lvl::cp_async<sizeof(c2<T>)>(su + q, uin + (long long)j * pu + i);
@@ -208,41 +213,41 @@ __global__ void __launch_bounds__(TB) kacz_sweep_tile_kernel(c2<T>* __restrict__
   }
   lvl::cp_async_wait_all();
   __syncthreads();
-  constexpr int PER_ROW = (KRX + 4) / 5;
-  if (gx >= 1 && gy >= 1 && gx + KRX <= n && gy + KRY <= n) {
+  constexpr int PER_ROW = (RX + 4) / 5;
+  if (gx >= 1 && gy >= 1 && gx + RX <= n && gy + RY <= n) {
     // region strictly inside the square: no mirrors, no boundary terms
-    __shared__ int c0tab[KRY];
-    for (int ph = 0; ph < 5; ++ph) {
-      const int colour = post ? 4 - ph : ph;
-      if (threadIdx.x < KRY) c0tab[threadIdx.x] = mod5(colour - 2 * (gy + (int)threadIdx.x) - gx);
+    __shared__ int c0tab[RY];
+    for (int ph = 0; ph < 5 * G::S; ++ph) {
+      const int colour = post ? 4 - ph % 5 : ph % 5;
+      if (threadIdx.x < RY) c0tab[threadIdx.x] = mod5(colour - 2 * (gy + (int)threadIdx.x) - gx);
       __syncthreads();
-      for (int q = threadIdx.x; q < KRY * PER_ROW; q += TB) {
+      for (int q = threadIdx.x; q < RY * PER_ROW; q += TBK) {
         const int r = q / PER_ROW, m = q - r * PER_ROW;
         const int c = c0tab[r] + 5 * m;
-        if (r < 1 || r > KRY - 2 || c < 1 || c > KRX - 2) continue;
-        row_action_inner<T>(su, sf, sk, KRX, r * KRX + c, bA);
+        if (r < 1 || r > RY - 2 || c < 1 || c > RX - 2) continue;
+        row_action_inner<T>(su, sf, sk, RX, r * RX + c, bA);
       }
       __syncthreads();
     }
   } else
-  for (int ph = 0; ph < 5; ++ph) {
-    const int colour = post ? 4 - ph : ph;
-    for (int q = threadIdx.x; q < KRY * PER_ROW; q += TB) {
+  for (int ph = 0; ph < 5 * G::S; ++ph) {
+    const int colour = post ? 4 - ph % 5 : ph % 5;
+    for (int q = threadIdx.x; q < RY * PER_ROW; q += TBK) {
       int r = q / PER_ROW, m = q - r * PER_ROW;
       int j = gy + r;
       int c = ((colour - 2 * j - gx) % 5 + 5) % 5 + 5 * m;
       int i = gx + c;
-      if (c >= KRX || (unsigned)i > (unsigned)n || (unsigned)j > (unsigned)n) continue;
+      if (c >= RX || (unsigned)i > (unsigned)n || (unsigned)j > (unsigned)n) continue;
       // the row's whole support (mirror neighbours included) must lie in the tile region
       Nbr b = neighbours(i, j, n);
-      if (b.iw < gx || b.ie >= gx + KRX || b.js < gy || b.jn >= gy + KRY) continue;
-      row_action<T>(su, sf, sk, KRX, gx, gy, i, j, n, bA);
+      if (b.iw < gx || b.ie >= gx + RX || b.js < gy || b.jn >= gy + RY) continue;
+      row_action<T>(su, sf, sk, RX, gx, gy, i, j, n, bA);
     }
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < KREG; q += TB) {
-    int r = q / KRX, c = q - r * KRX, i = gx + c, j = gy + r;
-    if (r >= below && r < below + KT && c >= KHX && c < KHX + KT && (unsigned)i <= (unsigned)n &&
+  for (int q = threadIdx.x; q < REG; q += TBK) {
+    int r = q / RX, c = q - r * RX, i = gx + c, j = gy + r;
+    if (r >= below && r < below + KT && c >= G::HX && c < G::HX + KT && (unsigned)i <= (unsigned)n &&
         (unsigned)j <= (unsigned)n)
       uout[(long long)j * po + i] = su[q];
   }
@@ -500,42 +505,46 @@ cudaError_t launch_cluster_kernel(void (*kernel)(Args...), int c, size_t smem, c
 
 }  // namespace
 
-template <class T, class F2>
+template <class T, class F2, class G>
 cudaError_t tile_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(KREG * (2 * sizeof(c2<T>) + sizeof(T))));
+  cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tile_smem<T, G>());
   if (!e) done = true;
   return e;
 }
 
-cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
-                                   bool f64_src, const void* kh, int pk, int n, double bA, bool post, const int* stop,
-                                   cudaStream_t s, const Inst& bi) {
-  dim3 grid((n + KT) / KT, (n + KT) / KT, bi.count);
-  cudaError_t e;
-  const size_t sm64 = KREG * (2 * sizeof(double2) + sizeof(double)), sm32 = KREG * (2 * sizeof(float2) + sizeof(float));
-  if (!fp32) {
-    if ((e = tile_attr<double, double2>())) return e;
-  } else if (f64_src) {
-    if ((e = tile_attr<float, double2>())) return e;
-  } else if ((e = tile_attr<float, float2>())) {
-    return e;
-  }
-  if (!fp32)
-    pdl_launch(kacz_sweep_tile_kernel<double, double2>, grid, TB, sm64, s, (double2*)uout, po, (const double2*)uin, pu,
-                                                                (const double2*)f, pf, (const double*)kh, pk, n, bA,
-                                                                post, stop, bi);
-  else if (f64_src)
-    pdl_launch(kacz_sweep_tile_kernel<float, double2>, grid, TB, sm32, s, (float2*)uout, po, (const float2*)uin, pu,
-                                                               (const double2*)f, pf, (const float*)kh, pk, n,
-                                                               (float)bA, post, stop, bi);
-  else
-    pdl_launch(kacz_sweep_tile_kernel<float, float2>, grid, TB, sm32, s, (float2*)uout, po, (const float2*)uin, pu,
-                                                              (const float2*)f, pf, (const float*)kh, pk, n, (float)bA,
-                                                              post, stop, bi);
+template <class T, class F2, class G>
+cudaError_t tile_launch(void* uout, int po, const void* uin, int pu, const void* f, int pf, const void* kh, int pk,
+                        int n, double bA, bool post, const int* stop, cudaStream_t s, const Inst& bi) {
+  cudaError_t e = tile_attr<T, F2, G>();
+  if (e) return e;
+  dim3 grid((n + G::KT) / G::KT, (n + G::KT) / G::KT, bi.count);
+  pdl_launch(kacz_sweep_tile_kernel<T, F2, G>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
+             (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, (int)post, stop, bi);
   return cudaGetLastError();
+}
+
+int kacz_tile_sweeps_per_launch(bool fp32, int n, int nu) {
+  // two sweeps per launch on FP32 levels of at least 1024 intervals: 64-node tiles with the
+  // two-sweep halo read 1.03 region nodes per output and sweep, against 2.06 for one sweep on
+  // 32-node tiles; smaller levels keep one sweep (too few 64-node tiles to fill the GPU). The
+  // launches ping-pong between two arrays and must end in u from an input in u, so their number
+  // has to be even: nu a multiple of 4.
+  return (fp32 && n >= 1024 && nu % 4 == 0) ? 2 : 1;
+}
+
+cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
+                                   bool f64_src, const void* kh, int pk, int n, double bA, bool post, int sweeps,
+                                   const int* stop, cudaStream_t s, const Inst& bi) {
+  if (!fp32)
+    return tile_launch<double, double2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
+  if (f64_src)
+    return sweeps == 2 ? tile_launch<float, double2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
+                       : tile_launch<float, double2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
+  return sweeps == 2 ? tile_launch<float, float2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
+                     : tile_launch<float, float2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
 }
 
 namespace {

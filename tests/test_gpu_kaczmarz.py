@@ -5,8 +5,9 @@ with grid-wide barriers.
 All five forms take the same fixed-rounding row actions in the same colour order, so V-cycles run
 with any of them give the same bits, in FP32 and in FP64. The FP64 cluster form is also checked
 against the oracle per level step (1e-12) and per V-cycle (1e-11). Kaczmarz levels of
-n = 48 (49 rows: ragged bands), 64, 128 and 256, the coarse tail off so that the level runs in
-the form under test; batches retire instances inside every form's launches.
+n = 48 (49 rows: ragged bands), 64, 128, 256 and 1024 (where the FP32 tiles take two sweeps per
+launch), the coarse tail off so that the level runs in the form under test; batches retire
+instances inside every form's launches.
 """
 import numpy as np
 import pytest
@@ -48,6 +49,9 @@ CASES = {
     "wedge512_k100": (lambda: wedge(512, 100.0), 64),
     "wedge512_k160": (lambda: wedge(512, 160.0), 128),
     "wedge1024_k320": (lambda: wedge(1024, 320.0), 256),
+    # n_l = 1024: the FP32 tiles run two sweeps per launch on 64-node tiles
+    "const2048_k1200": (lambda: I.Workload("const_n2048", 2048, 1200.0, I.constant_k(2048, 1200.0),
+                                           I.centre_source_rhs(2048), variant="hyb", levels=0), 1024),
 }
 
 
@@ -85,8 +89,9 @@ def test_kaczmarz_forms_give_the_same_bits(name, precision):
     wl = make()
     r = rand_c((wl.n + 1) ** 2, 77)
     out = {}
-    # the FP64 cluster form holds levels up to n = 128 (56 bytes a node in 16 x 200 KB)
-    cluster_fits = precision == "fp32" or nk <= 128
+    # the cluster form holds levels up to n = 256 in FP32 and 128 in FP64 (28 or 56 bytes a node
+    # in 16 x 200 KB)
+    cluster_fits = nk <= (256 if precision == "fp32" else 128)
     for form in ("colour", "level", "tile", "cluster", "grid"):
         z, s = vcycle(wl, precision, form, r)
         got = s[kacz_level(s, nk)]["kacz_form"]
