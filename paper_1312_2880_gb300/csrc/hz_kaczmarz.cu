@@ -43,7 +43,8 @@ struct TileGeo {
   static constexpr int RX = KT_ + 2 * HX, RY = KT_ + HN + HF, REG = RX * RY;
 };
 using TileOne = TileGeo<32, 1, 256>;   // one sweep per launch: 44 x 48 regions
-using TileTwo = TileGeo<64, 2, 1024>;  // two sweeps per launch: 88 x 96 regions (FP32, large levels)
+using TileTwo = TileGeo<64, 2, 1024>;  // two sweeps per launch: 88 x 96 regions (FP32, n_l >= 1024)
+using TileTwoS = TileGeo<32, 2, 512>;  // two sweeps per launch: 56 x 64 regions (FP32, n_l = 512 .. 1023)
 template <class T, class G>
 constexpr size_t tile_smem() { return (size_t)G::REG * (2 * sizeof(c2<T>) + sizeof(T)); }
 
@@ -527,12 +528,12 @@ cudaError_t tile_launch(void* uout, int po, const void* uin, int pu, const void*
 }
 
 int kacz_tile_sweeps_per_launch(bool fp32, int n, int nu) {
-  // two sweeps per launch on FP32 levels of at least 1024 intervals: 64-node tiles with the
-  // two-sweep halo read 1.03 region nodes per output and sweep, against 2.06 for one sweep on
-  // 32-node tiles; smaller levels keep one sweep (too few 64-node tiles to fill the GPU). The
-  // launches ping-pong between two arrays and must end in u from an input in u, so their number
-  // has to be even: nu a multiple of 4.
-  return (fp32 && n >= 1024 && nu % 4 == 0) ? 2 : 1;
+  // two sweeps per launch on FP32 levels of at least 512 intervals: with the two-sweep halo,
+  // 64-node tiles (n_l >= 1024) read 1.03 region nodes per output and sweep and 32-node tiles
+  // (n_l >= 512, where 64-node tiles are too few to fill the GPU) 1.75, against 2.06 for one
+  // sweep on 32-node tiles. The launches ping-pong between two arrays and must end in u from an
+  // input in u, so their number has to be even: nu a multiple of 4.
+  return (fp32 && n >= 512 && nu % 4 == 0) ? 2 : 1;
 }
 
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
@@ -540,11 +541,14 @@ cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* ui
                                    const int* stop, cudaStream_t s, const Inst& bi) {
   if (!fp32)
     return tile_launch<double, double2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
-  if (f64_src)
-    return sweeps == 2 ? tile_launch<float, double2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
-                       : tile_launch<float, double2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
-  return sweeps == 2 ? tile_launch<float, float2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
-                     : tile_launch<float, float2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
+  if (sweeps == 2 && n >= 1024)
+    return f64_src ? tile_launch<float, double2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
+                   : tile_launch<float, float2, TileTwo>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
+  if (sweeps == 2)
+    return f64_src ? tile_launch<float, double2, TileTwoS>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
+                   : tile_launch<float, float2, TileTwoS>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
+  return f64_src ? tile_launch<float, double2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi)
+                 : tile_launch<float, float2, TileOne>(uout, po, uin, pu, f, pf, kh, pk, n, bA, post, stop, s, bi);
 }
 
 namespace {

@@ -5,8 +5,8 @@ with grid-wide barriers.
 All five forms take the same fixed-rounding row actions in the same colour order, so V-cycles run
 with any of them give the same bits, in FP32 and in FP64. The FP64 cluster form is also checked
 against the oracle per level step (1e-12) and per V-cycle (1e-11). Kaczmarz levels of
-n = 48 (49 rows: ragged bands), 64, 128, 256 and 1024 (where the FP32 tiles take two sweeps per
-launch), the coarse tail off so that the level runs in the form under test; batches retire
+n = 48 (49 rows: ragged bands), 64, 128, 256, 512 and 1024 (where the FP32 tiles take two sweeps
+per launch), the coarse tail off so that the level runs in the form under test; batches retire
 instances inside every form's launches.
 """
 import numpy as np
@@ -49,7 +49,9 @@ CASES = {
     "wedge512_k100": (lambda: wedge(512, 100.0), 64),
     "wedge512_k160": (lambda: wedge(512, 160.0), 128),
     "wedge1024_k320": (lambda: wedge(1024, 320.0), 256),
-    # n_l = 1024: the FP32 tiles run two sweeps per launch on 64-node tiles
+    # n_l = 512 and 1024: the FP32 tiles run two sweeps per launch on 32- and 64-node tiles
+    "const1024_k600": (lambda: I.Workload("const_n1024", 1024, 600.0, I.constant_k(1024, 600.0),
+                                          I.centre_source_rhs(1024), variant="hyb", levels=0), 512),
     "const2048_k1200": (lambda: I.Workload("const_n2048", 2048, 1200.0, I.constant_k(2048, 1200.0),
                                            I.centre_source_rhs(2048), variant="hyb", levels=0), 1024),
 }
