@@ -95,8 +95,9 @@ typedef struct {
                        operations, same results as the per-level kernels for one-sweep Gauss-Seidel
                        and FP32 Kaczmarz levels); 0: one or more launches per level */
   int kacz_form;    /* how Kaczmarz levels below the finest run (hz_kacz_form): -1 (default) = one
-                       block if the level fits its shared memory, else a thread-block cluster, else
-                       tiles (even sweep counts), else colour launches in the FP32 form; a cluster,
+                       block if the level fits its shared memory, else tiles with two sweeps per
+                       launch (n_l >= 256, sweep count a multiple of 4), else a thread-block
+                       cluster, else tiles (even sweep counts), else colour launches in the FP32 form; a cluster,
                        else colour launches in the FP64 form. A form that does not apply to a level
                        falls back to that default. */
   int gs_smoother;  /* smoother of the levels the rules of Sec. 5 give Gauss-Seidel: HZ_SMOOTH_GS

@@ -371,6 +371,11 @@ bool kform_ok(const hz_problem* P, int l, int form) {
 // n_l = 128 cluster 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64
 // cluster 206 us, colour launches 820 us; FP64 n_l = 1024 tiles 4.49 ms, colour launches 2.39 ms.
 int default_kform(const hz_problem* P, int l) {
+  // FP32 levels of n_l >= 256 with a multiple of 4 sweeps: two sweeps per tiled launch beat the
+  // cluster (config 3, n_l = 256: 0.13 ms per iteration against 0.23)
+  if (P->plan.fp32 && kacz_tile_sweeps_per_launch(true, P->lv[l].n, P->lv[l].nu) == 2 &&
+      !kacz_level_fits(true, P->lv[l].n) && kform_ok(P, l, HZ_KACZ_TILE))
+    return HZ_KACZ_TILE;
   const int order32[] = {HZ_KACZ_LEVEL, HZ_KACZ_CLUSTER, HZ_KACZ_TILE}, order64[] = {HZ_KACZ_CLUSTER};
   const int* o = P->plan.fp32 ? order32 : order64;
   const int cnt = P->plan.fp32 ? 3 : 1;

@@ -44,7 +44,7 @@ struct TileGeo {
 };
 using TileOne = TileGeo<32, 1, 256>;   // one sweep per launch: 44 x 48 regions
 using TileTwo = TileGeo<64, 2, 1024>;  // two sweeps per launch: 88 x 96 regions (FP32, n_l >= 1024)
-using TileTwoS = TileGeo<32, 2, 512>;  // two sweeps per launch: 56 x 64 regions (FP32, n_l = 512 .. 1023)
+using TileTwoS = TileGeo<32, 2, 512>;  // two sweeps per launch: 56 x 64 regions (FP32, n_l = 256 .. 1023)
 template <class T, class G>
 constexpr size_t tile_smem() { return (size_t)G::REG * (2 * sizeof(c2<T>) + sizeof(T)); }
 
@@ -528,12 +528,12 @@ cudaError_t tile_launch(void* uout, int po, const void* uin, int pu, const void*
 }
 
 int kacz_tile_sweeps_per_launch(bool fp32, int n, int nu) {
-  // two sweeps per launch on FP32 levels of at least 512 intervals: with the two-sweep halo,
+  // two sweeps per launch on FP32 levels of at least 256 intervals: with the two-sweep halo,
   // 64-node tiles (n_l >= 1024) read 1.03 region nodes per output and sweep and 32-node tiles
-  // (n_l >= 512, where 64-node tiles are too few to fill the GPU) 1.75, against 2.06 for one
-  // sweep on 32-node tiles. The launches ping-pong between two arrays and must end in u from an
+  // (n_l = 256 .. 1023, where 64-node tiles are too few to fill the GPU) 1.75, against 2.06 for
+  // one sweep on 32-node tiles. The launches ping-pong between two arrays and must end in u from an
   // input in u, so their number has to be even: nu a multiple of 4.
-  return (fp32 && n >= 512 && nu % 4 == 0) ? 2 : 1;
+  return (fp32 && n >= 256 && nu % 4 == 0) ? 2 : 1;
 }
 
 cudaError_t launch_kacz_sweep_tile(bool fp32, void* uout, int po, const void* uin, int pu, const void* f, int pf,
