@@ -33,6 +33,7 @@ class Job:
     start: float | None = None
     end: float | None = None
     result: dict = field(default_factory=dict)
+    precision: str | None = None  # None: the server's; set to "fp64" when a solve falls back
 
 
 def device_io(n: int, source: tuple):
@@ -47,13 +48,16 @@ def device_io(n: int, source: tuple):
 
 class Server:
     """The serving loop. ``keep_solutions``: True copies every solution to the host (in the job's
-    result), a set of request ids only those requests' solutions."""
+    result), a set of request ids only those requests' solutions. ``fallback``: a request whose
+    FP32-form solve ends without reaching the tolerance (maxit or breakdown: FP32 rounding of the
+    V-cycle can stall a long Bi-CGSTAB run that the FP64 form completes) is solved again at once by
+    the FP64 form; its result records the first attempt."""
 
     ENOMEM = 2  # hz_status of a request whose hierarchy can never fit the budget
 
     def __init__(self, hbm_budget: int, precision: str = "fp32", tol: float = 1e-6, maxit: int = 4000,
                  max_active: int = 32, variant: str = "hyb", keep_solutions=False, backend=None,
-                 make_io=device_io):
+                 make_io=device_io, fallback: bool = True):
         if backend is None:
             from . import hz as backend
         self.hz = backend
@@ -65,6 +69,8 @@ class Server:
         self.max_active = max_active
         self.variant = variant
         self.keep = keep_solutions
+        self.fallback = fallback
+        self.fallbacks = 0
         self.queue = collections.deque()
         self.active = []  # (job, problem, rhs, x)
         self.idle = collections.OrderedDict()  # key -> list of idle problems (LRU order)
@@ -75,8 +81,15 @@ class Server:
         self.evictions = 0
 
     # ------------------------------------------------------------------ memory
-    def footprint(self, n: int) -> int:
-        return self.hz.footprint_bytes(n, precision=self.precision, variant=self.variant) + 2 * 16 * (n + 1) ** 2
+    def footprint(self, n: int, precision: str | None = None) -> int:
+        prec = precision or self.precision
+        return self.hz.footprint_bytes(n, precision=prec, variant=self.variant) + 2 * 16 * (n + 1) ** 2
+
+    def _prec(self, job: Job) -> str:
+        return job.precision or self.precision
+
+    def _key(self, job: Job) -> tuple:
+        return (job.key, self._prec(job))
 
     def _evict_for(self, need: int) -> bool:
         while self.used + need > self.budget and self.idle:
@@ -84,24 +97,25 @@ class Server:
             prob = plist.pop()
             if not plist:
                 del self.idle[key]
-            self.used -= self.footprint(prob.n)
+            self.used -= self.footprint(prob.n, prob.key[1])
             prob.close()
             self.evictions += 1
         return self.used + need <= self.budget
 
     def _acquire(self, job: Job):
-        plist = self.idle.get(job.key)
+        key = self._key(job)
+        plist = self.idle.get(key)
         if plist:
             prob = plist.pop()
             if not plist:
-                del self.idle[job.key]
+                del self.idle[key]
             return prob
-        need = self.footprint(job.n)
+        need = self.footprint(job.n, self._prec(job))
         if not self._evict_for(need):
             return None
-        prob = self.hz.Problem(job.n, job.kfield_fn(), 0.5, variant=self.variant, precision=self.precision,
+        prob = self.hz.Problem(job.n, job.kfield_fn(), 0.5, variant=self.variant, precision=self._prec(job),
                                k_ref=job.k_ref)
-        prob.key = job.key
+        prob.key = key
         self.used += need
         self.peak_used = max(self.peak_used, self.used)
         return prob
@@ -122,7 +136,7 @@ class Server:
     def _admit(self, now: float):
         while self.queue and len(self.active) < self.max_active:
             job = self.queue[0]
-            if job.key not in self.idle and self.footprint(job.n) > self.budget:
+            if self._key(job) not in self.idle and self.footprint(job.n, self._prec(job)) > self.budget:
                 # no amount of eviction makes room: fail the request instead of waiting forever
                 self.queue.popleft()
                 self._reject(job, now, self.ENOMEM, "footprint exceeds the device-memory budget")
@@ -142,8 +156,19 @@ class Server:
         for job, prob, rhs, x in self.active:
             if prob.solve_poll():
                 x, info, _ = prob.solve_finish(history_cap=0, allow_fail=True)
+                if info["status"] != 0 and self.fallback and self._prec(job) == "fp32":
+                    # solve it again with the FP64 V-cycle, ahead of the queue
+                    job.result = {"fp32_attempt": dict(info)}
+                    job.precision = "fp64"
+                    self.fallbacks += 1
+                    self._release(prob)
+                    self.queue.appendleft(job)
+                    continue
                 job.end = now_fn()
+                first = job.result.get("fp32_attempt")
                 job.result = dict(info)
+                if first is not None:
+                    job.result["fp32_attempt"] = first
                 if self.keep is True or (self.keep and job.rid in self.keep):
                     job.result["x"] = x.cpu().numpy()
                 self.done.append(job)
@@ -183,6 +208,7 @@ class Server:
             "peak_hbm_bytes": self.peak_used,
             "peak_active": self.peak_active,
             "evictions": self.evictions,
+            "fp64_fallbacks": self.fallbacks,
             "statuses": dict(collections.Counter(int(j.result.get("status", -1)) for j in self.done)),
         }
 

@@ -85,3 +85,33 @@ def test_request_larger_than_the_budget_is_rejected_not_queued_forever(server):
     assert out["statuses"] == {0: 2, serve.Server.ENOMEM: 1}
     big = [j for j in s.done if j.rid == 1][0]
     assert big.result["status"] == serve.Server.ENOMEM and "budget" in big.result["error"]
+
+
+class StallingFp32Problem(FakeProblem):
+    """FP32-form solves of odd request sizes end at maxit; FP64 ones converge."""
+
+    def __init__(self, n, kfield, beta, precision="fp32", **kw):
+        super().__init__(n, kfield, beta, **kw)
+        self.precision = precision
+
+    def solve_finish(self, history_cap=0, allow_fail=False):
+        if self.precision == "fp32" and self.n == 96:
+            return None, {"status": 6, "iterations": 4000.0, "relres_true": 1e-3, "restarts": 0}, []
+        return None, {"status": 0, "iterations": 10.0, "relres_true": 1e-7, "restarts": 0}, []
+
+
+class StallingHz(FakeHz):
+    Problem = StallingFp32Problem
+
+
+def test_fp32_solve_that_does_not_converge_falls_back_to_fp64():
+    s = serve.Server(hbm_budget=10**9, max_active=4, backend=StallingHz, make_io=lambda n, src: (None, None))
+    jobs = [_job(0, 64, ("a",)), _job(1, 96, ("b",)), _job(2, 64, ("a",))]
+    out = s.run(jobs, realtime=False, time_limit=30.0)
+    assert out["completed"] == 3 and out["converged"] == 3 and out["fp64_fallbacks"] == 1
+    j1 = [j for j in s.done if j.rid == 1][0]
+    assert j1.precision == "fp64" and j1.result["fp32_attempt"]["status"] == 6
+    assert all(j.precision is None for j in s.done if j.rid != 1)
+    off = serve.Server(hbm_budget=10**9, max_active=4, backend=StallingHz, make_io=lambda n, src: (None, None),
+                       fallback=False)
+    assert off.run([_job(1, 96, ("b",))], realtime=False, time_limit=30.0)["converged"] == 0
