@@ -63,3 +63,44 @@ def test_group_of_batched_problems_equals_separate_solves():
         for b in range(P.batch):
             assert infos[q]["iterations"] == ib[b]["iterations"] and infos[q]["status"] == 0
             q += 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_workload_matches_the_oracle(precision):
+    """The batched workload itself (64 right-hand sides over n = 96, 192, 384, 576 at kh = 2 pi / 12,
+    one group solve): right-hand side 0 of the two smaller grids against the oracle's own solves.
+    FP64 form: iterations within the oracle's spread under one-ulp rescalings of b, solution within max(1e-10, 10 x that
+    spread); FP32 form: relres 1e-6 on the oracle's operator and within 1e-4 of the oracle."""
+    from paper_1312_2880_gb300 import hz
+
+    wls = I.batch_problems(rhs_per_k=16)
+    probs = [hz.Problem(w.n, w.kfield, 0.5, variant=w.variant, precision=precision, k_ref=w.k_ref,
+                        batch=w.rhs.shape[0]) for w in wls]
+    G = hz.Group(probs)
+    xs, infos = G.solve([torch.from_numpy(w.rhs).cuda() for w in wls], tol=1e-6, maxit=3000)
+    G.close()
+    for P in probs:
+        P.close()
+    assert all(i["status"] == 0 for i in infos)
+    for pi in (0, 1):
+        w = wls[pi]
+        b = w.rhs[0].ravel()
+        A = o.helmholtz_matrix(w.n, w.kfield)
+        H = o.build_hierarchy(w.n, w.kfield, w.k_ref, w.variant, w.levels)
+        ref = o.bicgstab(A, b, lambda v: o.vcycle(H, v), tol=1e-6, maxit=3000)
+        x = xs[pi][0].cpu().numpy().ravel()
+        err = float(np.abs(x - ref.x).max() / np.abs(ref.x).max())
+        assert o.true_relres(A, b, x) <= 1e-6
+        it = infos[16 * pi]["iterations"]
+        if precision == "fp64":
+            # the oracle's own spread: its solution and iteration count under three one-ulp-scale
+            # rescalings of b
+            spread, spread_it = 0.0, 0.0
+            for sc in (1 + 2.0**-52, 1 - 2.0**-53, 1 + 2.0**-51):
+                alt = o.bicgstab(A, b * sc, lambda v: o.vcycle(H, v), tol=1e-6, maxit=3000)
+                spread = max(spread, float(np.abs(alt.x / sc - ref.x).max() / np.abs(ref.x).max()))
+                spread_it = max(spread_it, abs(alt.iterations - ref.iterations))
+            assert abs(it - ref.iterations) <= max(2.0, 2 * spread_it)
+            assert err <= max(1e-10, 10 * spread), (err, spread)
+        else:
+            assert err <= 1e-4, (w.n, err)
