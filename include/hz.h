@@ -186,8 +186,10 @@ hz_status hz_vcycle(hz_problem* p, const double* r, double* z);
  *  history : host, capacity history_cap doubles (may be NULL/0): relative recurrence residual
  *            after every half step.
  *  info    : host, may be NULL.
- * Returns HZ_OK, HZ_EMAXIT, HZ_EBREAKDOWN or HZ_ENONFINITE (x holds the last iterate), or an
- * argument/CUDA error. Synchronises the stream. */
+ * Returns HZ_OK, HZ_EMAXIT (also when the recurrence converged but the true residual never
+ * confirmed it, see hz_solve_info.restarts), HZ_EBREAKDOWN or HZ_ENONFINITE (x holds the last
+ * iterate), HZ_ETIMEOUT (a bounded wait of the grid-synchronised Kaczmarz form ran out; x is not
+ * meaningful), or an argument/CUDA error. Synchronises the stream. */
 hz_status hz_solve(hz_problem* p, const double* rhs, double* x, double tol, int maxit,
                    double* history, int history_cap, hz_solve_info* info);
 
