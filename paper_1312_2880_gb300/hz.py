@@ -117,7 +117,7 @@ def lib() -> ctypes.CDLL:
     return L
 
 
-def measure_fp64_rate(iters=(1 << 12, 1 << 14)) -> dict:
+def measure_fp64_rate(iters=(1 << 10, 1 << 12, 1 << 14)) -> dict:
     """FP64 FMA throughput of the current device in TFLOP/s (hz_measure_fp64_rate), on torch's
     current stream: the best over the given chain lengths (short launches see the burst clock, as
     the solver's sub-millisecond Krylov kernels do)."""
