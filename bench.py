@@ -385,6 +385,36 @@ def oracle_workload(kind: str, key):
     raise ValueError(kind)
 
 
+def oracle_batch_solve(key):
+    """One oracle solve of right-hand side `q` of batched grid `pi` (key = (pi, q)); returns its
+    wall time in seconds (worker process)."""
+    t0 = time.perf_counter()
+    oracle_job(("solve", "batch", key))
+    return time.perf_counter() - t0
+
+
+def allcore_batched_baseline(grids=(0, 1), per_grid: int = 16):
+    """The oracle on every host core: the right-hand sides of the batched workload's two smaller
+    grids (n = 96, 192) solved by one process per core (spawned), against the same solves on one
+    core (their summed single-process times). The oracle's own solve is single-threaded (scipy's
+    sparse products hold the GIL), so independent solves are how it uses more cores."""
+    import concurrent.futures
+    import multiprocessing
+
+    keys = [(pi, q) for pi in grids for q in range(per_grid)]
+    cores = os.cpu_count() or 1
+    with concurrent.futures.ProcessPoolExecutor(max_workers=cores,
+                                                mp_context=multiprocessing.get_context("spawn")) as pool:
+        list(pool.map(oracle_batch_solve, [(0, 0)] * cores))  # start every worker (imports)
+        t0 = time.perf_counter()
+        per = list(pool.map(oracle_batch_solve, keys))
+        wall = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": cores, "solves": len(keys), "wall_s": round(wall, 2),
+            "solves_per_s": round(len(keys) / wall, 3), "one_core_solves_per_s": round(len(keys) / sum(per), 3),
+            "sample": f"right-hand sides 0..{per_grid - 1} of the batched grids n = "
+                      f"{', '.join(str(I.BATCH_SPECS[g][1]) for g in grids)}, one process per core"}
+
+
 def rel_err(x, ref) -> float:
     x = np.asarray(x).ravel()
     ref = np.asarray(ref).ravel()
@@ -587,6 +617,8 @@ def run_ours(args):
     if with_oracle:
         line.update(oracle_fields(args, wl, results, fut, small, kept_b, kept_s, serve_ids))
         pool.shutdown()
+        if not args.skip_forms:
+            line["cpu_baseline"]["all_cores_batched"] = allcore_batched_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
