@@ -9,9 +9,10 @@
 //   diagonal and 1/|a_p|^2 computed once per launch (operations in hz_level.cuh). Pre mode: zero guess, nu sweeps (colours
 //   0..4), then the residual with the (B) operator and full weighting onto the coarse level. Post
 //   mode: u_pre + P e_c, then nu sweeps (colours 4..0).
-// kacz_sweep_tile: one full sweep (all five colours) per launch over tiles with a halo that holds
-//   the dependency cone of one sweep (6 columns each side, 6 and 10 rows), so the tile interior
-//   holds exactly the sequential sweep's values. Out of place.
+// kacz_sweep_tile: one or two full sweeps (all five colours each) per launch over tiles with a halo
+//   that holds the dependency cone of the sweeps (6 columns each side, 6 and 10 rows per sweep), so
+//   the tile interior holds exactly the sequential sweeps' values; each phase acts only on the
+//   part of the region that can still reach the tile. Out of place.
 // kacz_cluster_*: the kacz_level_* operations with the level split into row bands over a
 //   thread-block cluster of up to 16 blocks (distributed shared memory, one cluster barrier per
 //   colour), for levels too large for one block or, in FP64, too slow on one SM's FP64 pipe.
@@ -20,6 +21,7 @@
 
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "hz_common.cuh"
 #include "hz_internal.h"
@@ -48,28 +50,136 @@ using TileTwoS = TileGeo<32, 2, 512>;  // two sweeps per launch: 56 x 64 regions
 template <class T, class G>
 constexpr size_t tile_smem() { return (size_t)G::REG * (2 * sizeof(c2<T>) + sizeof(T)); }
 
-// Row action on row (i, j) of a level whose values sit in shared arrays of row pitch w with
-// origin (gx, gy): the row constants come from k H as in the whole-level forms, and the action is
-// lvl::act_at, so a tiled sweep gives the same bits as the whole-level and cluster forms.
-template <class T>
-__device__ __forceinline__ void row_action(c2<T>* su, const c2<T>* sf, const T* sk, int w, int gx, int gy, int i,
-                                           int j, int n, T beta) {
-  const int p = (j - gy) * w + (i - gx);
-  c2<T> d;
-  T inv;
-  lvl::row_consts<T>(sk[p], i, j, n, beta, &d, &inv);
-  lvl::act_at<T>(su, sf[p], d, inv, p, i > 0 ? -1 : 1, i < n ? 1 : -1, j > 0 ? -w : w, j < n ? w : -w);
-}
+// Actions of phase ph (of P = 5S; R = P - 1 - ph phases follow it) that can still reach the
+// tile's outputs. Propagating dependencies back from the outputs through the colour phases on an
+// unbounded grid (every residue of the colour pattern gives the same bounds) leaves, in tile
+// coordinates (output origin 0), the phase's colour in columns -1-R .. KT+R and rows -1-R .. KT+2R
+// (order 0..4) or -1-2R .. KT+R (order 4..0). An action outside that rectangle changes only values
+// no output depends on, so leaving it out keeps the outputs' bits, and it cuts the actions of a
+// two-sweep launch on 64-node tiles by a third against sweeping the whole region every phase.
+// Slot q of a phase is the (q mod per)-th node of the colour from column xlo in row ylo + q / per.
+template <class G, bool POST>
+struct PhaseRect {
+  static constexpr int P = 5 * G::S;
+  static constexpr int below = POST ? G::HF : G::HN;  // region rows below the tile
+  __host__ __device__ static constexpr int R(int ph) { return P - 1 - ph; }
+  __host__ __device__ static constexpr int xlo(int ph) { return G::HX - 1 - R(ph); }
+  __host__ __device__ static constexpr int xhi(int ph) { return G::HX + G::KT + R(ph); }
+  __host__ __device__ static constexpr int ylo(int ph) { return below - 1 - (POST ? 2 : 1) * R(ph); }
+  __host__ __device__ static constexpr int yhi(int ph) { return below + G::KT + (POST ? 1 : 2) * R(ph); }
+  __host__ __device__ static constexpr int per(int ph) { return (xhi(ph) - xlo(ph)) / 5 + 1; }
+  __host__ __device__ static constexpr int slots(int ph) { return (yhi(ph) - ylo(ph) + 1) * per(ph); }
+  // every rectangle's supports inside the region, at most two slots per thread
+  __host__ __device__ static constexpr bool fits() {
+    for (int ph = 0; ph < P; ++ph)
+      if (xlo(ph) < 1 || xhi(ph) > G::RX - 2 || ylo(ph) < 1 || yhi(ph) > G::RY - 2 || slots(ph) > 2 * G::TBK)
+        return false;
+    return true;
+  }
+};
 
-// The same row action for a node strictly inside the square (no mirror, no boundary term).
+// One slot's row action: shared offsets of the node and its W, E, S, N support (a mirror neighbour
+// at the boundary appears twice), the values read, and the row's right-hand side and constants.
 template <class T>
-__device__ __forceinline__ void row_action_inner(c2<T>* su, const c2<T>* sf, const T* sk, int w, int p, T beta) {
-  const c2<T> d = xr::diag<T>(sk[p], 0, beta);
-  const T inv = xr::rcp(xr::add(xr::cabs2<T>(d), (T)4));
-  lvl::act_at<T>(su, sf[p], d, inv, p, -1, 1, -w, w);
-}
+struct TileAct {
+  int op, ow, oe, os, on, i, j;
+  bool ok, mx, my;
+  c2<T> up, uw, ue, us, un, f;
+};
 
 __device__ __forceinline__ int mod5(int x) { return ((x % 5) + 5) % 5; }
+
+// Phase PH of a tile: each thread takes up to two slots, reads both supports before updating
+// either (same-colour supports are disjoint), then writes both back. The row constants come from
+// k H as in the whole-level forms (lvl::row_consts; strictly inside the square, no boundary term)
+// and the arithmetic is lvl::act_update, so a tiled sweep gives the same bits as the whole-level
+// and cluster forms.
+template <class T, class G, bool POST, bool INNER, int PH>
+__device__ __forceinline__ void tile_phase(c2<T>* su, const c2<T>* sf, const T* sk, const unsigned char* c0row,
+                                           int gx, int gy, int n, T beta) {
+  using PR = PhaseRect<G, POST>;
+  constexpr int colour = POST ? 4 - PH % 5 : PH % 5;
+  constexpr int xlo = PR::xlo(PH), xhi = PR::xhi(PH), ylo = PR::ylo(PH), per = PR::per(PH), slots = PR::slots(PH);
+  constexpr int K = ((colour - xlo) % 5 + 5) % 5;
+  constexpr int NS = slots > G::TBK ? 2 : 1;
+  constexpr int W = G::RX;
+  TileAct<T> a[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int q = (int)threadIdx.x + s * G::TBK;
+    const int rr = q / per, m = q - rr * per, r = ylo + rr;
+    int t = (q < slots ? (int)c0row[r] : 0) + K;  // column residue of the colour in row r, from xlo
+    t -= t >= 5 ? 5 : 0;
+    const int c = xlo + t + 5 * m, p = r * W + c;
+    TileAct<T>& A = a[s];
+    A.ok = q < slots && c <= xhi;
+    A.op = p;
+    if constexpr (INNER) {
+      A.mx = A.my = false;
+      A.ow = p - 1;
+      A.oe = p + 1;
+      A.os = p - W;
+      A.on = p + W;
+    } else {
+      A.i = gx + c;
+      A.j = gy + r;
+      A.ok = A.ok && (unsigned)A.i <= (unsigned)n && (unsigned)A.j <= (unsigned)n;
+      A.mx = A.i == 0 || A.i == n;
+      A.my = A.j == 0 || A.j == n;
+      A.ow = p + (A.i > 0 ? -1 : 1);
+      A.oe = p + (A.i < n ? 1 : -1);
+      A.os = p + (A.j > 0 ? -W : W);
+      A.on = p + (A.j < n ? W : -W);
+    }
+  }
+  T kh[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    TileAct<T>& A = a[s];
+    if (A.ok) {
+      A.up = su[A.op];
+      A.uw = su[A.ow];
+      A.ue = su[A.oe];
+      A.us = su[A.os];
+      A.un = su[A.on];
+      A.f = sf[A.op];
+      kh[s] = sk[A.op];
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    TileAct<T>& A = a[s];
+    if (A.ok) {
+      c2<T> d;
+      T inv;
+      if constexpr (INNER) {
+        d = xr::diag<T>(kh[s], 0, beta);
+        inv = xr::rcp(xr::add(xr::cabs2<T>(d), (T)4));
+      } else {
+        lvl::row_consts<T>(kh[s], A.i, A.j, n, beta, &d, &inv);
+      }
+      lvl::act_update<T>(A.up, A.uw, A.ue, A.us, A.un, A.f, d, inv, A.mx, A.my);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const TileAct<T>& A = a[s];
+    if (A.ok) {
+      su[A.op] = A.up;
+      su[A.ow] = A.uw;
+      if (!A.mx) su[A.oe] = A.ue;
+      su[A.os] = A.us;
+      if (!A.my) su[A.on] = A.un;
+    }
+  }
+}
+
+// All phases of a launch in order, a barrier after each.
+template <class T, class G, bool POST, bool INNER, int... PH>
+__device__ __forceinline__ void tile_phases(c2<T>* su, const c2<T>* sf, const T* sk, const unsigned char* c0row,
+                                            int gx, int gy, int n, T beta, std::integer_sequence<int, PH...>) {
+  ((tile_phase<T, G, POST, INNER, PH>(su, sf, sk, c0row, gx, gy, n, beta), __syncthreads()), ...);
+}
 
 // ------------------------------------------------------------------ whole level in one block
 // Shared layout of the whole-level kernels: u, f~, d (complex) and 1/|a|^2 (real) per node, each
@@ -175,12 +285,14 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
   lvl::for_nodes_blocked(n, [&](int, int i, int j, int p) { u[(long long)j * pu + i] = S.su[p]; });
 }
 
-template <class T, class F2, class G>
+template <class T, class F2, class G, bool POST>
 __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restrict__ uout, int po,
                                                                   const c2<T>* __restrict__ uin, int pu,
                                                                   const F2* __restrict__ f, int pf,
                                                                   const T* __restrict__ kh, int pk, int n, T bA,
-                                                                  int post, const int* __restrict__ stop, Inst bi) {
+                                                                  const int* __restrict__ stop, Inst bi) {
+  using PR = PhaseRect<G, POST>;
+  static_assert(PR::fits(), "phase rectangles must keep their supports inside the tile region");
   constexpr int TBK = G::TBK, RX = G::RX, RY = G::RY, REG = G::REG, KT = G::KT;
   pdl_enter();
   if (stop && stop[blockIdx.z * bi.stop_stride]) return;
@@ -191,9 +303,10 @@ __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restri
   c2<T>* su = reinterpret_cast<c2<T>*>(smem);
   c2<T>* sf = su + REG;
   T* sk = reinterpret_cast<T*>(sf + REG);
+  __shared__ unsigned char c0row[RY];  // column residue of colour 0 in each region row
   const int x0 = blockIdx.x * KT, y0 = blockIdx.y * KT;
   // sweeps in the order 0..4 (pre) need the near halo below the tile, 4..0 (post) above it
-  const int below = post ? G::HF : G::HN;
+  constexpr int below = PR::below;
   const int gx = x0 - G::HX, gy = y0 - below;
   // the tile region's u, f~ and k H in flight at once (cp.async, one wait): a plain load per node
   // would put one L2 latency per node a thread copies on the launch's critical path
@@ -212,40 +325,17 @@ __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restri
       lvl::cp_async<sizeof(T)>(sk + q, kh + (long long)j * pk + i);
     }
   }
+  for (int r = threadIdx.x; r < RY; r += TBK) c0row[r] = (unsigned char)mod5(-2 * (gy + r) - gx);
   lvl::cp_async_wait_all();
   __syncthreads();
-  constexpr int PER_ROW = (RX + 4) / 5;
-  if (gx >= 1 && gy >= 1 && gx + RX <= n && gy + RY <= n) {
-    // region strictly inside the square: no mirrors, no boundary terms
-    __shared__ int c0tab[RY];
-    for (int ph = 0; ph < 5 * G::S; ++ph) {
-      const int colour = post ? 4 - ph % 5 : ph % 5;
-      if (threadIdx.x < RY) c0tab[threadIdx.x] = mod5(colour - 2 * (gy + (int)threadIdx.x) - gx);
-      __syncthreads();
-      for (int q = threadIdx.x; q < RY * PER_ROW; q += TBK) {
-        const int r = q / PER_ROW, m = q - r * PER_ROW;
-        const int c = c0tab[r] + 5 * m;
-        if (r < 1 || r > RY - 2 || c < 1 || c > RX - 2) continue;
-        row_action_inner<T>(su, sf, sk, RX, r * RX + c, bA);
-      }
-      __syncthreads();
-    }
-  } else
-  for (int ph = 0; ph < 5 * G::S; ++ph) {
-    const int colour = post ? 4 - ph % 5 : ph % 5;
-    for (int q = threadIdx.x; q < RY * PER_ROW; q += TBK) {
-      int r = q / PER_ROW, m = q - r * PER_ROW;
-      int j = gy + r;
-      int c = ((colour - 2 * j - gx) % 5 + 5) % 5 + 5 * m;
-      int i = gx + c;
-      if (c >= RX || (unsigned)i > (unsigned)n || (unsigned)j > (unsigned)n) continue;
-      // the row's whole support (mirror neighbours included) must lie in the tile region
-      Nbr b = neighbours(i, j, n);
-      if (b.iw < gx || b.ie >= gx + RX || b.js < gy || b.jn >= gy + RY) continue;
-      row_action<T>(su, sf, sk, RX, gx, gy, i, j, n, bA);
-    }
-    __syncthreads();
-  }
+  // every action strictly inside the square: no mirrors, no boundary terms (phase 0's rectangle
+  // holds every later one)
+  const bool inner = gx + PR::xlo(0) >= 1 && gx + PR::xhi(0) <= n - 1 && gy + PR::ylo(0) >= 1 &&
+                     gy + PR::yhi(0) <= n - 1;
+  if (inner)
+    tile_phases<T, G, POST, true>(su, sf, sk, c0row, gx, gy, n, bA, std::make_integer_sequence<int, PR::P>{});
+  else
+    tile_phases<T, G, POST, false>(su, sf, sk, c0row, gx, gy, n, bA, std::make_integer_sequence<int, PR::P>{});
   for (int q = threadIdx.x; q < REG; q += TBK) {
     int r = q / RX, c = q - r * RX, i = gx + c, j = gy + r;
     if (r >= below && r < below + KT && c >= G::HX && c < G::HX + KT && (unsigned)i <= (unsigned)n &&
@@ -506,12 +596,12 @@ cudaError_t launch_cluster_kernel(void (*kernel)(Args...), int c, size_t smem, c
 
 }  // namespace
 
-template <class T, class F2, class G>
+template <class T, class F2, class G, bool POST>
 cudaError_t tile_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tile_smem<T, G>());
+  cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2, G, POST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<T, G>());
   if (!e) done = true;
   return e;
 }
@@ -519,11 +609,15 @@ cudaError_t tile_attr() {
 template <class T, class F2, class G>
 cudaError_t tile_launch(void* uout, int po, const void* uin, int pu, const void* f, int pf, const void* kh, int pk,
                         int n, double bA, bool post, const int* stop, cudaStream_t s, const Inst& bi) {
-  cudaError_t e = tile_attr<T, F2, G>();
+  cudaError_t e = post ? tile_attr<T, F2, G, true>() : tile_attr<T, F2, G, false>();
   if (e) return e;
   dim3 grid((n + G::KT) / G::KT, (n + G::KT) / G::KT, bi.count);
-  pdl_launch(kacz_sweep_tile_kernel<T, F2, G>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
-             (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, (int)post, stop, bi);
+  if (post)
+    pdl_launch(kacz_sweep_tile_kernel<T, F2, G, true>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
+               (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop, bi);
+  else
+    pdl_launch(kacz_sweep_tile_kernel<T, F2, G, false>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
+               (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop, bi);
   return cudaGetLastError();
 }
 

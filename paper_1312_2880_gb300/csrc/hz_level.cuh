@@ -97,24 +97,37 @@ __device__ __forceinline__ void row_consts(T kh, int i, int j, int n, T beta, c2
 // uw, ue, us, un (a mirror neighbour across the boundary is the same node on both sides, so its
 // two pointers coincide and it receives 2 delta in one update). The five values are read once and
 // written once. Every Kaczmarz kernel form goes through this function, so they give the same bits.
+// The arithmetic on the five values already read (mx / my: the W and E, or S and N, support nodes
+// are one mirror node, held in uw / us); act_nodes and the two-action form of the tiled sweep call it.
+template <class T>
+__device__ __forceinline__ void act_update(c2<T>& up, c2<T>& uw, c2<T>& ue, c2<T>& us, c2<T>& un, c2<T> f, c2<T> d,
+                                           T inv, bool mx, bool my) {
+  const c2<T> delta = xr::cscale<T>(xr::resid<T>(f, up, xr::nb4<T>(uw, ue, us, un), d), inv);
+  up = xr::cadd<T>(up, xr::cmulc<T>(d, delta));
+  if (mx) {
+    uw = xr::cadd<T>(uw, xr::cscale<T>(delta, (T)2));
+  } else {
+    uw = xr::cadd<T>(uw, delta);
+    ue = xr::cadd<T>(ue, delta);
+  }
+  if (my) {
+    us = xr::cadd<T>(us, xr::cscale<T>(delta, (T)2));
+  } else {
+    us = xr::cadd<T>(us, delta);
+    un = xr::cadd<T>(un, delta);
+  }
+}
 template <class T>
 __device__ __forceinline__ void act_nodes(c2<T>* pp, c2<T>* pw, c2<T>* pe, c2<T>* ps, c2<T>* pn, c2<T> f, c2<T> d,
                                           T inv) {
-  const c2<T> up = *pp, uw = *pw, ue = *pe, us = *ps, un = *pn;
-  const c2<T> delta = xr::cscale<T>(xr::resid<T>(f, up, xr::nb4<T>(uw, ue, us, un), d), inv);
-  *pp = xr::cadd<T>(up, xr::cmulc<T>(d, delta));
-  if (pw == pe) {
-    *pw = xr::cadd<T>(uw, xr::cscale<T>(delta, (T)2));
-  } else {
-    *pw = xr::cadd<T>(uw, delta);
-    *pe = xr::cadd<T>(ue, delta);
-  }
-  if (ps == pn) {
-    *ps = xr::cadd<T>(us, xr::cscale<T>(delta, (T)2));
-  } else {
-    *ps = xr::cadd<T>(us, delta);
-    *pn = xr::cadd<T>(un, delta);
-  }
+  c2<T> up = *pp, uw = *pw, ue = *pe, us = *ps, un = *pn;
+  const bool mx = pw == pe, my = ps == pn;
+  act_update<T>(up, uw, ue, us, un, f, d, inv, mx, my);
+  *pp = up;
+  *pw = uw;
+  if (!mx) *pe = ue;
+  *ps = us;
+  if (!my) *pn = un;
 }
 // The same at shared position p with neighbour offsets dw, de, ds, dn.
 template <class T>
