@@ -146,17 +146,6 @@ __device__ __forceinline__ void store_pair(c2<T>* __restrict__ row, int c0, int 
   if (s1) row[c0 + 1] = U.b;
 }
 
-// Four-row window after two stages: slot k takes the row of slot k + 2 (mod 4), so the stage code
-// written for slots 0 and 1 serves every pair of rows.
-template <class X>
-__device__ __forceinline__ void rotate2(X (&w)[4]) {
-  const X a = w[0], b = w[1];
-  w[0] = w[2];
-  w[1] = w[3];
-  w[2] = a;
-  w[3] = b;
-}
-
 template <class T>
 struct Lane {  // per-lane constants of a strip
   int c0, m0, m1;
@@ -295,15 +284,14 @@ __device__ __forceinline__ void sr_run(unsigned char* ring, const SRArgs<Real>& 
   for (int k = 0; k < 4; ++k) S.U[k].a = S.U[k].b = mk<Real>(0, 0);
   S.hS = S.hC = mk<Real>(0, 0);
   for (int t = 0; t < SR_R - 1; ++t) sr_issue<Real, EDGE, VF>(ring, A, t, T, y0, q);
-  // two stages of code per iteration (a small loop body keeps the instruction cache warm when
-  // few warps run); the four-row windows rotate by two rows between iterations
+  // four stages of code per iteration, one per slot of the four-row windows (row t in slot
+  // t mod 4), so no register moves rotate the windows between iterations
 #pragma unroll 1
-  for (int t0 = 0; t0 < T; t0 += 2) {
+  for (int t0 = 0; t0 < T; t0 += 4) {
     sr_stage<Real, 0, EDGE, VF>(S, ring, A, t0 + 0, T, y0, row_end, gx, q);
     sr_stage<Real, 1, EDGE, VF>(S, ring, A, t0 + 1, T, y0, row_end, gx, q);
-    rotate2(S.U);
-    rotate2(S.F);
-    rotate2(S.K);
+    sr_stage<Real, 2, EDGE, VF>(S, ring, A, t0 + 2, T, y0, row_end, gx, q);
+    sr_stage<Real, 3, EDGE, VF>(S, ring, A, t0 + 3, T, y0, row_end, gx, q);
   }
   cp_wait<0>();
 }
@@ -460,12 +448,11 @@ __device__ __forceinline__ void ps_run(unsigned char* ring, const PSArgs<Real>& 
   S.Ee = mk<Real>(0, 0);
   for (int t = 0; t < PS_R - 1; ++t) ps_issue<Real, EDGE, V>(ring, A, t, T, y0, q, ci);
 #pragma unroll 1
-  for (int t0 = 0; t0 < T; t0 += 2) {
+  for (int t0 = 0; t0 < T; t0 += 4) {  // as in sr_run: row t in window slot t mod 4
     ps_stage<Real, 0, EDGE, V>(S, ring, A, t0 + 0, T, y0, row_end, gx, q, ci);
     ps_stage<Real, 1, EDGE, V>(S, ring, A, t0 + 1, T, y0, row_end, gx, q, ci);
-    rotate2(S.U);
-    rotate2(S.F);
-    rotate2(S.K);
+    ps_stage<Real, 2, EDGE, V>(S, ring, A, t0 + 2, T, y0, row_end, gx, q, ci);
+    ps_stage<Real, 3, EDGE, V>(S, ring, A, t0 + 3, T, y0, row_end, gx, q, ci);
   }
   cp_wait<0>();
 }
