@@ -309,20 +309,27 @@ __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restri
   constexpr int below = PR::below;
   const int gx = x0 - G::HX, gy = y0 - below;
   // the tile region's u, f~ and k H in flight at once (cp.async, one wait): a plain load per node
-  // would put one L2 latency per node a thread copies on the launch's critical path
+  // would put one L2 latency per node a thread copies on the launch's critical path. A warp
+  // takes whole region rows, a lane every 32nd column: no division per node.
   constexpr bool async_f = sizeof(F2) == sizeof(c2<T>);  // f~ in the level's own precision
-  for (int q = threadIdx.x; q < REG; q += TBK) {
-    int r = q / RX, c = q - r * RX, i = gx + c, j = gy + r;
-    if ((unsigned)i <= (unsigned)n && (unsigned)j <= (unsigned)n) {
+  constexpr int NW = TBK / 32;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  for (int r = warp; r < RY; r += NW) {
+    const int j = gy + r;
+    if ((unsigned)j > (unsigned)n) continue;
+    const long long ju = (long long)j * pu, jf = (long long)j * pf, jk = (long long)j * pk;
+    for (int c = lane; c < RX; c += 32) {
+      const int i = gx + c, q = r * RX + c;
+      if ((unsigned)i > (unsigned)n) continue;
       if (uin)
-        lvl::cp_async<sizeof(c2<T>)>(su + q, uin + (long long)j * pu + i);
+        lvl::cp_async<sizeof(c2<T>)>(su + q, uin + ju + i);
       else
         su[q] = mk<T>(0, 0);
       if constexpr (async_f)
-        lvl::cp_async<sizeof(c2<T>)>(sf + q, f + (long long)j * pf + i);
+        lvl::cp_async<sizeof(c2<T>)>(sf + q, f + jf + i);
       else
-        sf[q] = ldc<T>(f, (long long)j * pf + i);
-      lvl::cp_async<sizeof(T)>(sk + q, kh + (long long)j * pk + i);
+        sf[q] = ldc<T>(f, jf + i);
+      lvl::cp_async<sizeof(T)>(sk + q, kh + jk + i);
     }
   }
   for (int r = threadIdx.x; r < RY; r += TBK) c0row[r] = (unsigned char)mod5(-2 * (gy + r) - gx);
@@ -336,11 +343,16 @@ __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restri
     tile_phases<T, G, POST, true>(su, sf, sk, c0row, gx, gy, n, bA, std::make_integer_sequence<int, PR::P>{});
   else
     tile_phases<T, G, POST, false>(su, sf, sk, c0row, gx, gy, n, bA, std::make_integer_sequence<int, PR::P>{});
-  for (int q = threadIdx.x; q < REG; q += TBK) {
-    int r = q / RX, c = q - r * RX, i = gx + c, j = gy + r;
-    if (r >= below && r < below + KT && c >= G::HX && c < G::HX + KT && (unsigned)i <= (unsigned)n &&
-        (unsigned)j <= (unsigned)n)
-      uout[(long long)j * po + i] = su[q];
+  // the tile's own KT x KT nodes (those inside the square) back to global memory, rows by warp
+  for (int r = below + warp; r < below + KT; r += NW) {
+    const int j = gy + r;
+    if (j > n) break;
+    c2<T>* orow = uout + (long long)j * po;
+    for (int c = G::HX + lane; c < G::HX + KT; c += 32) {
+      const int i = gx + c;
+      if (i > n) break;
+      orow[i] = su[r * RX + c];
+    }
   }
 }
 
