@@ -783,6 +783,28 @@ def run_profile_case(args):
     P.close()
 
 
+def run_sweep(args):
+    """The fused passes and Kaczmarz sweeps of the FP32 form on a larger grid of the same medium and
+    kh (n = --sweep-n; k scaled with n): per-kernel HBM rates from two profiled iterations, as the
+    bench line's sweep_hbm, on arrays four or more times the size of config 3's."""
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    torch.cuda.set_device(0)
+    build.build()
+    hbm_peak, peak_kind = load_peaks()
+    n = args.sweep_n
+    wl = I.grf_n4096(n=n, k=1000.0 * n / 4096)
+    P = hz.Problem(wl.n, wl.kfield, 0.5, variant=wl.variant, precision="fp32", levels=wl.levels, k_ref=wl.k_ref)
+    per = profile(P, torch.from_numpy(wl.rhs).cuda())
+    torch.cuda.synchronize()
+    print(json.dumps({"sweep_workload": wl.name, "n": n, "hbm_peak": hbm_peak, "peak_source": peak_kind,
+                      "sweep_hbm": sweep_rates(per, True, hbm_peak, n), "kernel_share": shares(per),
+                      "tile_autotuner": pass_forms(P)}), flush=True)
+    P.close()
+
+
 def run_serving_only(args):
     """The served stream alone (both forms, or --serve-precision): a long run of the config."""
     import torch
@@ -868,9 +890,13 @@ def main():
     ap.add_argument("--tables", action="store_true", help="re-run the paper's Tables 1, 2 and 6 and exit")
     ap.add_argument("--tables-maxit", type=int, default=400)
     ap.add_argument("--tables-max-n", type=int, default=1024)
+    ap.add_argument("--sweep-n", type=int, default=0,
+                    help="time the V-cycle passes of the FP32 form on an n = SWEEP_N grid of the same medium and exit")
     args = ap.parse_args()
     if args.tables:
         run_tables(args)
+    elif args.sweep_n:
+        run_sweep(args)
     elif args.profile_case:
         run_profile_case(args)
     elif args.serve_only:
