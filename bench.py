@@ -66,7 +66,8 @@ def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
         "k_apply_rv": y + 8 + 16 + 16,
         "k_update_s": 48 + w,
         "k_apply_ts": y + 8 + 16 + 16,
-        "k_update_xr": 16 + 2 * y + 16 + 16 + 16 + 32,
+        "k_update_r": 16 + 16 + 16 + 16,           # s, t, r^; write r
+        "k_update_x": y + 32,                      # y or z; x in and out (one half of the update)
     }
     return table.get(kernel, 0.0)
 
@@ -74,7 +75,7 @@ def kernel_bytes_per_node(kernel: str, fp32: bool) -> float:
 # FP64 work per node of the Krylov kernels: (flops with an FMA counted 2, FP64-pipe instructions).
 # The operator on an interior node: 3 complex adds (6), d = (kh)^2 - 4 (1 FMA), v = nb + d y (2 FMA).
 KRYLOV_FP64 = {"k_update_p": (16, 8), "k_apply_rv": (20, 13), "k_update_s": (12, 6), "k_apply_ts": (24, 15),
-               "k_update_xr": (36, 18)}
+               "k_update_r": (20, 10), "k_update_x": (8, 4)}
 
 
 def load_peaks():
@@ -255,22 +256,27 @@ def profile(P, rhs, iterations: int = 2):
 
 def roofline(per, fp32: bool, hbm_peak: float, peak_kind: str, n: int, fp64_peak: dict | None):
     """The dominant kernel (largest total time) of a profile and its achieved rate: an FP64 Krylov
-    kernel against the measured FP64 FMA rate (flops, an FMA counted 2), a V-cycle kernel against
-    the measured HBM copy rate; the HBM fraction is given beside the FP64 one."""
+    kernel against the measured FP64 FMA rate, a V-cycle kernel against the measured HBM copy
+    rate; the HBM fraction is given beside the FP64 one. An FP64 kernel's rate is its FP64-pipe
+    issue rate in FMA-equivalents (every DFMA, DADD or DMUL takes one pipe slot and counts 2
+    flops, as the probe's DFMA chains do), its algorithmic flops (an add counted 1) beside."""
     total = sum(sum(v) for v in per.values())
     (name, level), times = max(per.items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
     nodes = ((n >> level) + 1) ** 2
     gbs = kernel_bytes_per_node(name, fp32) * nodes / (avg_ms * 1e-3) / 1e9
     if name.startswith("k_") and fp64_peak:
-        flops = KRYLOV_FP64[name][0] * nodes
-        achieved = flops / (avg_ms * 1e-3) / 1e12
+        flops, instr = KRYLOV_FP64[name]
+        secs = avg_ms * 1e-3
+        achieved = 2 * instr * nodes / secs / 1e12
         peak = fp64_peak["tflops"]
         roof = {"kernel": name, "level": level, "bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": "measured: hz_measure_fp64_rate in this run (DFMA chains on every SM, CUDA events); "
                                "FMA = 2 flops",
-                "flops_per_node": KRYLOV_FP64[name][0], "nodes": nodes,
+                "achieved_is": "FP64-pipe issue rate in FMA-equivalents (each DFMA, DADD or DMUL one pipe slot = 2 flops)",
+                "fp64_instructions_per_node": instr, "algorithmic_flops_per_node": flops,
+                "algorithmic_tflops": round(flops * nodes / secs / 1e12, 4), "nodes": nodes,
                 "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4), "hbm_peak": hbm_peak}
     else:
         roof = {"kernel": name, "level": level, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,

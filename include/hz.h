@@ -274,8 +274,8 @@ typedef enum {
   HZ_K_UPDATE_P,       /* p = r + beta (p - omega v) */
   HZ_K_APPLY_RV,       /* v = A y with <r^, v> */
   HZ_K_UPDATE_S,       /* s = r - alpha v with |s|^2 */
-  HZ_K_APPLY_TS,       /* t = A z with <t, s>, <t, t> (or, after a half-step stop, x += alpha y) */
-  HZ_K_UPDATE_XR,      /* x, r updates with <r^, r>, |r|^2 */
+  HZ_K_APPLY_TS,       /* t = A z with <t, s>, <t, t> */
+  HZ_K_UPDATE_R,       /* r = s - omega t with <r^, r>, |r|^2 */
   HZ_K_SMOOTH_RESTRICT, /* fused: GS sweep from a zero guess, residual, full weighting */
   HZ_K_PROLONG_SMOOTH, /* fused: bilinear correction and GS post-sweep */
   HZ_K_KACZ_LEVEL,     /* whole Kaczmarz level in one block (pre: sweeps + residual + FW; post: correction + sweeps) */
@@ -284,6 +284,7 @@ typedef enum {
   HZ_K_KACZ_CLUSTER,   /* whole Kaczmarz level over a thread-block cluster (pre or post, as HZ_K_KACZ_LEVEL) */
   HZ_K_JACOBI,         /* one damped Jacobi sweep, out of place */
   HZ_K_KACZ_GRID,      /* whole Kaczmarz level by one cooperative launch (pre or post, as HZ_K_KACZ_LEVEL) */
+  HZ_K_UPDATE_X,       /* half of the deferred solution update: x += alpha y or x += omega z */
   HZ_K_COUNT
 } hz_kernel;
 

@@ -200,6 +200,10 @@ struct hz_problem {
   } run;
   KState* kstate_host = nullptr;  // pinned copy of the device Krylov state at the end of a solve
   cudaEvent_t ev_final = nullptr;
+  // Side branch of an iteration: half of the deferred solution update (k_update_x) beside each
+  // V-cycle, forked at its start and joined before its finest post-smoothing pass.
+  cudaStream_t xstream = nullptr;
+  cudaEvent_t ev_xfork = nullptr, ev_xjoin = nullptr;
   // Measurement: when set, every launch is followed by an event on `stream` (hz_profile_iteration).
   struct ProfRec { int kernel, level; cudaEvent_t ev; };
   std::vector<ProfRec>* prof = nullptr;
@@ -598,14 +602,34 @@ Src level_src(const hz_problem* P, int l, const void* f0) {
   return l == 0 ? Src{f0, P->n + 1, !P->plan.fp32} : Src{P->lv[l].f, P->lv[l].pitch, false};
 }
 
+// Half of the deferred solution update (omega_half: x += omega z, else x += alpha y) on the side
+// stream; in line on the library stream in the FP64 form (whose V-cycle uses the FP64 pipe itself)
+// and while every launch is being timed. *forked tells whether a join is due.
+cudaError_t fork_x_update(hz_problem* P, bool omega_half, bool* forked) {
+  *forked = false;
+  if (P->prof || !P->plan.fp32) return mark(P, launch_k_update_x(P->kv, omega_half, P->stream), HZ_K_UPDATE_X, 0);
+  cudaError_t e = cudaEventRecord(P->ev_xfork, P->stream);
+  if (!e) e = cudaStreamWaitEvent(P->xstream, P->ev_xfork, 0);
+  if (!e) e = launch_k_update_x(P->kv, omega_half, P->xstream);
+  if (!e) e = cudaEventRecord(P->ev_xjoin, P->xstream);
+  *forked = !e;
+  return e;
+}
+
 // z = V-cycle(f0) with f0 already h^2-scaled; f0 and z (pitch n+1) are double2 in the FP64 form
-// and float2 in the FP32 form.
-cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, bool all = false) {
+// and float2 in the FP32 form. xhalf >= 0 runs that half of the deferred solution update beside
+// the cycle (0: x += alpha y, 1: x += omega z), from after its finest pre-smoothing pass (which
+// streams the finest grid through HBM at ~70% of the copy rate) until its finest post-smoothing
+// pass, the only launch of the cycle that writes z.
+cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, bool all = false, int xhalf = -1) {
   const int L = P->plan.levels, lt = P->tail_start;
   cudaError_t e;
+  bool forked = false;
   const int down_end = lt > 0 ? lt : L - 1;
-  for (int l = 0; l < down_end; ++l)
+  for (int l = 0; l < down_end; ++l) {
     if ((e = level_down(P, l, level_src(P, l, f0), stop, all))) return e;
+    if (l == 0 && xhalf >= 0 && (e = fork_x_update(P, xhalf == 1, &forked))) return e;
+  }
   if (lt > 0) {
     const Inst bi = inst_for(P, lt, all);
     if ((e = mark(P, launch_tail(P->plan.fp32, P->tail, P->tail_smem, stop, P->stream, bi), HZ_K_TAIL, lt))) return e;
@@ -613,6 +637,7 @@ cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, 
     return e;
   }
   for (int l = down_end - 1; l >= 0; --l) {
+    if (l == 0 && forked && (e = cudaStreamWaitEvent(P->stream, P->ev_xjoin, 0))) return e;
     void* out = l == 0 ? (void*)z : final_u(P, l);
     int po = l == 0 ? P->n + 1 : P->lv[l].pitch;
     if ((e = level_up(P, l, level_src(P, l, f0), out, po, stop, all))) return e;
@@ -620,7 +645,9 @@ cudaError_t run_vcycle(hz_problem* P, const void* f0, void* z, const int* stop, 
   return cudaSuccess;
 }
 
-// One Bi-CGSTAB iteration (two preconditioner applications, Sec. 6).
+// One Bi-CGSTAB iteration (two preconditioner applications, Sec. 6). The solution update is
+// deferred: x += alpha y of the previous step beside the first V-cycle, x += omega z beside the
+// second (KState::xa, xw; k_update_x).
 cudaError_t enqueue_iteration(hz_problem* P) {
   const KrylovVecs& k = P->kv;
   cudaStream_t s = P->stream;
@@ -628,12 +655,12 @@ cudaError_t enqueue_iteration(hz_problem* P) {
   cudaError_t e;
   const bool fp32 = P->plan.fp32;
   if ((e = mark(P, launch_k_update_p(k, s), HZ_K_UPDATE_P, 0))) return e;
-  if ((e = run_vcycle(P, fp32 ? (const void*)k.p32 : k.p, fp32 ? (void*)k.y32 : k.y, stop, true))) return e;
+  if ((e = run_vcycle(P, fp32 ? (const void*)k.p32 : k.p, fp32 ? (void*)k.y32 : k.y, stop, true, 0))) return e;
   if ((e = mark(P, launch_k_apply_rv(k, s), HZ_K_APPLY_RV, 0))) return e;
   if ((e = mark(P, launch_k_update_s(k, s), HZ_K_UPDATE_S, 0))) return e;
-  if ((e = run_vcycle(P, fp32 ? (const void*)k.s32 : k.s, fp32 ? (void*)k.z32 : k.z, stop, true))) return e;
+  if ((e = run_vcycle(P, fp32 ? (const void*)k.s32 : k.s, fp32 ? (void*)k.z32 : k.z, stop, true, 1))) return e;
   if ((e = mark(P, launch_k_apply_ts(k, s), HZ_K_APPLY_TS, 0))) return e;
-  return mark(P, launch_k_update_xr(k, s), HZ_K_UPDATE_XR, 0);
+  return mark(P, launch_k_update_r(k, s), HZ_K_UPDATE_R, 0);
 }
 
 // The solve graph: the loop counter is zeroed, then a WHILE conditional node runs body() (one
@@ -738,7 +765,9 @@ cudaError_t enqueue_replay(hz_problem* P) {
 
 cudaError_t launch_final(hz_problem* P) {
   cudaStream_t s = P->stream;
-  cudaError_t e = launch_k_true_residual(P->kv, s);
+  cudaError_t e = launch_k_update_x(P->kv, false, s);  // the last steps' pending solution update
+  if (!e) e = launch_k_update_x(P->kv, true, s);
+  if (!e) e = launch_k_true_residual(P->kv, s);
   if (!e) e = cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * P->plan.batch, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaEventRecord(P->ev_final, s);
   return e;
@@ -1216,6 +1245,9 @@ static void release(hz_problem* P) {
   P->run = hz_problem::Run();
   if (P->ev_out) { cudaEventDestroy(P->ev_out); P->ev_out = nullptr; }
   if (P->stream) { cudaStreamSynchronize(P->stream); cudaStreamDestroy(P->stream); P->stream = nullptr; }
+  if (P->xstream) { cudaStreamSynchronize(P->xstream); cudaStreamDestroy(P->xstream); P->xstream = nullptr; }
+  if (P->ev_xfork) { cudaEventDestroy(P->ev_xfork); P->ev_xfork = nullptr; }
+  if (P->ev_xjoin) { cudaEventDestroy(P->ev_xjoin); P->ev_xjoin = nullptr; }
   if (P->own_arena && P->arena) cudaFree(P->arena);
   P->arena = nullptr;
   P->own_arena = false;
@@ -1251,6 +1283,9 @@ hz_status hz_setup_hierarchy(hz_problem* P, const hz_hierarchy_opts* opts, void*
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&P->xstream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->ev_xfork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_xjoin, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&P->ev_final, cudaEventDisableTiming));
@@ -1739,6 +1774,8 @@ hz_status hz_group_solve(hz_group* g, const double* const* rhs, double* const* x
     for (size_t i = 0; i < np; ++i) {
       hz_problem* P = g->probs[i];
       GK(cudaStreamWaitEvent(P->stream, g->fork, 0));
+      GK(launch_k_update_x(P->kv, false, P->stream));  // the last steps' pending solution update
+      GK(launch_k_update_x(P->kv, true, P->stream));
       GK(launch_k_true_residual(P->kv, P->stream));
       GK(cudaMemcpyAsync(P->kstate_host, P->kv.st, sizeof(KState) * P->plan.batch, cudaMemcpyDeviceToHost, P->stream));
     }
@@ -1811,8 +1848,8 @@ hz_status hz_set_stall_detection(hz_problem* P, double cos2, double step2, int m
 const char* hz_kernel_name(int k) {
   static const char* names[] = {"gs_first", "gs_colour", "kacz_colour", "zero", "restrict_residual", "prolong_add",
                                 "coarse_solve", "export", "k_update_p", "k_apply_rv", "k_update_s",
-                                "k_apply_ts", "k_update_xr", "smooth_restrict", "prolong_smooth", "kacz_level",
-                                "kacz_sweep", "coarse_tail", "kacz_cluster", "jacobi", "kacz_grid"};
+                                "k_apply_ts", "k_update_r", "smooth_restrict", "prolong_smooth", "kacz_level",
+                                "kacz_sweep", "coarse_tail", "kacz_cluster", "jacobi", "kacz_grid", "k_update_x"};
   return (k >= 0 && k < HZ_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -180,7 +180,7 @@ struct KState {
   int first;     // 1: the next direction update is p = r (start or restart)
   int done;      // 0 running, 1 recurrence converged, 2 breakdown, 3 non-finite, 4 maxit,
                  // 5 near-breakdown: renew the shadow residual at the next direction update
-  int half;      // 1: converged after the half step, x += alpha y pending; 2: applied
+  int half;      // 1: converged after the half step (x += alpha y is then the step's only update)
   int hist_len;  // entries written to hist (may exceed hist_cap; extra entries are dropped)
   int hist_cap;
   int maxit;
@@ -191,10 +191,14 @@ struct KState {
   double min_step2;     // smallest |omega|^2 |t|^2 / |r|^2 seen while cos2 < stall_cos2 (diagnostics)
   double stall_cos2, stall_step2;  // near-breakdown thresholds of this solve (below)
   int max_shadow_restarts;
+  // Deferred solution update (k_update_x): x += alpha_x y is due when xa is set (from k_apply_rv),
+  // x += omega_x z when xw is set (from k_update_r); applied in that order.
+  double2 alpha_x, omega_x;
+  int xa, xw;
   unsigned int ticket[16];  // last-block counters, one per reduction kernel
 };
 
-enum { KT_INIT = 0, KT_RV, KT_S, KT_XHALF, KT_TS, KT_XR, KT_TRUE, KT_RESTART, KT_SHADOW };
+enum { KT_INIT = 0, KT_RV, KT_S, KT_XA, KT_TS, KT_XR, KT_TRUE, KT_RESTART, KT_SHADOW, KT_XW };
 
 // Shadow residual r^ (a reading of the paper's Bi-CGSTAB: pseudo-random instead of r^ = b).
 constexpr unsigned long long SHADOW_SEED = 0x5EED1312ull;
@@ -255,7 +259,9 @@ cudaError_t launch_k_update_p(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s);
-cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s);
+cudaError_t launch_k_update_r(const KrylovVecs& k, cudaStream_t s);
+// Half A (x += alpha y, omega_half false) or W (x += omega z) of the deferred solution update.
+cudaError_t launch_k_update_x(const KrylovVecs& k, bool omega_half, cudaStream_t s);
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s);
 cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s);  // every instance of k (use instance_of for one)
 // v = A u (scaled by out_scale) on the finest grid in FP64; beta = 0 for L, the shift for M.

@@ -286,11 +286,9 @@ __global__ void __launch_bounds__(LB) kacz_level_post_kernel(c2<T>* __restrict__
 }
 
 template <class T, class F2, class G, bool POST>
-__global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restrict__ uout, int po,
-                                                                  const c2<T>* __restrict__ uin, int pu,
-                                                                  const F2* __restrict__ f, int pf,
-                                                                  const T* __restrict__ kh, int pk, int n, T bA,
-                                                                  const int* __restrict__ stop, Inst bi) {
+__device__ __forceinline__ void tile_sweeps(c2<T>* __restrict__ uout, int po, const c2<T>* __restrict__ uin, int pu,
+                                            const F2* __restrict__ f, int pf, const T* __restrict__ kh, int pk, int n,
+                                            T bA, const int* __restrict__ stop, Inst bi) {
   using PR = PhaseRect<G, POST>;
   static_assert(PR::fits(), "phase rectangles must keep their supports inside the tile region");
   constexpr int TBK = G::TBK, RX = G::RX, RY = G::RY, REG = G::REG, KT = G::KT;
@@ -355,6 +353,33 @@ __global__ void __launch_bounds__(G::TBK) kacz_sweep_tile_kernel(c2<T>* __restri
     }
   }
 }
+
+// FP32 tiles are held to 56 registers a thread, so that a 1024-thread block leaves room for the
+// deferred solution update (k_update_x, one 128-thread block per SM) beside it; the FP64 tiles
+// (256 threads) need more.
+template <class F2, class G, bool POST>
+__global__ void __maxnreg__(56) kacz_sweep_tile_kernel(float2* __restrict__ uout, int po,
+                                                       const float2* __restrict__ uin, int pu,
+                                                       const F2* __restrict__ f, int pf, const float* __restrict__ kh,
+                                                       int pk, int n, float bA, const int* __restrict__ stop, Inst bi) {
+  tile_sweeps<float, F2, G, POST>(uout, po, uin, pu, f, pf, kh, pk, n, bA, stop, bi);
+}
+template <class G, bool POST>
+__global__ void __launch_bounds__(G::TBK) kacz_sweep_tile64_kernel(double2* __restrict__ uout, int po,
+                                                                   const double2* __restrict__ uin, int pu,
+                                                                   const double2* __restrict__ f, int pf,
+                                                                   const double* __restrict__ kh, int pk, int n,
+                                                                   double bA, const int* __restrict__ stop, Inst bi) {
+  tile_sweeps<double, double2, G, POST>(uout, po, uin, pu, f, pf, kh, pk, n, bA, stop, bi);
+}
+template <class T, class F2, class G, bool POST>
+struct TileKernel {
+  static constexpr auto fn = kacz_sweep_tile_kernel<F2, G, POST>;
+};
+template <class G, bool POST>
+struct TileKernel<double, double2, G, POST> {
+  static constexpr auto fn = kacz_sweep_tile64_kernel<G, POST>;
+};
 
 template <class T>
 size_t level_smem(int n) {
@@ -612,8 +637,8 @@ template <class T, class F2, class G, bool POST>
 cudaError_t tile_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kacz_sweep_tile_kernel<T, F2, G, POST>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<T, G>());
+  cudaError_t e = cudaFuncSetAttribute(TileKernel<T, F2, G, POST>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tile_smem<T, G>());
   if (!e) done = true;
   return e;
 }
@@ -625,10 +650,10 @@ cudaError_t tile_launch(void* uout, int po, const void* uin, int pu, const void*
   if (e) return e;
   dim3 grid((n + G::KT) / G::KT, (n + G::KT) / G::KT, bi.count);
   if (post)
-    pdl_launch(kacz_sweep_tile_kernel<T, F2, G, true>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
+    pdl_launch(TileKernel<T, F2, G, true>::fn, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
                (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop, bi);
   else
-    pdl_launch(kacz_sweep_tile_kernel<T, F2, G, false>, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
+    pdl_launch(TileKernel<T, F2, G, false>::fn, grid, G::TBK, tile_smem<T, G>(), s, (c2<T>*)uout, po,
                (const c2<T>*)uin, pu, (const F2*)f, pf, (const T*)kh, pk, n, (T)bA, stop, bi);
   return cudaGetLastError();
 }

@@ -42,6 +42,8 @@ __device__ __forceinline__ double2 ldy(const float2* p, int e) {
   float2 v = p[e];
   return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
 }
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
 // FP64 value rounded to FP32 for the FP32 V-cycle (integer pipe, see f64_to_f32).
 __device__ __forceinline__ float2 narrow(double2 v) { return make_float2(f64_to_f32(v.x), f64_to_f32(v.y)); }
 
@@ -120,6 +122,16 @@ __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket
 // (h^2 A y) at node (i, j) = flat index e of the finest grid (pitch n+1), A = L (beta = 0) or M.
 // The FP64 pipe bounds these kernels, so interior nodes of L take the real-diagonal path:
 // d = (kh)^2 - 4 (one FMA) and v = nb + d y (two FMAs); boundary nodes and M use the complex row.
+// Boundary rows and the shifted operator M: the complex diagonal. Out of line, so that the
+// compiler never evaluates this branch's FP64 arithmetic for interior nodes (it is taken by 4n of
+// (n+1)^2 nodes; with the branch if-converted the apply kernels were measured 1.65x slower).
+template <class Y2>
+__device__ __noinline__ double2 apply_row(const Y2* __restrict__ y, double k, int e, int sides, double beta,
+                                          double2 nb) {
+  double2 d = row_diag<double>(k, sides, beta);
+  return d2add(d2mul(d, ldy(y, e)), nb);
+}
+
 template <class Y2>
 __device__ __forceinline__ double2 apply_at(const Y2* __restrict__ y, const double* __restrict__ kh, int e, int i,
                                             int j, int n, double beta) {
@@ -127,13 +139,12 @@ __device__ __forceinline__ double2 apply_at(const Y2* __restrict__ y, const doub
   Nbr b = neighbours(i, j, n);
   double2 nb = d2add(d2add(ldy(y, j * w + b.iw), ldy(y, j * w + b.ie)), d2add(ldy(y, b.js * w + i), ldy(y, b.jn * w + i)));
   const double k = kh[e];
-  const double2 ye = ldy(y, e);
   if (b.sides == 0 && beta == 0.0) {
+    const double2 ye = ldy(y, e);
     const double dr = fma(k, k, -4.0);
     return make_double2(fma(dr, ye.x, nb.x), fma(dr, ye.y, nb.y));
   }
-  double2 d = row_diag<double>(k, b.sides, beta);
-  return d2add(d2mul(d, ye), nb);
+  return apply_row(y, k, e, b.sides, beta, nb);
 }
 
 // Grid-stride walk over the (n+1)^2 nodes that keeps (i, j) up to date without dividing per node.
@@ -227,6 +238,10 @@ __global__ void k_init_kernel(KrylovVecs k, double tol, int maxit, int hist_cap)
     st->alpha = make_double2(1, 0);
     st->omega = make_double2(1, 0);
     st->beta = make_double2(0, 0);
+    st->alpha_x = make_double2(0, 0);
+    st->omega_x = make_double2(0, 0);
+    st->xa = 0;
+    st->xw = 0;
     st->first = 1;
     st->half = 0;
     st->it = 1;
@@ -336,6 +351,8 @@ __global__ void k_apply_rv_kernel(KrylovVecs k, const Y2* __restrict__ y) {
       st->iters_x2 = 2 * (st->it - 1);
     } else {
       st->alpha = d2div(st->rho, rv);
+      st->alpha_x = st->alpha;  // x += alpha y is due (k_update_x, beside the next preconditioner application)
+      st->xa = 1;
     }
   }
 }
@@ -370,30 +387,13 @@ __global__ void k_update_s_kernel(KrylovVecs k) {
   }
 }
 
-// t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>. After a stop at the half step (the
-// second preconditioner application was skipped) it instead applies x += alpha y, once.
+// t = A z with <t, s> and <t, t>; omega = <t, s> / <t, t>.
 template <class Y2>
-__global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ y, const Y2* __restrict__ z) {
+__global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ z) {
   pdl_enter();
   k = instance(k);
-  y += blockIdx.z * k.sv;
   z += blockIdx.z * k.sv;
   KState* st = k.st;
-  if (st->half == 1) {
-    const double2 alpha = st->alpha;
-    const int N = (int)k.N;
-    GRID_STRIDE(e, N) { k.x[e] = d2axpy(k.x[e], alpha, ldy(y, e)); }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      unsigned int t = atomicAdd(&st->ticket[KT_XHALF], 1u);
-      if (t == gridDim.x - 1) {
-        st->half = 2;
-        st->ticket[KT_XHALF] = 0;
-      }
-    }
-    return;
-  }
   if (st->done) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const int N = (int)k.N;
@@ -422,21 +422,17 @@ __global__ void k_apply_ts_kernel(KrylovVecs k, const Y2* __restrict__ y, const 
   }
 }
 
-// x += alpha y + omega z, r = s - omega t, with <r^, r> and |r|^2; the next beta.
-template <class Y2>
-__global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const Y2* __restrict__ z) {
+// r = s - omega t with <r^, r> and |r|^2; the next beta. This step's solution update (x += alpha y
+// + omega z) is deferred to k_update_x.
+__global__ void k_update_r_kernel(KrylovVecs k) {
   pdl_enter();
   k = instance(k);
-  y += blockIdx.z * k.sv;
-  z += blockIdx.z * k.sv;
   KState* st = k.st;
   if (st->done) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const double2 alpha = st->alpha, omega = st->omega;
   const int N = (int)k.N;
   GRID_STRIDE(e, N) {
-    double2 x = d2axpy(d2axpy(k.x[e], alpha, ldy(y, e)), omega, ldy(z, e));
-    k.x[e] = x;
     double2 r = d2axmy(k.s[e], omega, k.t[e]);
     k.r[e] = r;
     double2 rh = k.rhat[e];
@@ -447,6 +443,8 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
   double tot[3];
   if (!grid_sum<3>(acc, k.partials, &st->ticket[KT_XR], tot)) return;
   if (threadIdx.x == 0) {
+    st->omega_x = omega;  // x += omega z is due (k_update_x, beside the next preconditioner application)
+    st->xw = 1;
     st->rr = tot[2];
     hist_push(st, k.hist, sqrt(tot[2] / st->bnorm2));
     double2 rho_new = make_double2(tot[0], tot[1]);
@@ -481,6 +479,50 @@ __global__ void k_update_xr_kernel(KrylovVecs k, const Y2* __restrict__ y, const
       st->beta = d2mul(d2div(rho_new, st->rho_old), d2div(alpha, omega));
       st->first = 0;
       st->it += 1;
+    }
+  }
+}
+
+// The deferred solution update, in two halves that keep the order of an immediate
+// x += alpha y + omega z (two FMA-based complex updates per node, alpha y first), so the bits do
+// not change: half A applies x += alpha y of the last step whose alpha was computed (KState::xa),
+// half W x += omega z of the last full step (xw). Half A runs on a side branch beside the next
+// step's first preconditioner application, which leaves x and y alone until its finest
+// post-smoothing pass (which waits for it) writes y; half W beside the second one, likewise
+// for z; after the last step both run once more, A first. One 128-thread block per SM with four
+// nodes in flight per thread: few threads and registers, leaving the SMs to the V-cycle kernels.
+constexpr int XB = 128;  // threads per block of k_update_x
+template <class Y2, bool W>
+__global__ void __launch_bounds__(XB, 8) k_update_x_kernel(KrylovVecs k, const Y2* __restrict__ yz) {
+  pdl_enter();
+  k = instance(k);
+  yz += blockIdx.z * k.sv;
+  KState* st = k.st;
+  int* flag = W ? &st->xw : &st->xa;
+  if (!*flag) return;
+  const double2 c = W ? st->omega_x : st->alpha_x;
+  const int N = (int)k.N, stride = gridDim.x * XB;
+  int e = blockIdx.x * XB + threadIdx.x;
+  for (; e + 3 * stride < N; e += 4 * stride) {
+    double2 x[4];
+    Y2 a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x[q] = k.x[e + q * stride];
+      a[q] = yz[e + q * stride];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) k.x[e + q * stride] = d2axpy(x[q], c, widen(a[q]));
+  }
+  for (; e < N; e += stride) k.x[e] = d2axpy(k.x[e], c, ldy(yz, e));
+  // the last block to finish clears the flag (every block has read it by then)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(&st->ticket[W ? KT_XW : KT_XA], 1u);
+    if (t == gridDim.x - 1) {
+      *flag = 0;
+      st->ticket[W ? KT_XW : KT_XA] = 0;
     }
   }
 }
@@ -586,13 +628,25 @@ cudaError_t launch_k_apply_rv(const KrylovVecs& k, cudaStream_t s) {
 }
 cudaError_t launch_k_update_s(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_s_kernel) }
 cudaError_t launch_k_apply_ts(const KrylovVecs& k, cudaStream_t s) {
-  if (k.z32) pdl_launch(k_apply_ts_kernel<float2>, KGRID, KB, 0, s, k, k.y32, k.z32);
-  else pdl_launch(k_apply_ts_kernel<double2>, KGRID, KB, 0, s, k, k.y, k.z);
+  if (k.z32) pdl_launch(k_apply_ts_kernel<float2>, KGRID, KB, 0, s, k, k.z32);
+  else pdl_launch(k_apply_ts_kernel<double2>, KGRID, KB, 0, s, k, k.z);
   return cudaGetLastError();
 }
-cudaError_t launch_k_update_xr(const KrylovVecs& k, cudaStream_t s) {
-  if (k.y32) pdl_launch(k_update_xr_kernel<float2>, KGRID, KB, 0, s, k, k.y32, k.z32);
-  else pdl_launch(k_update_xr_kernel<double2>, KGRID, KB, 0, s, k, k.y, k.z);
+cudaError_t launch_k_update_r(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_update_r_kernel) }
+cudaError_t launch_k_update_x(const KrylovVecs& k, bool omega_half, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || sms < 1) sms = 1;
+  }
+  const dim3 grid(sms, 1, k.batch);  // one block per SM: the V-cycle kernels beside it keep the rest
+  if (k.y32) {
+    if (omega_half) pdl_launch(k_update_x_kernel<float2, true>, grid, XB, 0, s, k, (const float2*)k.z32);
+    else pdl_launch(k_update_x_kernel<float2, false>, grid, XB, 0, s, k, (const float2*)k.y32);
+  } else {
+    if (omega_half) pdl_launch(k_update_x_kernel<double2, true>, grid, XB, 0, s, k, (const double2*)k.z);
+    else pdl_launch(k_update_x_kernel<double2, false>, grid, XB, 0, s, k, (const double2*)k.y);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_k_true_residual(const KrylovVecs& k, cudaStream_t s) { KLAUNCH(k_true_residual_kernel) }

@@ -21,7 +21,7 @@ namespace {
 constexpr int TAIL_THREADS = 1024;
 
 template <class T>
-__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, const int* __restrict__ stop, Inst bi) {
+__device__ __forceinline__ void tail_body(const TailArgs& A, const int* __restrict__ stop, const Inst& bi) {
   extern __shared__ __align__(16) unsigned char smem[];
   const c2<T>* fin = reinterpret_cast<const c2<T>*>(A.f_in) + blockIdx.z * bi.sf;
   c2<T>* uout = reinterpret_cast<c2<T>*>(A.u_out) + blockIdx.z * bi.so;
@@ -153,6 +153,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs A, co
     lvl::for_nodes(w, w * w, [&](int q, int i, int j) { uout[(long long)j * A.po + i] = U(0)[q]; });
 }
 
+// The FP32 tail is held to 56 registers a thread, so that its 1024-thread block fits beside the
+// deferred solution update (k_update_x, one 128-thread block per SM) that runs during the cycle.
+__global__ void __maxnreg__(56) tail_kernel32(const TailArgs A, const int* __restrict__ stop, Inst bi) {
+  tail_body<float>(A, stop, bi);
+}
+__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel64(const TailArgs A, const int* __restrict__ stop, Inst bi) {
+  tail_body<double>(A, stop, bi);
+}
+
 }  // namespace
 
 size_t tail_layout(bool fp32, TailArgs* A) {
@@ -199,16 +208,16 @@ cudaError_t launch_tail(bool fp32, const TailArgs& A, size_t smem, const int* st
   static bool ready[2] = {false, false};
   cudaError_t e;
   if (!ready[fp32]) {
-    e = fp32 ? cudaFuncSetAttribute(tail_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM)
-             : cudaFuncSetAttribute(tail_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM);
+    e = fp32 ? cudaFuncSetAttribute(tail_kernel32, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM)
+             : cudaFuncSetAttribute(tail_kernel64, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_MAX_SMEM);
     if (e) return e;
     ready[fp32] = true;
   }
   dim3 grid(1, 1, bi.count);
   if (fp32)
-    pdl_launch(tail_kernel<float>, grid, TAIL_THREADS, smem, s, A, stop, bi);
+    pdl_launch(tail_kernel32, grid, TAIL_THREADS, smem, s, A, stop, bi);
   else
-    pdl_launch(tail_kernel<double>, grid, TAIL_THREADS, smem, s, A, stop, bi);
+    pdl_launch(tail_kernel64, grid, TAIL_THREADS, smem, s, A, stop, bi);
   return cudaGetLastError();
 }
 
