@@ -186,6 +186,9 @@ PAPER_TABLE6 = ((15.0, 64), (30.0, 128), (60.0, 256), (120.0, 512), (240.0, 1024
 # The Table 6 wedge: the figure is missing; its caption puts k between k_ref and 2 k_ref and the
 # source at the middle of the upper boundary, so the layers read k_ref * {1, 1.5, 2} top to bottom.
 PAPER_WEDGE_FACTORS = (1.0, 1.5, 2.0)
+# Table 7: V-cycles with the ray correction used as a stand-alone solver, kh = 0.3125, centre source.
+PAPER_TABLE7 = ((20.0, 64), (40.0, 128), (80.0, 256), (160.0, 512))
+PAPER_TABLE7_CYCLES = {"hlm": (16, 16, 17, 18), "sl": (23, 34, 41, 48), "hyb": (26, 31, 37, 39)}
 
 
 def paper_table_workloads(tables=("table1", "table2", "table6"), variant: str = "hyb", max_n: int = 1 << 30):
@@ -210,6 +213,19 @@ def paper_table_workloads(tables=("table1", "table2", "table6"), variant: str = 
             col = f"k_ref={k:g}" if name == "table6" else f"k={k:g},h=1/{n}"
             out.append((name, col, Workload(f"{name}_n{n}_k{k:g}", n, k, kf, rhs, variant=variant, levels=0,
                                              tol=1e-7, meta=meta)))
+    return out
+
+
+def paper_table7_workloads(max_n: int = 1 << 30):
+    """The stand-alone cycle solves of Sec. 6, Table 7 (tolerance 1e-7, x0 = 0): constant k,
+    kh = 0.3125, unit source at the centre. Yields (column, Workload)."""
+    out = []
+    for k, n in PAPER_TABLE7:
+        if n > max_n:
+            continue
+        out.append((f"k={k:g}", Workload(f"table7_n{n}_k{k:g}", n, k, constant_k(n, k), centre_source_rhs(n, 1.0),
+                                         variant="hlm", levels=0, tol=1e-7,
+                                         meta={"medium": "constant k", "rhs": "unit source at (0.5, 0.5)"})))
     return out
 
 
