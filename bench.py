@@ -871,6 +871,63 @@ def run_tables(args):
     print(json.dumps({"tables": summary, "paper": paper, "tol": 1e-7, "maxit": args.tables_maxit}), flush=True)
 
 
+def run_table7(args):
+    """Sec. 6, Table 7 on the GPU: V-cycle plus ray correction as a stand-alone solver (relres 1e-7,
+    kh = 0.3125, centre source) for HLM-V, SL-V and HYB-V, FP64 and FP32 V-cycle forms (the ray
+    correction is FP64 in both). One JSON line per run with the cycle count beside the stored
+    oracle's and the paper's, the solve time, the ray set-up time and one V-cycle and one ray
+    correction timed alone (CUDA events on the library's stream, 20 launches after 3 untimed)."""
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    torch.cuda.set_device(0)
+    build.build()
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "table7_oracle.json")))
+    summary = {}
+    for ci, (col, wl) in enumerate(I.paper_table7_workloads(max_n=args.tables_max_n)):
+        rhs = torch.from_numpy(wl.rhs).cuda()
+        for variant in ("hlm", "sl", "hyb"):
+            for prec in ("fp64", "fp32"):
+                P = hz.Problem(wl.n, wl.kfield, 0.5, variant=variant, precision=prec, k_ref=wl.k_ref)
+                R = hz.Ray(P, wl.k_ref)
+                try:
+                    P.cycle_solve(rhs, R, tol=wl.tol, maxc=60, allow_fail=True)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, info, _ = P.cycle_solve(rhs, R, tol=wl.tol, maxc=60, allow_fail=True)
+                    torch.cuda.synchronize()
+                    ms = (time.perf_counter() - t0) * 1e3
+                    r = torch.randn(wl.n + 1, wl.n + 1, dtype=torch.complex128, device="cuda")
+                    x = torch.zeros_like(r)
+                    split = {}
+                    for name, fn in (("vcycle_ms", lambda: P.vcycle(r)), ("ray_correction_ms", lambda: R.correct(r, x))):
+                        for _ in range(3):
+                            fn()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        for _ in range(20):
+                            fn()
+                        e1.record()
+                        torch.cuda.synchronize()
+                        split[name] = round(e0.elapsed_time(e1) / 20, 4)
+                finally:
+                    setup_ms, m, unknowns = R.setup_ms, R.m, R.unknowns
+                    R.close()
+                    P.close()
+                cyc = info["cycles"] if info["status"] == 0 else None
+                ref = golden["oracle"][variant][ci]
+                print(json.dumps({"table": "table7", "column": col, "variant": variant, "precision": prec, "n": wl.n,
+                                  "ray_m": m, "ray_unknowns": unknowns, "cycles": cyc, "status": info["status"],
+                                  "oracle_cycles": ref["cycles"], "paper_cycles": golden["paper"][variant][ci],
+                                  "relres_true": info["relres_true"], "solve_ms": round(ms, 2),
+                                  "ms_per_cycle": round(ms / max(1, info["cycles"]), 3), **split,
+                                  "ray_setup_ms": round(setup_ms, 1)}), flush=True)
+                summary.setdefault(f"{variant} {prec}", []).append(cyc)
+    print(json.dumps({"table7": summary, "oracle": {v: [c["cycles"] for c in golden["oracle"][v]] for v in golden["oracle"]},
+                      "paper": golden["paper"], "tol": golden["tol"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -894,6 +951,8 @@ def main():
     ap.add_argument("--pass-variant", type=int, default=-1,
                     help="fused-pass form for --profile-case (-1: tile autotuner; 0: tiles; 1..8: streaming)")
     ap.add_argument("--tables", action="store_true", help="re-run the paper's Tables 1, 2 and 6 and exit")
+    ap.add_argument("--table7", action="store_true",
+                    help="re-run the paper's Table 7 (V-cycle plus ray correction as a solver) and exit")
     ap.add_argument("--tables-maxit", type=int, default=400)
     ap.add_argument("--tables-max-n", type=int, default=1024)
     ap.add_argument("--sweep-n", type=int, default=0,
@@ -901,6 +960,8 @@ def main():
     args = ap.parse_args()
     if args.tables:
         run_tables(args)
+    elif args.table7:
+        run_table7(args)
     elif args.sweep_n:
         run_sweep(args)
     elif args.profile_case:

@@ -361,6 +361,67 @@ hz_status hz_measure_fp64_rate(int iters, void* stream, double* tflops, double* 
 hz_status hz_apply_dot_noalloc(int n, const double* kh, double beta, const double* u, const double* w, double* v,
                                double* dot, void* stream);
 
+/* ---- Ray correction and the stand-alone cycle solver (Sec. 6, Table 7) ----
+ * The near-kernel error is written as sum_j exp(i k d_j . x) a_j(x) over the eight directions
+ * d_j = (cos j pi/4, sin j pi/4) with smooth ray functions a_j, which are approximated on a coarse
+ * ray grid (Sec. 6; the paper leaves the construction to [BL97]). Reading implemented here: the
+ * a_j are bilinear on the vertex grid of spacing H = m h, and the correction is the Galerkin
+ * projection  x += P (P^H A P)^{-1} P^H r,  where column 8 C + j of P is the bilinear hat of ray
+ * node C (C = J (n/m + 1) + I, node (I m, J m)) times the plane wave exp(i k_ref d_j . x), A = L^h
+ * of the problem and r = rhs - A x. All of it is complex FP64; P^H A P is assembled and factored on
+ * the device (block tridiagonal by rows of ray nodes, block LU with pivoted Gauss-Jordan inverses
+ * of the pivot blocks, one refinement step per solve). */
+typedef struct hz_ray hz_ray; /* opaque; created by hz_ray_create, freed by hz_ray_destroy */
+
+typedef struct {
+  int m;           /* ray grid factor: H = m h */
+  int nc;          /* ray cells per side, n / m */
+  int unknowns;    /* 8 (nc + 1)^2 */
+  double kH;       /* k_ref H */
+  size_t bytes;    /* device memory the ray correction holds */
+  double setup_ms; /* wall time of hz_ray_create's assembly and factorisation */
+} hz_ray_info;
+
+#define HZ_RAY_MAX_NC 128
+
+/* Build the ray correction of problem p (after hz_setup_hierarchy; uses p's stream and k field).
+ *  k_ref : wavenumber of the plane waves, > 0.
+ *  m     : ray grid factor, a power of two dividing n with 1 <= n / m <= HZ_RAY_MAX_NC; 0 = the
+ *          largest power of two with k_ref m h <= 2.5 (the paper's coarsest scale) that divides n
+ *          and leaves at least two ray cells.
+ *  out   : receives the object; destroy it before p (hz_ray_destroy waits for the device).
+ * Allocates its own device memory (hz_ray_info.bytes: six sets of (nc + 1) blocks of
+ * (8 (nc + 1))^2 complex128 and the plane-wave table, 8 (n+1)^2 complex128). Synchronises the
+ * stream. Returns HZ_EINVAL (bad k_ref or m), HZ_ENOTSETUP, HZ_ENOMEM, HZ_EBREAKDOWN (a pivot
+ * block of the ray operator is singular) or HZ_ECUDA. */
+hz_status hz_ray_create(hz_problem* p, double k_ref, int m, hz_ray** out);
+hz_status hz_ray_get_info(const hz_ray* r, hz_ray_info* info);
+
+/* g = P^H res (res: device (n+1)^2 complex128; g: device 8 (nc+1)^2 complex128, ordered 8 C + j). */
+hz_status hz_ray_restrict(hz_ray* r, const double* res, double* g);
+/* z = (P^H A P)^{-1} g (device, 8 (nc+1)^2 complex128 each, not aliased). */
+hz_status hz_ray_coarse_solve(hz_ray* r, const double* g, double* z);
+/* Copies of the assembled blocks of P^H A P (before factorisation): device buffers of
+ * (nc+1) * (8 (nc+1))^2 complex128 each, block J row-major; lower[J] couples ray row J with row
+ * J - 1 (lower[0] is zero), upper[J] with row J + 1 (upper[nc] is zero). Any pointer may be NULL. */
+hz_status hz_ray_blocks(hz_ray* r, double* lower, double* diag, double* upper);
+/* x += P (P^H A P)^{-1} P^H res (device (n+1)^2 complex128 each, not aliased). */
+hz_status hz_ray_correct(hz_ray* r, const double* res, double* x);
+void hz_ray_destroy(hz_ray* r);
+
+/* Table 7's stand-alone solver of L^h x = rhs from x = 0: every cycle adds the V-cycle of the
+ * residual (hz_vcycle; the hierarchy's variant and precision) and then, when ray is not NULL, the
+ * ray correction of the new residual; after each cycle the FP64 residual |rhs - L^h x| / |rhs| is
+ * read back and the solve stops when it is <= tol.
+ *  rhs, x  : device (n+1)^2 complex128, not aliased; x receives the last iterate.
+ *  history : host, capacity history_cap (may be NULL/0): the relative residual after each cycle.
+ *  info    : host, may be NULL; iterations = cycles, relres_true = the last relative residual.
+ * Returns HZ_OK, HZ_EMAXIT (maxc cycles, or the residual grew above 1e8 |rhs|: diverged),
+ * HZ_ENONFINITE, or an argument/allocation/CUDA error. Allocates 3 (n+1)^2 complex128 of scratch
+ * for the call; one right-hand side (batch 1). Synchronises the stream every cycle. */
+hz_status hz_cycle_solve(hz_problem* p, hz_ray* ray, const double* rhs, double* x, double tol, int maxc,
+                         double* history, int history_cap, hz_solve_info* info);
+
 /* Last error message on p (never NULL), and a name for a status code. */
 const char* hz_last_error(const hz_problem* p);
 const char* hz_status_string(int status);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libhz.so")
 SOURCES = ("hz_vcycle.cu", "hz_fused.cu", "hz_stream.cu", "hz_kaczmarz.cu", "hz_tail.cu", "hz_krylov.cu",
-           "hz_capi.cu", "hz_noalloc.cu", "hz_probe.cu", "hz_kgrid.cu")
+           "hz_capi.cu", "hz_noalloc.cu", "hz_probe.cu", "hz_kgrid.cu", "hz_ray.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -1,8 +1,10 @@
 // C ABI (include/hz.h): problem set-up, the level hierarchy of Sec. 5, the V-cycle driver, the
-// graph-replayed Bi-CGSTAB loop of Sec. 6, and the step entry points used by the tests.
+// graph-replayed Bi-CGSTAB loop of Sec. 6, the ray correction and stand-alone cycle solver of
+// Sec. 6 (Table 7), and the step entry points used by the tests.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -208,6 +210,18 @@ struct hz_problem {
   struct ProfRec { int kernel, level; cudaEvent_t ev; };
   std::vector<ProfRec>* prof = nullptr;
   bool prof_capture = false;  // prof events are recorded into a graph being captured
+};
+
+// Ray correction of one problem (hz_ray.cu): one device allocation holding the blocks, the
+// solve vectors and the plane-wave table.
+struct hz_ray {
+  hz_problem* P = nullptr;
+  double k = 0;
+  RayBlocks B{};
+  double2* ph = nullptr;  // 8 (n+1)^2: ph[j (n+1)^2 + p] = exp(i k d_j . x_p)
+  void* mem = nullptr;
+  size_t bytes = 0;
+  double setup_ms = 0;
 };
 
 namespace {
@@ -1414,11 +1428,7 @@ hz_status hz_get_level_info(const hz_problem* P, int level, hz_level_info* info)
   return HZ_OK;
 }
 
-hz_status hz_vcycle(hz_problem* P, const double* r, double* z) {
-  if (!P) return HZ_EINVAL;
-  if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
-  if (!r || !z || (const double*)r == z) return fail(P, HZ_EINVAL, "bad vcycle arguments");
-  StreamScope scope(P);
+static hz_status vcycle_dev(hz_problem* P, const double* r, double* z) {
   double h = 1.0 / P->n;
   if (P->plan.fp32) {
     CK(launch_import(true, P->kv.p32, P->n + 1, (const double2*)r, P->n + 1, P->n, h * h, P->stream));
@@ -1429,6 +1439,14 @@ hz_status hz_vcycle(hz_problem* P, const double* r, double* z) {
     CK(run_vcycle(P, P->kv.p, z, nullptr));
   }
   return HZ_OK;
+}
+
+hz_status hz_vcycle(hz_problem* P, const double* r, double* z) {
+  if (!P) return HZ_EINVAL;
+  if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
+  if (!r || !z || (const double*)r == z) return fail(P, HZ_EINVAL, "bad vcycle arguments");
+  StreamScope scope(P);
+  return vcycle_dev(P, r, z);
 }
 
 hz_status hz_solve_batch(hz_problem* P, const double* rhs, double* x, double tol, int maxit, hz_solve_info* infos) {
@@ -1879,6 +1897,227 @@ const char* hz_status_string(int s) {
     case HZ_ETIMEOUT: return "HZ_ETIMEOUT";
     default: return "unknown";
   }
+}
+
+// ---------------------------------------------------------------- ray correction (Sec. 6, Table 7)
+
+// The ray grid factor of the reading: the largest power of two with k m h <= 2.5 that divides n
+// and leaves at least two ray cells.
+static int ray_rule(int n, double k) {
+  int m = 1;
+  while (n % (2 * m) == 0 && n / (2 * m) >= 2 && k * (2 * m) / n <= 2.5 * (1 + 1e-12)) m *= 2;
+  return m;
+}
+
+// Carves the ray correction's arrays out of `base` (null: sizes only); returns the bytes.
+static size_t ray_layout(int n, int m, RayBlocks* B, double2** ph, unsigned char* base) {
+  const int Nr = n / m + 1, Bs = 8 * Nr;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  const size_t blk = sizeof(double2) * (size_t)Bs * Bs * Nr, vec = sizeof(double2) * (size_t)Bs * Nr;
+  B->n = n;
+  B->m = m;
+  B->Nr = Nr;
+  B->Bs = Bs;
+  B->L = (double2*)take(blk);
+  B->D = (double2*)take(blk);
+  B->U = (double2*)take(blk);
+  B->Sinv = (double2*)take(blk);
+  B->G = (double2*)take(blk);
+  B->W = (double2*)take(blk);
+  B->g = (double2*)take(vec);
+  B->z = (double2*)take(vec);
+  B->y = (double2*)take(vec);
+  B->e = (double2*)take(vec);
+  B->dz = (double2*)take(vec);
+  B->fcol = (double2*)take(sizeof(double2) * Bs);
+  B->perm = (int*)take(sizeof(int) * Bs);
+  B->status = (int*)take(sizeof(int));
+  *ph = (double2*)take(sizeof(double2) * 8 * (size_t)(n + 1) * (n + 1));
+  return off;
+}
+
+static hz_status ray_build(hz_ray* R) {
+  hz_problem* P = R->P;
+  const RayBlocks& B = R->B;
+  cudaStream_t s = P->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t blk = sizeof(double2) * (size_t)B.Bs * B.Bs * B.Nr;
+  CK(cudaMemsetAsync(B.L, 0, blk, s));
+  CK(cudaMemsetAsync(B.D, 0, blk, s));
+  CK(cudaMemsetAsync(B.U, 0, blk, s));
+  CK(cudaMemsetAsync(B.status, 0, sizeof(int), s));
+  CK(launch_ray_phases(R->ph, P->n, R->k, s));
+  CK(launch_ray_assemble(B, R->ph, P->kh64, s));
+  CK(ray_factor(B, s));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, B.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  R->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (bad) return fail(P, HZ_EBREAKDOWN, "ray correction: a pivot block of P^H A P is singular");
+  return HZ_OK;
+}
+
+hz_status hz_ray_create(hz_problem* P, double k_ref, int m, hz_ray** out) {
+  if (!P || !out) return HZ_EINVAL;
+  *out = nullptr;
+  if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
+  if (!(k_ref > 0) || !std::isfinite(k_ref)) return fail(P, HZ_EINVAL, "ray correction: k_ref must be positive and finite");
+  const int n = P->n;
+  if (m == 0) m = ray_rule(n, k_ref);
+  if (m < 1 || (m & (m - 1)) || n % m || n / m > HZ_RAY_MAX_NC)
+    return fail(P, HZ_EINVAL, "ray correction: m must be a power of two dividing n with n / m <= HZ_RAY_MAX_NC");
+  StreamScope scope(P);
+  hz_ray* R = new hz_ray;
+  R->P = P;
+  R->k = k_ref;
+  R->bytes = ray_layout(n, m, &R->B, &R->ph, nullptr);
+  if (cudaMalloc(&R->mem, R->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete R;
+    return fail(P, HZ_ENOMEM, "ray correction: device allocation refused");
+  }
+  ray_layout(n, m, &R->B, &R->ph, (unsigned char*)R->mem);
+  const hz_status st = ray_build(R);
+  if (st != HZ_OK) {
+    hz_ray_destroy(R);
+    return st;
+  }
+  *out = R;
+  return HZ_OK;
+}
+
+hz_status hz_ray_get_info(const hz_ray* R, hz_ray_info* info) {
+  if (!R || !info) return HZ_EINVAL;
+  info->m = R->B.m;
+  info->nc = R->B.Nr - 1;
+  info->unknowns = R->B.Bs * R->B.Nr;
+  info->kH = R->k * R->B.m / R->B.n;
+  info->bytes = R->bytes;
+  info->setup_ms = R->setup_ms;
+  return HZ_OK;
+}
+
+hz_status hz_ray_restrict(hz_ray* R, const double* res, double* g) {
+  if (!R) return HZ_EINVAL;
+  hz_problem* P = R->P;
+  if (!res || !g || (const double*)g == res) return fail(P, HZ_EINVAL, "bad ray restriction arguments");
+  StreamScope scope(P);
+  CK(launch_ray_restrict((double2*)g, (const double2*)res, R->ph, R->B.n, R->B.m, P->stream));
+  return HZ_OK;
+}
+
+hz_status hz_ray_coarse_solve(hz_ray* R, const double* g, double* z) {
+  if (!R) return HZ_EINVAL;
+  hz_problem* P = R->P;
+  if (!g || !z || (const double*)z == g) return fail(P, HZ_EINVAL, "bad ray solve arguments");
+  StreamScope scope(P);
+  CK(ray_coarse_solve(R->B, (double2*)z, (const double2*)g, P->stream));
+  return HZ_OK;
+}
+
+hz_status hz_ray_blocks(hz_ray* R, double* lower, double* diag, double* upper) {
+  if (!R) return HZ_EINVAL;
+  hz_problem* P = R->P;
+  StreamScope scope(P);
+  const size_t blk = sizeof(double2) * (size_t)R->B.Bs * R->B.Bs * R->B.Nr;
+  if (lower) CK(cudaMemcpyAsync(lower, R->B.L, blk, cudaMemcpyDeviceToDevice, P->stream));
+  if (diag) CK(cudaMemcpyAsync(diag, R->B.D, blk, cudaMemcpyDeviceToDevice, P->stream));
+  if (upper) CK(cudaMemcpyAsync(upper, R->B.U, blk, cudaMemcpyDeviceToDevice, P->stream));
+  return HZ_OK;
+}
+
+hz_status hz_ray_correct(hz_ray* R, const double* res, double* x) {
+  if (!R) return HZ_EINVAL;
+  hz_problem* P = R->P;
+  if (!res || !x || (const double*)x == res) return fail(P, HZ_EINVAL, "bad ray correction arguments");
+  StreamScope scope(P);
+  CK(ray_correct(R->B, (double2*)x, (const double2*)res, R->ph, P->stream));
+  return HZ_OK;
+}
+
+void hz_ray_destroy(hz_ray* R) {
+  if (!R) return;
+  if (R->mem) cudaFree(R->mem);  // waits for the device; touches no stream of the problem
+  delete R;
+}
+
+static hz_status cycle_run(hz_problem* P, hz_ray* R, const double2* b, double2* x, double tol, int maxc,
+                           double* history, int history_cap, hz_solve_info* info, unsigned char* mem) {
+  const long long N = (long long)(P->n + 1) * (P->n + 1);
+  cudaStream_t s = P->stream;
+  double2* r = (double2*)mem;
+  double2* v = r + N;
+  double2* z = v + N;
+  double* partials = (double*)(z + N);
+  double* nrm = partials + ray_reduction_blocks();
+  const double n2 = (double)P->n * P->n;
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * N, s));
+  CK(launch_ray_residual_norm(nullptr, b, nullptr, N, partials, nrm, s));
+  double b2 = 0, rr = 0;
+  CK(cudaMemcpyAsync(&b2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  hz_status st = b2 > 0 ? HZ_EMAXIT : HZ_OK;
+  int cycles = 0, hl = 0;
+  while (st == HZ_EMAXIT && cycles < maxc) {
+    ++cycles;
+    CK(launch_apply_fp64(v, x, P->kh64, P->n, 0.0, n2, s));
+    CK(launch_ray_residual_norm(r, b, v, N, partials, nrm, s));
+    const hz_status vs = vcycle_dev(P, (const double*)r, (double*)z);
+    if (vs != HZ_OK) return vs;
+    CK(launch_ray_axpy(x, z, N, s));
+    if (R) {
+      CK(launch_apply_fp64(v, x, P->kh64, P->n, 0.0, n2, s));
+      CK(launch_ray_residual_norm(r, b, v, N, partials, nrm, s));
+      CK(ray_correct(R->B, x, r, R->ph, s));
+    }
+    CK(launch_apply_fp64(v, x, P->kh64, P->n, 0.0, n2, s));
+    CK(launch_ray_residual_norm(r, b, v, N, partials, nrm, s));
+    double r2 = 0;
+    CK(cudaMemcpyAsync(&r2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rr = std::sqrt(r2 / b2);
+    if (history && hl < history_cap) history[hl] = rr;
+    ++hl;
+    if (!std::isfinite(rr)) st = HZ_ENONFINITE;
+    else if (rr <= tol) st = HZ_OK;
+    else if (rr > 1e8) break;  // diverged: reported as HZ_EMAXIT
+  }
+  if (info) {
+    info->iterations = cycles;
+    info->relres_true = rr;
+    info->history_len = std::min(hl, history_cap > 0 ? history_cap : 0);
+    info->status = st;
+    info->restarts = 0;
+  }
+  if (st == HZ_EMAXIT) return fail(P, st, rr > 1e8 ? "cycle solver diverged" : "cycle solver: maxc cycles without reaching tol");
+  if (st == HZ_ENONFINITE) return fail(P, st, "cycle solver: non-finite residual");
+  return HZ_OK;
+}
+
+hz_status hz_cycle_solve(hz_problem* P, hz_ray* R, const double* rhs, double* x, double tol, int maxc,
+                         double* history, int history_cap, hz_solve_info* info) {
+  if (!P) return HZ_EINVAL;
+  if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
+  if (P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: the cycle solver takes one right-hand side");
+  if (!rhs || !x || (const double*)x == rhs || maxc < 1 || !(tol >= 0))
+    return fail(P, HZ_EINVAL, "bad cycle-solve arguments");
+  if (R && R->P != P) return fail(P, HZ_EINVAL, "ray correction built for another problem");
+  StreamScope scope(P);
+  const size_t N = (size_t)(P->n + 1) * (P->n + 1);
+  unsigned char* mem = nullptr;
+  if (cudaMalloc(&mem, 3 * sizeof(double2) * N + sizeof(double) * (ray_reduction_blocks() + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(P, HZ_ENOMEM, "cycle solver: scratch allocation refused");
+  }
+  const hz_status st = cycle_run(P, R, (const double2*)rhs, (double2*)x, tol, maxc, history, history_cap, info, mem);
+  cudaStreamSynchronize(P->stream);
+  cudaFree(mem);
+  return st;
 }
 
 void hz_destroy(hz_problem* P) {

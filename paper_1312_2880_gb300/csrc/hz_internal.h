@@ -268,4 +268,33 @@ cudaError_t launch_k_restart(const KrylovVecs& k, cudaStream_t s);  // every ins
 cudaError_t launch_apply_fp64(double2* v, const double2* u, const double* kh, int n, double beta, double out_scale,
                               cudaStream_t s);
 
+// ---------------------------------------------------------------- ray correction (hz_ray.cu)
+
+// The Galerkin ray operator P^H A P in block-tridiagonal form and its block LU (hz_ray.cu): Nr
+// rows of ray nodes, Bs = 8 Nr unknowns per block row; every block array holds Nr row-major
+// Bs x Bs blocks (L[0] and U[Nr-1] unused), every vector Nr * Bs entries.
+struct RayBlocks {
+  int n = 0, m = 0, Nr = 0, Bs = 0;
+  double2 *L = nullptr, *D = nullptr, *U = nullptr;     // assembled blocks (kept)
+  double2 *Sinv = nullptr, *G = nullptr, *W = nullptr;  // S_J^{-1}, L_J S_{J-1}^{-1}, S_J^{-1} U_J
+  double2 *g = nullptr, *z = nullptr, *y = nullptr, *e = nullptr, *dz = nullptr;  // solve vectors
+  double2* fcol = nullptr;  // Bs: pivot column of the current Gauss-Jordan step
+  int* perm = nullptr;      // Bs: pivot rows of the current inversion
+  int* status = nullptr;    // device int: set to 1 by a zero or non-finite pivot column
+};
+cudaError_t launch_ray_phases(double2* ph, int n, double k, cudaStream_t s);
+cudaError_t launch_ray_assemble(const RayBlocks& B, const double2* ph, const double* kh, cudaStream_t s);
+cudaError_t launch_ray_restrict(double2* g, const double2* r, const double2* ph, int n, int m, cudaStream_t s);
+cudaError_t launch_ray_prolong_add(double2* x, const double2* z, const double2* ph, int n, int m, cudaStream_t s);
+cudaError_t ray_factor(const RayBlocks& B, cudaStream_t s);
+// z = (P^H A P)^{-1} g by block substitution and one refinement step (z aliases neither g nor B's vectors).
+cudaError_t ray_coarse_solve(const RayBlocks& B, double2* z, const double2* g, cudaStream_t s);
+// x += P (P^H A P)^{-1} P^H r.
+cudaError_t ray_correct(const RayBlocks& B, double2* x, const double2* r, const double2* ph, cudaStream_t s);
+// r = b - v (v null: r untouched) and *out = |r|^2 (|b|^2), through ray_reduction_blocks() partials.
+cudaError_t launch_ray_residual_norm(double2* r, const double2* b, const double2* v, long long N, double* partials,
+                                     double* out, cudaStream_t s);
+cudaError_t launch_ray_axpy(double2* x, const double2* z, long long N, cudaStream_t s);
+int ray_reduction_blocks();
+
 }  // namespace hz

@@ -48,6 +48,11 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("kernel", c_int), ("level", c_int), ("ms", ctypes.c_float)]
 
 
+class RayInfo(ctypes.Structure):
+    _fields_ = [("m", c_int), ("nc", c_int), ("unknowns", c_int), ("kH", c_double), ("bytes", c_size_t),
+                ("setup_ms", c_double)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", c_double), ("relres_true", c_double), ("history_len", c_int), ("status", c_int),
                 ("restarts", c_int)]
@@ -108,6 +113,14 @@ def lib() -> ctypes.CDLL:
         "hz_group_last_error": (ctypes.c_char_p, [c_void_p]),
         "hz_group_destroy": (None, [c_void_p]),
         "hz_measure_fp64_rate": (c_int, [c_int, c_void_p, dp, dp]),
+        "hz_ray_create": (c_int, [P, c_double, c_int, POINTER(c_void_p)]),
+        "hz_ray_get_info": (c_int, [c_void_p, POINTER(RayInfo)]),
+        "hz_ray_restrict": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "hz_ray_coarse_solve": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "hz_ray_blocks": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+        "hz_ray_correct": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "hz_ray_destroy": (None, [c_void_p]),
+        "hz_cycle_solve": (c_int, [P, c_void_p, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -292,6 +305,20 @@ class Problem:
              "restarts": info.restarts}
         return x, d, hist[: info.history_len].copy()
 
+    def cycle_solve(self, rhs, ray=None, tol: float = 1e-7, maxc: int = 100, x=None, history_cap: int = 1024,
+                    allow_fail: bool = False):
+        """Table 7's stand-alone solver (hz_cycle_solve): V-cycle, then the ray correction of ``ray``
+        (a :class:`Ray` of this problem, or None) per cycle. Returns (x, info dict, history ndarray)."""
+        self._stream()
+        x = self._empty() if x is None else x
+        hist = np.zeros(max(1, history_cap), dtype=np.float64)
+        info = SolveInfo()
+        st = lib().hz_cycle_solve(self._h, ray._h if ray is not None else None, _ptr(rhs), _ptr(x), tol, maxc,
+                                  hist.ctypes.data_as(POINTER(c_double)), history_cap, byref(info))
+        self._check(st, (HZ_OK, HZ_EMAXIT, HZ_ENONFINITE) if allow_fail else (HZ_OK,))
+        d = {"cycles": int(info.iterations), "relres_true": info.relres_true, "status": st}
+        return x, d, hist[: info.history_len].copy()
+
     def solve_batch(self, rhs, tol: float = 1e-6, maxit: int = 1000, x=None, allow_fail: bool = False):
         """All `batch` right-hand sides at once: rhs is a (batch, n+1, n+1) complex128 CUDA tensor.
         Returns (x, list of info dicts)."""
@@ -411,6 +438,67 @@ class Problem:
         u = self._empty(self.num_levels - 1)
         self._check(lib().hz_coarse_solve(self._h, _ptr(f), _ptr(u)))
         return u
+
+
+class Ray:
+    """Ray correction of a :class:`Problem` (hz_ray_create): the Galerkin plane-wave coarse problem of
+    Sec. 6 on the ray grid of factor ``m`` (0 = the kH <= 2.5 rule)."""
+
+    def __init__(self, problem: Problem, k_ref: float, m: int = 0):
+        problem._stream()
+        h = c_void_p()
+        problem._check(lib().hz_ray_create(problem._h, float(k_ref), int(m), byref(h)))
+        self._h = h
+        self.problem = problem
+        info = RayInfo()
+        problem._check(lib().hz_ray_get_info(h, byref(info)))
+        self.m, self.nc, self.unknowns = info.m, info.nc, info.unknowns
+        self.kH, self.bytes, self.setup_ms = info.kH, int(info.bytes), info.setup_ms
+
+    def _vec(self):
+        import torch
+
+        return torch.empty(self.unknowns, dtype=torch.complex128, device="cuda")
+
+    def restrict(self, r):
+        """P^H r: a complex128 CUDA vector of 8 (nc+1)^2 entries ordered 8 C + j."""
+        self.problem._stream()
+        g = self._vec()
+        self.problem._check(lib().hz_ray_restrict(self._h, _ptr(r), _ptr(g)))
+        return g
+
+    def coarse_solve(self, g):
+        self.problem._stream()
+        z = self._vec()
+        self.problem._check(lib().hz_ray_coarse_solve(self._h, _ptr(g), _ptr(z)))
+        return z
+
+    def blocks(self):
+        """The assembled (lower, diag, upper) blocks of P^H A P: (nc+1, Bs, Bs) complex128 CUDA tensors."""
+        import torch
+
+        self.problem._stream()
+        Bs = 8 * (self.nc + 1)
+        out = [torch.empty((self.nc + 1, Bs, Bs), dtype=torch.complex128, device="cuda") for _ in range(3)]
+        self.problem._check(lib().hz_ray_blocks(self._h, *[_ptr(t) for t in out]))
+        return tuple(out)
+
+    def correct(self, r, x):
+        """x += P (P^H A P)^{-1} P^H r, in place on x."""
+        self.problem._stream()
+        self.problem._check(lib().hz_ray_correct(self._h, _ptr(r), _ptr(x)))
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hz_ray_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Group:
