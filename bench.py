@@ -901,7 +901,9 @@ def run_table7(args):
                     r = torch.randn(wl.n + 1, wl.n + 1, dtype=torch.complex128, device="cuda")
                     x = torch.zeros_like(r)
                     split = {}
-                    for name, fn in (("vcycle_ms", lambda: P.vcycle(r)), ("ray_correction_ms", lambda: R.correct(r, x))):
+                    g = R.restrict(r)
+                    for name, fn in (("vcycle_ms", lambda: P.vcycle(r)), ("ray_correction_ms", lambda: R.correct(r, x)),
+                                     ("ray_restrict_ms", lambda: R.restrict(r)), ("ray_solve_ms", lambda: R.coarse_solve(g))):
                         for _ in range(3):
                             fn()
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -222,6 +222,8 @@ struct hz_ray {
   void* mem = nullptr;
   size_t bytes = 0;
   double setup_ms = 0;
+  // The ray solve B.z = (P^H A P)^{-1} B.g (about 4 (n/m + 1) chained launches) captured once.
+  cudaGraphExec_t solve_graph = nullptr;
 };
 
 namespace {
@@ -1957,9 +1959,26 @@ static hz_status ray_build(hz_ray* R) {
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, B.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  R->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (bad) return fail(P, HZ_EBREAKDOWN, "ray correction: a pivot block of P^H A P is singular");
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t ec = ray_coarse_solve(B, B.z, B.g, s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (ec != cudaSuccess) e = ec;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&R->solve_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(P, e, "capture of the ray solve");
+  R->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return HZ_OK;
+}
+
+// x += P (P^H A P)^{-1} P^H r through the internal vectors and the captured solve.
+static cudaError_t ray_apply(hz_ray* R, double2* x, const double2* r) {
+  cudaStream_t s = R->P->stream;
+  cudaError_t e = launch_ray_restrict(R->B.g, r, R->ph, R->B.n, R->B.m, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(R->solve_graph, s);
+  if (e == cudaSuccess) e = launch_ray_prolong_add(x, R->B.z, R->ph, R->B.n, R->B.m, s);
+  return e;
 }
 
 hz_status hz_ray_create(hz_problem* P, double k_ref, int m, hz_ray** out) {
@@ -2016,7 +2035,10 @@ hz_status hz_ray_coarse_solve(hz_ray* R, const double* g, double* z) {
   hz_problem* P = R->P;
   if (!g || !z || (const double*)z == g) return fail(P, HZ_EINVAL, "bad ray solve arguments");
   StreamScope scope(P);
-  CK(ray_coarse_solve(R->B, (double2*)z, (const double2*)g, P->stream));
+  const size_t bytes = sizeof(double2) * (size_t)R->B.Bs * R->B.Nr;
+  CK(cudaMemcpyAsync(R->B.g, g, bytes, cudaMemcpyDeviceToDevice, P->stream));
+  CK(cudaGraphLaunch(R->solve_graph, P->stream));
+  CK(cudaMemcpyAsync(z, R->B.z, bytes, cudaMemcpyDeviceToDevice, P->stream));
   return HZ_OK;
 }
 
@@ -2036,12 +2058,13 @@ hz_status hz_ray_correct(hz_ray* R, const double* res, double* x) {
   hz_problem* P = R->P;
   if (!res || !x || (const double*)x == res) return fail(P, HZ_EINVAL, "bad ray correction arguments");
   StreamScope scope(P);
-  CK(ray_correct(R->B, (double2*)x, (const double2*)res, R->ph, P->stream));
+  CK(ray_apply(R, (double2*)x, (const double2*)res));
   return HZ_OK;
 }
 
 void hz_ray_destroy(hz_ray* R) {
   if (!R) return;
+  if (R->solve_graph) cudaGraphExecDestroy(R->solve_graph);
   if (R->mem) cudaFree(R->mem);  // waits for the device; touches no stream of the problem
   delete R;
 }
@@ -2073,7 +2096,7 @@ static hz_status cycle_run(hz_problem* P, hz_ray* R, const double2* b, double2* 
     if (R) {
       CK(launch_apply_fp64(v, x, P->kh64, P->n, 0.0, n2, s));
       CK(launch_ray_residual_norm(r, b, v, N, partials, nrm, s));
-      CK(ray_correct(R->B, x, r, R->ph, s));
+      CK(ray_apply(R, x, r));
     }
     CK(launch_apply_fp64(v, x, P->kh64, P->n, 0.0, n2, s));
     CK(launch_ray_residual_norm(r, b, v, N, partials, nrm, s));

@@ -289,8 +289,6 @@ cudaError_t launch_ray_prolong_add(double2* x, const double2* z, const double2* 
 cudaError_t ray_factor(const RayBlocks& B, cudaStream_t s);
 // z = (P^H A P)^{-1} g by block substitution and one refinement step (z aliases neither g nor B's vectors).
 cudaError_t ray_coarse_solve(const RayBlocks& B, double2* z, const double2* g, cudaStream_t s);
-// x += P (P^H A P)^{-1} P^H r.
-cudaError_t ray_correct(const RayBlocks& B, double2* x, const double2* r, const double2* ph, cudaStream_t s);
 // r = b - v (v null: r untouched) and *out = |r|^2 (|b|^2), through ray_reduction_blocks() partials.
 cudaError_t launch_ray_residual_norm(double2* r, const double2* b, const double2* v, long long N, double* partials,
                                      double* out, cudaStream_t s);

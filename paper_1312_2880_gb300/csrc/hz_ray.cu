@@ -13,7 +13,8 @@
 // elimination with row pivoting; the solve keeps S_J^{-1}, G_J = L_J S_{J-1}^{-1} and
 // W_J = S_J^{-1} U_J, and runs one step of iterative refinement on the block residual.
 //
-// Kernels here are launched without programmatic serialization: each waits for its predecessor.
+// Every kernel here is launched with programmatic stream serialization and starts with pdl_enter()
+// (hz_common.cuh): it waits for its predecessor before reading anything.
 #include "hz_common.cuh"
 #include "hz_internal.h"
 
@@ -52,6 +53,7 @@ __device__ __forceinline__ double hat_w(int di, int dj, double rm) {
 
 // ph[j N + p] = exp(i k (d_x x + d_y y)) at node p = (i, jj), x = i h, y = jj h.
 __global__ void ray_phase_kernel(double2* ph, int n, double k) {
+  pdl_enter();
   const long long N = (long long)(n + 1) * (n + 1);
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 8 * N) return;
@@ -73,6 +75,7 @@ __global__ void ray_phase_kernel(double2* ph, int n, double k) {
 // the scaled 5-point rows with mirrored boundary neighbours (hz_common.cuh), times 1/h^2.
 __global__ void __launch_bounds__(256) ray_assemble_kernel(double2* Lb, double2* Db, double2* Ub, const double2* ph,
                                                            const double* kh, int n, int m) {
+  pdl_enter();
   const int nc = n / m, Nr = nc + 1, Bs = 8 * Nr;
   const long long Nc = (long long)Nr * Nr;
   const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -123,12 +126,16 @@ __global__ void __launch_bounds__(256) ray_assemble_kernel(double2* Lb, double2*
   }
 }
 
-// g[8 C + j] = sum over the hat of ray node C of hat(p) conj(ph_j[p]) r[p]   (g = P^H r)
+// g[8 C + j] = sum over the hat of ray node C of hat(p) conj(ph_j[p]) r[p]   (g = P^H r). One warp
+// per ray node (eight per block of 256 threads).
 __global__ void __launch_bounds__(256) ray_restrict_kernel(double2* g, const double2* r, const double2* ph, int n,
                                                            int m) {
+  pdl_enter();
   const int nc = n / m, Nr = nc + 1;
-  const int C = blockIdx.x;
-  const int I = C % Nr, J = C / Nr;
+  const long long C = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (C >= (long long)Nr * Nr) return;
+  const int I = (int)(C % Nr), J = (int)(C / Nr);
   const int i0 = max(0, I * m - m + 1), i1 = min(n, I * m + m - 1);
   const int j0 = max(0, J * m - m + 1), j1 = min(n, J * m + m - 1);
   const int wi = i1 - i0 + 1, cnt = wi * (j1 - j0 + 1);
@@ -137,37 +144,27 @@ __global__ void __launch_bounds__(256) ray_restrict_kernel(double2* g, const dou
   double ar[8], ai[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) ar[j] = ai[j] = 0.0;
-  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+  for (int q = lane; q < cnt; q += 32) {
     const int i = i0 + q % wi, jj = j0 + q / wi;
     const long long p = (long long)jj * (n + 1) + i;
     const double2 wr = zscale(r[p], hat_w(i - I * m, jj - J * m, rm));
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const double2 e = zmulc(ph[j * N + p], wr);
-      ar[j] += e.x;
-      ai[j] += e.y;
+      const double2 e = ph[j * N + p];
+      ar[j] = fma(e.x, wr.x, fma(e.y, wr.y, ar[j]));
+      ai[j] = fma(e.x, wr.y, fma(-e.y, wr.x, ai[j]));
     }
   }
-  __shared__ double red[8][16];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const double re = warp_sum(ar[j]), im = warp_sum(ai[j]);
-    if (lane == 0) {
-      red[warp][2 * j] = re;
-      red[warp][2 * j + 1] = im;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 16) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    reinterpret_cast<double*>(g + 8LL * C)[threadIdx.x] = s;
+    if (lane == j) g[8 * C + j] = make_double2(re, im);
   }
 }
 
 // x[p] += sum_j ph_j[p] * (bilinear interpolation of the ray function z_j at p)   (x += P z)
 __global__ void ray_prolong_add_kernel(double2* x, const double2* z, const double2* ph, int n, int m) {
+  pdl_enter();
   const long long N = (long long)(n + 1) * (n + 1);
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -197,6 +194,7 @@ __global__ void ray_prolong_add_kernel(double2* x, const double2* z, const doubl
 // 1 / pivot. A zero or non-finite pivot column sets *status = 1 (the inverse is then meaningless).
 __global__ void __launch_bounds__(1024) ray_gj_pivot_kernel(double2* S, int Bs, int k, double2* fcol, int* perm,
                                                             int* status) {
+  pdl_enter();
   __shared__ double sv[32];
   __shared__ int si[32];
   __shared__ int piv;
@@ -262,6 +260,7 @@ __global__ void __launch_bounds__(1024) ray_gj_pivot_kernel(double2* S, int Bs, 
 
 // Rows i != k: S[i][c] = (c == k ? 0 : S[i][c]) - fcol[i] S[k][c]  (row k is only read).
 __global__ void ray_gj_elim_kernel(double2* S, int Bs, int k, const double2* fcol) {
+  pdl_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (c >= Bs || i == k) return;
@@ -275,6 +274,7 @@ __global__ void ray_gj_elim_kernel(double2* S, int Bs, int k, const double2* fco
 
 // Undo the row interchanges on the inverse: columns k and perm[k] swapped, k = Bs-1 .. 0.
 __global__ void ray_gj_unpermute_kernel(double2* S, int Bs, const int* perm) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Bs) return;
   double2* row = S + (long long)i * Bs;
@@ -292,6 +292,7 @@ __global__ void ray_gj_unpermute_kernel(double2* S, int Bs, const int* perm) {
 // A 32 x 32 tile of C per block of 256 threads, each thread 2 x 2 entries, k in steps of 16.
 __global__ void __launch_bounds__(256) ray_gemm_kernel(double2* C, const double2* A, const double2* B, int Bs,
                                                        int acc) {
+  pdl_enter();
   __shared__ double2 As[32][17];
   __shared__ double2 Bsh[16][33];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -332,50 +333,83 @@ __global__ void __launch_bounds__(256) ray_gemm_kernel(double2* C, const double2
 }
 
 // out_b = base_b + sgn M_b x_b for b = blockIdx.y (M_b advances Bs^2 entries, the vectors Bs);
-// base may be null (zero) or equal to out; x aliases neither. One warp per row.
-__global__ void __launch_bounds__(128) ray_gemv_kernel(double2* out, const double2* base, const double2* M,
-                                                       const double2* x, int Bs, double sgn) {
-  const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (row >= Bs) return;
+// base may be null (zero) or equal to out; x aliases neither. One block of GEMV_THREADS per row
+// (blockIdx.x): GB300's FP64 pipe is narrow, so a row is spread over four warps to keep every SM
+// sub-partition busy, and each complex product is accumulated with four FMAs.
+constexpr int GEMV_THREADS = 128;
+__global__ void __launch_bounds__(GEMV_THREADS) ray_gemv_kernel(double2* out, const double2* base, const double2* M,
+                                                                const double2* x, int Bs, double sgn) {
+  pdl_enter();
+  const int row = blockIdx.x;
   const long long b = blockIdx.y;
   const double2* Mr = M + b * Bs * (long long)Bs + (long long)row * Bs;
   const double2* xb = x + b * Bs;
   double re = 0.0, im = 0.0;
-  for (int c = lane; c < Bs; c += 32) {
-    const double2 e = zmul(Mr[c], xb[c]);
-    re += e.x;
-    im += e.y;
+  for (int c0 = threadIdx.x; c0 < Bs; c0 += 4 * GEMV_THREADS) {
+    double2 a[4], v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + GEMV_THREADS * u;
+      a[u] = c < Bs ? Mr[c] : make_double2(0.0, 0.0);
+      v[u] = c < Bs ? xb[c] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      re = fma(a[u].x, v[u].x, re);
+      re = fma(-a[u].y, v[u].y, re);
+      im = fma(a[u].x, v[u].y, im);
+      im = fma(a[u].y, v[u].x, im);
+    }
   }
   re = warp_sum(re);
   im = warp_sum(im);
-  if (lane == 0) {
+  __shared__ double red[2][GEMV_THREADS / 32];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][warp] = re;
+    red[1][warp] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int w = 0; w < GEMV_THREADS / 32; ++w) {
+      sr += red[0][w];
+      si += red[1][w];
+    }
     const double2 o = base ? base[b * Bs + row] : make_double2(0.0, 0.0);
-    out[b * Bs + row] = make_double2(o.x + sgn * re, o.y + sgn * im);
+    out[b * Bs + row] = make_double2(o.x + sgn * sr, o.y + sgn * si);
   }
 }
 
-// e_J = g_J - (L_J z_{J-1} + D_J z_J + U_J z_{J+1}) for J = blockIdx.y. One warp per row.
+// e_J = g_J - (L_J z_{J-1} + D_J z_J + U_J z_{J+1}), one thread per row of the whole system. Row
+// 8 I + j of block row J couples only ray nodes I - 1 .. I + 1 of the three ray rows, so only those
+// 24 columns of each block are read (the others are zero by construction).
 __global__ void __launch_bounds__(128) ray_block_residual_kernel(double2* e, const double2* g, const double2* z,
                                                                  const double2* Lb, const double2* Db,
                                                                  const double2* Ub, int Bs, int Nr) {
-  const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (row >= Bs) return;
-  const int J = blockIdx.y;
-  const long long bs2 = (long long)Bs * Bs, off = (long long)J * bs2 + (long long)row * Bs;
+  pdl_enter();
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)Nr * Bs) return;
+  const int J = (int)(t / Bs), row = (int)(t % Bs), I = row / 8;
+  const int c0 = 8 * max(I - 1, 0), c1 = 8 * min(I + 2, Nr);
+  const long long off = (long long)J * Bs * Bs + (long long)row * Bs;
+  const double2* zJ = z + (long long)J * Bs;
   double re = 0.0, im = 0.0;
-  for (int c = lane; c < Bs; c += 32) {
-    double2 t = zmul(Db[off + c], z[(long long)J * Bs + c]);
-    if (J > 0) t = zadd(t, zmul(Lb[off + c], z[(long long)(J - 1) * Bs + c]));
-    if (J < Nr - 1) t = zadd(t, zmul(Ub[off + c], z[(long long)(J + 1) * Bs + c]));
-    re += t.x;
-    im += t.y;
+  for (int c = c0; c < c1; ++c) {
+    double2 q = zmul(Db[off + c], zJ[c]);
+    if (J > 0) q = zadd(q, zmul(Lb[off + c], zJ[c - Bs]));
+    if (J < Nr - 1) q = zadd(q, zmul(Ub[off + c], zJ[c + Bs]));
+    re += q.x;
+    im += q.y;
   }
-  re = warp_sum(re);
-  im = warp_sum(im);
-  if (lane == 0) {
-    const long long q = (long long)J * Bs + row;
-    e[q] = make_double2(g[q].x - re, g[q].y - im);
-  }
+  e[t] = make_double2(g[t].x - re, g[t].y - im);
+}
+
+__global__ void ray_copy_kernel(double2* dst, const double2* src, int cnt) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) dst[i] = src[i];
 }
 
 constexpr int RED_BLOCKS = 512, RED_THREADS = 256;
@@ -383,6 +417,7 @@ constexpr int RED_BLOCKS = 512, RED_THREADS = 256;
 // r = b - v and per-block partial sums of |r|^2 (v null: |b|^2 only, r untouched).
 __global__ void __launch_bounds__(RED_THREADS) ray_residual_norm_kernel(double2* r, const double2* b, const double2* v,
                                                                         long long N, double* partials) {
+  pdl_enter();
   double s = 0.0;
   for (long long p = blockIdx.x * (long long)RED_THREADS + threadIdx.x; p < N; p += (long long)RED_BLOCKS * RED_THREADS) {
     double2 t = b[p];
@@ -405,6 +440,7 @@ __global__ void __launch_bounds__(RED_THREADS) ray_residual_norm_kernel(double2*
 }
 
 __global__ void ray_sum_kernel(const double* partials, double* out) {
+  pdl_enter();
   __shared__ double red[RED_BLOCKS];
   for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) red[i] = partials[i];
   __syncthreads();
@@ -416,6 +452,7 @@ __global__ void ray_sum_kernel(const double* partials, double* out) {
 }
 
 __global__ void ray_axpy_kernel(double2* x, const double2* z, long long N) {
+  pdl_enter();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p < N) x[p] = zadd(x[p], z[p]);
 }
@@ -428,25 +465,23 @@ inline unsigned blocks_for(long long work, int threads) { return (unsigned)((wor
 
 cudaError_t launch_ray_phases(double2* ph, int n, double k, cudaStream_t s) {
   const long long work = 8LL * (n + 1) * (n + 1);
-  ray_phase_kernel<<<blocks_for(work, 256), 256, 0, s>>>(ph, n, k);
-  return cudaGetLastError();
+  return pdl_launch(ray_phase_kernel, dim3(blocks_for(work, 256)), dim3(256), 0, s, ph, n, k);
 }
 
 cudaError_t launch_ray_assemble(const RayBlocks& B, const double2* ph, const double* kh, cudaStream_t s) {
   const long long warps = 72LL * B.Nr * B.Nr;
-  ray_assemble_kernel<<<blocks_for(warps * 32, 256), 256, 0, s>>>(B.L, B.D, B.U, ph, kh, B.n, B.m);
-  return cudaGetLastError();
+  return pdl_launch(ray_assemble_kernel, dim3(blocks_for(warps * 32, 256)), dim3(256), 0, s, B.L, B.D, B.U, ph, kh,
+                    B.n, B.m);
 }
 
 cudaError_t launch_ray_restrict(double2* g, const double2* r, const double2* ph, int n, int m, cudaStream_t s) {
-  const int Nr = n / m + 1;
-  ray_restrict_kernel<<<Nr * Nr, 256, 0, s>>>(g, r, ph, n, m);
-  return cudaGetLastError();
+  const long long Nr = n / m + 1;
+  return pdl_launch(ray_restrict_kernel, dim3(blocks_for(32 * Nr * Nr, 256)), dim3(256), 0, s, g, r, ph, n, m);
 }
 
 cudaError_t launch_ray_prolong_add(double2* x, const double2* z, const double2* ph, int n, int m, cudaStream_t s) {
-  ray_prolong_add_kernel<<<blocks_for((long long)(n + 1) * (n + 1), 256), 256, 0, s>>>(x, z, ph, n, m);
-  return cudaGetLastError();
+  return pdl_launch(ray_prolong_add_kernel, dim3(blocks_for((long long)(n + 1) * (n + 1), 256)), dim3(256), 0, s, x,
+                    z, ph, n, m);
 }
 
 namespace {
@@ -454,43 +489,34 @@ namespace {
 cudaError_t gj_inverse(double2* S, int Bs, double2* fcol, int* perm, int* status, cudaStream_t s) {
   const dim3 eg(blocks_for(Bs, 128), Bs);
   for (int k = 0; k < Bs; ++k) {
-    ray_gj_pivot_kernel<<<1, 1024, 0, s>>>(S, Bs, k, fcol, perm, status);
-    ray_gj_elim_kernel<<<eg, 128, 0, s>>>(S, Bs, k, fcol);
+    cudaError_t e = pdl_launch(ray_gj_pivot_kernel, dim3(1), dim3(1024), 0, s, S, Bs, k, fcol, perm, status);
+    if (e == cudaSuccess) e = pdl_launch(ray_gj_elim_kernel, eg, dim3(128), 0, s, S, Bs, k, (const double2*)fcol);
+    if (e != cudaSuccess) return e;
   }
-  ray_gj_unpermute_kernel<<<blocks_for(Bs, 128), 128, 0, s>>>(S, Bs, perm);
-  return cudaGetLastError();
+  return pdl_launch(ray_gj_unpermute_kernel, dim3(blocks_for(Bs, 128)), dim3(128), 0, s, S, Bs, (const int*)perm);
 }
 
 cudaError_t gemm(double2* C, const double2* A, const double2* Bm, int Bs, int acc, cudaStream_t s) {
   const dim3 g(blocks_for(Bs, 32), blocks_for(Bs, 32));
-  ray_gemm_kernel<<<g, 256, 0, s>>>(C, A, Bm, Bs, acc);
-  return cudaGetLastError();
+  return pdl_launch(ray_gemm_kernel, g, dim3(256), 0, s, C, A, Bm, Bs, acc);
 }
 
 cudaError_t gemv(double2* out, const double2* base, const double2* M, const double2* x, int Bs, int batch, double sgn,
                  cudaStream_t s) {
-  const dim3 g(blocks_for(32LL * Bs, 128), batch);
-  ray_gemv_kernel<<<g, 128, 0, s>>>(out, base, M, x, Bs, sgn);
-  return cudaGetLastError();
+  return pdl_launch(ray_gemv_kernel, dim3(Bs, batch), dim3(GEMV_THREADS), 0, s, out, base, M, x, Bs, sgn);
 }
 
 // z = (block LU)^{-1} g; y is scratch of one vector.
 cudaError_t block_substitute(const RayBlocks& B, double2* z, const double2* g, double2* y, cudaStream_t s) {
   const int Bs = B.Bs, Nr = B.Nr;
   const long long bs2 = (long long)Bs * Bs;
-  cudaError_t e = cudaMemcpyAsync(y, g, sizeof(double2) * (size_t)Bs * Nr, cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return e;
-  for (int J = 1; J < Nr; ++J) {
-    e = gemv(y + (long long)J * Bs, y + (long long)J * Bs, B.G + J * bs2, y + (long long)(J - 1) * Bs, Bs, 1, -1.0, s);
-    if (e != cudaSuccess) return e;
-  }
-  e = gemv(z, nullptr, B.Sinv, y, Bs, Nr, 1.0, s);
-  if (e != cudaSuccess) return e;
-  for (int J = Nr - 2; J >= 0; --J) {
+  cudaError_t e = pdl_launch(ray_copy_kernel, dim3(blocks_for(Bs, 128)), dim3(128), 0, s, y, g, Bs);
+  for (int J = 1; J < Nr && e == cudaSuccess; ++J)
+    e = gemv(y + (long long)J * Bs, g + (long long)J * Bs, B.G + J * bs2, y + (long long)(J - 1) * Bs, Bs, 1, -1.0, s);
+  if (e == cudaSuccess) e = gemv(z, nullptr, B.Sinv, y, Bs, Nr, 1.0, s);
+  for (int J = Nr - 2; J >= 0 && e == cudaSuccess; --J)
     e = gemv(z + (long long)J * Bs, z + (long long)J * Bs, B.W + J * bs2, z + (long long)(J + 1) * Bs, Bs, 1, -1.0, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return e;
 }
 
 }  // namespace
@@ -517,32 +543,23 @@ cudaError_t ray_coarse_solve(const RayBlocks& B, double2* z, const double2* g, c
   cudaError_t e = block_substitute(B, z, g, B.y, s);
   if (e != cudaSuccess) return e;
   // one step of iterative refinement: z += (block LU)^{-1} (g - A_ray z)
-  ray_block_residual_kernel<<<dim3(blocks_for(32LL * B.Bs, 128), B.Nr), 128, 0, s>>>(B.e, g, z, B.L, B.D, B.U, B.Bs,
-                                                                                   B.Nr);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = block_substitute(B, B.dz, B.e, B.y, s)) != cudaSuccess) return e;
   const long long cnt = (long long)B.Bs * B.Nr;
-  ray_axpy_kernel<<<blocks_for(cnt, 256), 256, 0, s>>>(z, B.dz, cnt);
-  return cudaGetLastError();
-}
-
-cudaError_t ray_correct(const RayBlocks& B, double2* x, const double2* r, const double2* ph, cudaStream_t s) {
-  cudaError_t e = launch_ray_restrict(B.g, r, ph, B.n, B.m, s);
-  if (e != cudaSuccess) return e;
-  if ((e = ray_coarse_solve(B, B.z, B.g, s)) != cudaSuccess) return e;
-  return launch_ray_prolong_add(x, B.z, ph, B.n, B.m, s);
+  e = pdl_launch(ray_block_residual_kernel, dim3(blocks_for(cnt, 128)), dim3(128), 0, s, B.e, g, (const double2*)z,
+                 (const double2*)B.L, (const double2*)B.D, (const double2*)B.U, B.Bs, B.Nr);
+  if (e == cudaSuccess) e = block_substitute(B, B.dz, B.e, B.y, s);
+  if (e == cudaSuccess) e = pdl_launch(ray_axpy_kernel, dim3(blocks_for(cnt, 256)), dim3(256), 0, s, z, (const double2*)B.dz, cnt);
+  return e;
 }
 
 cudaError_t launch_ray_residual_norm(double2* r, const double2* b, const double2* v, long long N, double* partials,
                                      double* out, cudaStream_t s) {
-  ray_residual_norm_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(r, b, v, N, partials);
-  ray_sum_kernel<<<1, 256, 0, s>>>(partials, out);
-  return cudaGetLastError();
+  cudaError_t e = pdl_launch(ray_residual_norm_kernel, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, s, r, b, v, N, partials);
+  if (e == cudaSuccess) e = pdl_launch(ray_sum_kernel, dim3(1), dim3(256), 0, s, (const double*)partials, out);
+  return e;
 }
 
 cudaError_t launch_ray_axpy(double2* x, const double2* z, long long N, cudaStream_t s) {
-  ray_axpy_kernel<<<blocks_for(N, 256), 256, 0, s>>>(x, z, N);
-  return cudaGetLastError();
+  return pdl_launch(ray_axpy_kernel, dim3(blocks_for(N, 256)), dim3(256), 0, s, x, z, N);
 }
 
 int ray_reduction_blocks() { return RED_BLOCKS; }
