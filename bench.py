@@ -930,6 +930,36 @@ def run_table7(args):
                       "paper": golden["paper"], "tol": golden["tol"]}), flush=True)
 
 
+def run_ray_profile(args):
+    """One Table 7 column (k = RAY_PROFILE, HLM-V, FP32 V-cycle): ray set-up, then three ray
+    corrections of a seeded residual, each timed with CUDA events (the launches an ncu launch list
+    of this command sees after the set-up)."""
+    import torch
+
+    from paper_1312_2880_gb300 import build, hz
+
+    torch.cuda.set_device(0)
+    build.build()
+    wl = next(w for c, w in I.paper_table7_workloads() if c == f"k={args.ray_profile:g}")
+    P = hz.Problem(wl.n, wl.kfield, 0.5, variant="hlm", precision="fp32", k_ref=wl.k_ref)
+    R = hz.Ray(P, wl.k_ref)
+    g = torch.Generator().manual_seed(I.SEED_BASE + 7)
+    r = torch.randn(wl.n + 1, wl.n + 1, dtype=torch.complex128, generator=g).cuda()
+    x = torch.zeros_like(r)
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R.correct(r, x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(round(e0.elapsed_time(e1), 4))
+    print(json.dumps({"ray_profile": f"table7_n{wl.n}_k{wl.k_ref:g}", "m": R.m, "unknowns": R.unknowns,
+                      "setup_ms": round(R.setup_ms, 1), "correction_ms": ms}), flush=True)
+    R.close()
+    P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -955,6 +985,8 @@ def main():
     ap.add_argument("--tables", action="store_true", help="re-run the paper's Tables 1, 2 and 6 and exit")
     ap.add_argument("--table7", action="store_true",
                     help="re-run the paper's Table 7 (V-cycle plus ray correction as a solver) and exit")
+    ap.add_argument("--ray-profile", type=float, default=0.0,
+                    help="set up the ray correction of one Table 7 column (its k) and time three corrections")
     ap.add_argument("--tables-maxit", type=int, default=400)
     ap.add_argument("--tables-max-n", type=int, default=1024)
     ap.add_argument("--sweep-n", type=int, default=0,
@@ -964,6 +996,8 @@ def main():
         run_tables(args)
     elif args.table7:
         run_table7(args)
+    elif args.ray_profile:
+        run_ray_profile(args)
     elif args.sweep_n:
         run_sweep(args)
     elif args.profile_case:
