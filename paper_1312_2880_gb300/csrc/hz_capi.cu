@@ -386,19 +386,22 @@ bool kform_ok(const hz_problem* P, int l, int form) {
   return false;
 }
 // Default form: FP32 - one block if the level fits, else a cluster, else tiles; FP64 - a cluster
-// (the FP64 pipe of one SM bounds the one-block form), else colour launches (the tiles' 2.6x halo
-// recomputation is FP64 work). Measured per Bi-CGSTAB iteration (four level launches): FP32
-// n_l = 128 cluster 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64
-// cluster 206 us, colour launches 820 us; FP64 n_l = 1024 tiles 4.49 ms, colour launches 2.39 ms.
+// (the FP64 pipe of one SM bounds the one-block form), else tiles up to n_l = 512, else colour
+// launches (the tiles' halo recomputation is FP64 work, which outweighs the saved launches on the
+// largest levels). Measured per Bi-CGSTAB iteration (four level launches): FP32 n_l = 128 cluster
+// 118 us, tiles 247 us; n_l = 256 cluster 240 us, tiles 259 us; FP64 n_l = 64 cluster 206 us,
+// colour launches 820 us; FP64 in the n = 4096 solve's graph: n_l = 1024 tiles 2.67 ms, colour
+// launches 2.39 ms; n_l = 512 0.94 and 1.21 ms; n_l = 256 0.58 and 0.92 ms. All forms give the
+// same bits.
 int default_kform(const hz_problem* P, int l) {
   // FP32 levels of n_l >= 256 with a multiple of 4 sweeps: two sweeps per tiled launch beat the
   // cluster (config 3, n_l = 256: 0.13 ms per iteration against 0.23)
   if (P->plan.fp32 && kacz_tile_sweeps_per_launch(true, P->lv[l].n, P->lv[l].nu) == 2 &&
       !kacz_level_fits(true, P->lv[l].n) && kform_ok(P, l, HZ_KACZ_TILE))
     return HZ_KACZ_TILE;
-  const int order32[] = {HZ_KACZ_LEVEL, HZ_KACZ_CLUSTER, HZ_KACZ_TILE}, order64[] = {HZ_KACZ_CLUSTER};
+  const int order32[] = {HZ_KACZ_LEVEL, HZ_KACZ_CLUSTER, HZ_KACZ_TILE}, order64[] = {HZ_KACZ_CLUSTER, HZ_KACZ_TILE};
   const int* o = P->plan.fp32 ? order32 : order64;
-  const int cnt = P->plan.fp32 ? 3 : 1;
+  const int cnt = P->plan.fp32 ? 3 : (P->lv[l].n <= 512 ? 2 : 1);
   for (int q = 0; q < cnt; ++q)
     if (kform_ok(P, l, o[q])) return o[q];
   return HZ_KACZ_COLOUR;

@@ -158,6 +158,18 @@ def test_fp64_form_defaults_to_the_cluster():
         P.close()
 
 
+def test_fp64_form_takes_tiles_on_levels_the_cluster_cannot_hold():
+    # the random medium at n = 2048 (config 3's kh): Kaczmarz levels 512, 256 (tiles) and 128 (cluster)
+    wl = I.grf_n4096(n=2048, k=500.0)
+    P = hzmod().Problem(wl.n, wl.kfield, 0.5, variant="hyb", precision="fp64", levels=wl.levels, k_ref=wl.k_ref)
+    try:
+        forms = {d["n"]: d["kacz_form"] for d in P.schedule() if d["smoother"] == "kaczmarz" and not d["in_tail"]}
+        assert forms.get(512) == "tile" and forms.get(256) == "tile", forms
+        assert forms.get(128, "cluster") == "cluster", forms
+    finally:
+        P.close()
+
+
 @pytest.mark.parametrize("form,precision", [("cluster", "fp32"), ("cluster", "fp64"), ("level", "fp32"),
                                             ("level", "fp64"), ("tile", "fp32"), ("colour", "fp64")])
 def test_batched_solves_equal_single_solves(form, precision):
