@@ -384,6 +384,11 @@ typedef struct {
 
 #define HZ_RAY_MAX_NC 128
 
+/* The ray grid factor hz_ray_create takes for m = 0: the largest power of two m with
+ * k_ref m / n <= 2.5 that divides n and leaves n / m >= 2 (1 if none larger does). Host only;
+ * 0 for n < 2 or a non-positive or non-finite k_ref. */
+int hz_ray_spacing(int n, double k_ref);
+
 /* Build the ray correction of problem p (after hz_setup_hierarchy; uses p's stream and k field).
  *  k_ref : wavenumber of the plane waves, > 0.
  *  m     : ray grid factor, a power of two dividing n with 1 <= n / m <= HZ_RAY_MAX_NC; 0 = the

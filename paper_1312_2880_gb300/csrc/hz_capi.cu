@@ -1984,6 +1984,11 @@ static cudaError_t ray_apply(hz_ray* R, double2* x, const double2* r) {
   return e;
 }
 
+int hz_ray_spacing(int n, double k_ref) {
+  if (n < 2 || !(k_ref > 0) || !std::isfinite(k_ref)) return 0;
+  return ray_rule(n, k_ref);
+}
+
 hz_status hz_ray_create(hz_problem* P, double k_ref, int m, hz_ray** out) {
   if (!P || !out) return HZ_EINVAL;
   *out = nullptr;

@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
         "hz_group_destroy": (None, [c_void_p]),
         "hz_measure_fp64_rate": (c_int, [c_int, c_void_p, dp, dp]),
         "hz_ray_create": (c_int, [P, c_double, c_int, POINTER(c_void_p)]),
+        "hz_ray_spacing": (c_int, [c_int, c_double]),
         "hz_ray_get_info": (c_int, [c_void_p, POINTER(RayInfo)]),
         "hz_ray_restrict": (c_int, [c_void_p, c_void_p, c_void_p]),
         "hz_ray_coarse_solve": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -438,6 +439,11 @@ class Problem:
         u = self._empty(self.num_levels - 1)
         self._check(lib().hz_coarse_solve(self._h, _ptr(f), _ptr(u)))
         return u
+
+
+def ray_spacing(n: int, k_ref: float) -> int:
+    """The ray grid factor of the kH <= 2.5 rule (hz_ray_spacing; host only)."""
+    return int(lib().hz_ray_spacing(int(n), float(k_ref)))
 
 
 class Ray:

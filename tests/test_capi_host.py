@@ -115,3 +115,14 @@ def test_noalloc_rejects_overlapping_outputs_before_any_device_call(L):
     assert call(kh, u, w, v, u) == hz.HZ_EINVAL  # dot inside u
     assert call(kh, u, w, v, w + 8) == hz.HZ_EINVAL  # dot straddles w
     assert call(kh, u, w, v, kh) == hz.HZ_EINVAL  # dot inside kh
+
+
+def test_ray_grid_rule_matches_the_oracle(L):
+    # the library's host rule for hz_ray_create's m = 0 against oracle.ray_spacing, over the Table 7
+    # columns and grids whose power-of-two factors are cut short by divisibility or the two-cell floor
+    cases = [(n, k) for k, n in I.PAPER_TABLE7]
+    cases += [(n, kh * n) for n in (2, 3, 4, 6, 12, 16, 24, 48, 96, 100, 640, 1024, 4096)
+              for kh in (0.01, 0.156, 0.2, 0.3125, 0.625, 1.25, 2.5, 3.0)]
+    for n, k in cases:
+        assert hz.ray_spacing(n, k) == o.ray_spacing(n, k), (n, k)
+    assert hz.ray_spacing(1, 1.0) == 0 and hz.ray_spacing(64, 0.0) == 0 and hz.ray_spacing(64, float("inf")) == 0

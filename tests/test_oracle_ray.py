@@ -132,3 +132,17 @@ def test_table7_cycle_counts_do_not_grow_with_k(variant):
         assert res.status == "converged"
         counts.append(res.cycles)
     assert counts[1] <= counts[0] + 1
+
+
+def test_cycle_solver_with_an_exact_cycle_stops_after_one(monkeypatch):
+    # with the V-cycle replaced by the exact inverse, the first cycle reaches the solution (the ray
+    # correction of a zero residual adds nothing), so the loop must stop after one cycle
+    import oracle.ray as R
+    import scipy.sparse.linalg as spla
+
+    _, w = I.paper_table7_workloads(max_n=64)[0]
+    A = o.helmholtz_matrix(w.n, w.kfield)
+    lu = spla.splu(A.tocsc())
+    monkeypatch.setattr(R, "vcycle", lambda h, r: lu.solve(r))
+    res = o.cycle_solve(A, w.rhs.ravel(), None, o.ray_setup(A, w.n, w.k_ref), tol=1e-10, maxc=5)
+    assert res.status == "converged" and res.cycles == 1 and res.history[0] <= 1e-12
