@@ -389,17 +389,24 @@ typedef struct {
  * 0 for n < 2 or a non-positive or non-finite k_ref. */
 int hz_ray_spacing(int n, double k_ref);
 
+/* Device bytes of the ray correction of an n-interval grid (m = 0: the factor hz_ray_spacing
+ * gives for k_ref): six sets of (nc + 1) blocks of (8 (nc + 1))^2 complex128, the plane-wave table
+ * (8 (n+1)^2 complex128) and a few ray vectors; 0 for an invalid n or m. */
+size_t hz_ray_footprint_bytes(int n, double k_ref, int m);
+
 /* Build the ray correction of problem p (after hz_setup_hierarchy; uses p's stream and k field).
  *  k_ref : wavenumber of the plane waves, > 0.
  *  m     : ray grid factor, a power of two dividing n with 1 <= n / m <= HZ_RAY_MAX_NC; 0 = the
  *          largest power of two with k_ref m h <= 2.5 (the paper's coarsest scale) that divides n
- *          and leaves at least two ray cells.
+ *          and leaves at least two ray cells (hz_ray_spacing).
+ *  arena : device buffer of at least hz_ray_footprint_bytes bytes, 256-byte aligned, owned by the
+ *          caller and kept alive until hz_ray_destroy; NULL = the library allocates it with
+ *          cudaMalloc and frees it in hz_ray_destroy.
  *  out   : receives the object; destroy it before p (hz_ray_destroy waits for the device).
- * Allocates its own device memory (hz_ray_info.bytes: six sets of (nc + 1) blocks of
- * (8 (nc + 1))^2 complex128 and the plane-wave table, 8 (n+1)^2 complex128). Synchronises the
- * stream. Returns HZ_EINVAL (bad k_ref or m), HZ_ENOTSETUP, HZ_ENOMEM, HZ_EBREAKDOWN (a pivot
- * block of the ray operator is singular) or HZ_ECUDA. */
-hz_status hz_ray_create(hz_problem* p, double k_ref, int m, hz_ray** out);
+ * Synchronises the stream. Returns HZ_EINVAL (bad k_ref, m or arena alignment), HZ_ENOTSETUP,
+ * HZ_ENOMEM (arena too small or allocation refused), HZ_EBREAKDOWN (a pivot block of the ray
+ * operator is singular) or HZ_ECUDA. */
+hz_status hz_ray_create(hz_problem* p, double k_ref, int m, void* arena, size_t arena_bytes, hz_ray** out);
 hz_status hz_ray_get_info(const hz_ray* r, hz_ray_info* info);
 
 /* g = P^H res (res: device (n+1)^2 complex128; g: device 8 (nc+1)^2 complex128, ordered 8 C + j). */
@@ -414,18 +421,25 @@ hz_status hz_ray_blocks(hz_ray* r, double* lower, double* diag, double* upper);
 hz_status hz_ray_correct(hz_ray* r, const double* res, double* x);
 void hz_ray_destroy(hz_ray* r);
 
+/* Bytes of scratch hz_cycle_solve needs for an n-interval grid (three (n+1)^2 complex128 vectors
+ * and the reduction partials); 0 for n outside [2, 32768]. */
+size_t hz_cycle_scratch_bytes(int n);
+
 /* Table 7's stand-alone solver of L^h x = rhs from x = 0: every cycle adds the V-cycle of the
  * residual (hz_vcycle; the hierarchy's variant and precision) and then, when ray is not NULL, the
  * ray correction of the new residual; after each cycle the FP64 residual |rhs - L^h x| / |rhs| is
  * read back and the solve stops when it is <= tol.
  *  rhs, x  : device (n+1)^2 complex128, not aliased; x receives the last iterate.
+ *  scratch : device buffer of at least hz_cycle_scratch_bytes(n) bytes, 256-byte aligned, owned
+ *            by the caller; NULL = the library allocates and frees it within the call.
  *  history : host, capacity history_cap (may be NULL/0): the relative residual after each cycle.
  *  info    : host, may be NULL; iterations = cycles, relres_true = the last relative residual.
  * Returns HZ_OK, HZ_EMAXIT (maxc cycles, or the residual grew above 1e8 |rhs|: diverged),
- * HZ_ENONFINITE, or an argument/allocation/CUDA error. Allocates 3 (n+1)^2 complex128 of scratch
- * for the call; one right-hand side (batch 1). Synchronises the stream every cycle. */
+ * HZ_ENONFINITE, or an argument/allocation/CUDA error. One right-hand side (batch 1).
+ * Synchronises the stream every cycle. */
 hz_status hz_cycle_solve(hz_problem* p, hz_ray* ray, const double* rhs, double* x, double tol, int maxc,
-                         double* history, int history_cap, hz_solve_info* info);
+                         void* scratch, size_t scratch_bytes, double* history, int history_cap,
+                         hz_solve_info* info);
 
 /* Last error message on p (never NULL), and a name for a status code. */
 const char* hz_last_error(const hz_problem* p);

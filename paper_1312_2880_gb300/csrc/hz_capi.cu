@@ -220,6 +220,7 @@ struct hz_ray {
   RayBlocks B{};
   double2* ph = nullptr;  // 8 (n+1)^2: ph[j (n+1)^2 + p] = exp(i k d_j . x_p)
   void* mem = nullptr;
+  bool own_mem = false;  // mem allocated by the library (no caller arena)
   size_t bytes = 0;
   double setup_ms = 0;
   // The ray solve B.z = (P^H A P)^{-1} B.g (about 4 (n/m + 1) chained launches) captured once.
@@ -1989,24 +1990,43 @@ int hz_ray_spacing(int n, double k_ref) {
   return ray_rule(n, k_ref);
 }
 
-hz_status hz_ray_create(hz_problem* P, double k_ref, int m, hz_ray** out) {
+static bool ray_factor_ok(int n, int m) { return n >= 2 && m >= 1 && !(m & (m - 1)) && n % m == 0 && n / m <= HZ_RAY_MAX_NC; }
+
+size_t hz_ray_footprint_bytes(int n, double k_ref, int m) {
+  if (m == 0) m = hz_ray_spacing(n, k_ref);
+  if (!ray_factor_ok(n, m)) return 0;
+  RayBlocks B;
+  double2* ph = nullptr;
+  return ray_layout(n, m, &B, &ph, nullptr);
+}
+
+hz_status hz_ray_create(hz_problem* P, double k_ref, int m, void* arena, size_t arena_bytes, hz_ray** out) {
   if (!P || !out) return HZ_EINVAL;
   *out = nullptr;
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
   if (!(k_ref > 0) || !std::isfinite(k_ref)) return fail(P, HZ_EINVAL, "ray correction: k_ref must be positive and finite");
   const int n = P->n;
   if (m == 0) m = ray_rule(n, k_ref);
-  if (m < 1 || (m & (m - 1)) || n % m || n / m > HZ_RAY_MAX_NC)
+  if (!ray_factor_ok(n, m))
     return fail(P, HZ_EINVAL, "ray correction: m must be a power of two dividing n with n / m <= HZ_RAY_MAX_NC");
+  RayBlocks B0;
+  double2* ph0 = nullptr;
+  const size_t need = ray_layout(n, m, &B0, &ph0, nullptr);
+  if (arena && arena_bytes < need) return fail(P, HZ_ENOMEM, "ray arena smaller than hz_ray_footprint_bytes");
+  if (arena && ((uintptr_t)arena & 255)) return fail(P, HZ_EINVAL, "ray arena must be 256-byte aligned");
   StreamScope scope(P);
   hz_ray* R = new hz_ray;
   R->P = P;
   R->k = k_ref;
-  R->bytes = ray_layout(n, m, &R->B, &R->ph, nullptr);
-  if (cudaMalloc(&R->mem, R->bytes) != cudaSuccess) {
+  R->bytes = need;
+  if (arena) {
+    R->mem = arena;
+  } else if (cudaMalloc(&R->mem, R->bytes) != cudaSuccess) {
     cudaGetLastError();
     delete R;
     return fail(P, HZ_ENOMEM, "ray correction: device allocation refused");
+  } else {
+    R->own_mem = true;
   }
   ray_layout(n, m, &R->B, &R->ph, (unsigned char*)R->mem);
   const hz_status st = ray_build(R);
@@ -2073,7 +2093,8 @@ hz_status hz_ray_correct(hz_ray* R, const double* res, double* x) {
 void hz_ray_destroy(hz_ray* R) {
   if (!R) return;
   if (R->solve_graph) cudaGraphExecDestroy(R->solve_graph);
-  if (R->mem) cudaFree(R->mem);  // waits for the device; touches no stream of the problem
+  if (R->own_mem) cudaFree(R->mem);  // waits for the device; touches no stream of the problem
+  else if (R->mem) cudaDeviceSynchronize();  // the caller's arena may be reused once this returns
   delete R;
 }
 
@@ -2130,24 +2151,34 @@ static hz_status cycle_run(hz_problem* P, hz_ray* R, const double2* b, double2* 
   return HZ_OK;
 }
 
-hz_status hz_cycle_solve(hz_problem* P, hz_ray* R, const double* rhs, double* x, double tol, int maxc,
-                         double* history, int history_cap, hz_solve_info* info) {
+size_t hz_cycle_scratch_bytes(int n) {
+  if (n < 2 || n > 32768) return 0;
+  const size_t N = (size_t)(n + 1) * (n + 1);
+  return 3 * sizeof(double2) * N + sizeof(double) * (ray_reduction_blocks() + 2);
+}
+
+hz_status hz_cycle_solve(hz_problem* P, hz_ray* R, const double* rhs, double* x, double tol, int maxc, void* scratch,
+                         size_t scratch_bytes, double* history, int history_cap, hz_solve_info* info) {
   if (!P) return HZ_EINVAL;
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
   if (P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: the cycle solver takes one right-hand side");
   if (!rhs || !x || (const double*)x == rhs || maxc < 1 || !(tol >= 0))
     return fail(P, HZ_EINVAL, "bad cycle-solve arguments");
   if (R && R->P != P) return fail(P, HZ_EINVAL, "ray correction built for another problem");
+  const size_t need = hz_cycle_scratch_bytes(P->n);
+  if (scratch && scratch_bytes < need) return fail(P, HZ_ENOMEM, "scratch smaller than hz_cycle_scratch_bytes");
+  if (scratch && ((uintptr_t)scratch & 255)) return fail(P, HZ_EINVAL, "scratch must be 256-byte aligned");
   StreamScope scope(P);
-  const size_t N = (size_t)(P->n + 1) * (P->n + 1);
-  unsigned char* mem = nullptr;
-  if (cudaMalloc(&mem, 3 * sizeof(double2) * N + sizeof(double) * (ray_reduction_blocks() + 2)) != cudaSuccess) {
+  unsigned char* mem = (unsigned char*)scratch;
+  if (!mem && cudaMalloc(&mem, need) != cudaSuccess) {
     cudaGetLastError();
     return fail(P, HZ_ENOMEM, "cycle solver: scratch allocation refused");
   }
   const hz_status st = cycle_run(P, R, (const double2*)rhs, (double2*)x, tol, maxc, history, history_cap, info, mem);
-  cudaStreamSynchronize(P->stream);
-  cudaFree(mem);
+  if (!scratch) {
+    cudaStreamSynchronize(P->stream);
+    cudaFree(mem);
+  }
   return st;
 }
 

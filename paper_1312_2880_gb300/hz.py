@@ -113,7 +113,9 @@ def lib() -> ctypes.CDLL:
         "hz_group_last_error": (ctypes.c_char_p, [c_void_p]),
         "hz_group_destroy": (None, [c_void_p]),
         "hz_measure_fp64_rate": (c_int, [c_int, c_void_p, dp, dp]),
-        "hz_ray_create": (c_int, [P, c_double, c_int, POINTER(c_void_p)]),
+        "hz_ray_footprint_bytes": (c_size_t, [c_int, c_double, c_int]),
+        "hz_ray_create": (c_int, [P, c_double, c_int, c_void_p, c_size_t, POINTER(c_void_p)]),
+        "hz_cycle_scratch_bytes": (c_size_t, [c_int]),
         "hz_ray_spacing": (c_int, [c_int, c_double]),
         "hz_ray_get_info": (c_int, [c_void_p, POINTER(RayInfo)]),
         "hz_ray_restrict": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -121,7 +123,8 @@ def lib() -> ctypes.CDLL:
         "hz_ray_blocks": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
         "hz_ray_correct": (c_int, [c_void_p, c_void_p, c_void_p]),
         "hz_ray_destroy": (None, [c_void_p]),
-        "hz_cycle_solve": (c_int, [P, c_void_p, c_void_p, c_void_p, c_double, c_int, dp, c_int, POINTER(SolveInfo)]),
+        "hz_cycle_solve": (c_int, [P, c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p, c_size_t, dp, c_int,
+                                   POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -310,11 +313,17 @@ class Problem:
                     allow_fail: bool = False):
         """Table 7's stand-alone solver (hz_cycle_solve): V-cycle, then the ray correction of ``ray``
         (a :class:`Ray` of this problem, or None) per cycle. Returns (x, info dict, history ndarray)."""
+        import torch
+
         self._stream()
         x = self._empty() if x is None else x
+        nb = int(lib().hz_cycle_scratch_bytes(self.n))
+        if getattr(self, "_cycle_scratch", None) is None or self._cycle_scratch.numel() < nb:
+            self._cycle_scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
         hist = np.zeros(max(1, history_cap), dtype=np.float64)
         info = SolveInfo()
         st = lib().hz_cycle_solve(self._h, ray._h if ray is not None else None, _ptr(rhs), _ptr(x), tol, maxc,
+                                  c_void_p(self._cycle_scratch.data_ptr()), nb,
                                   hist.ctypes.data_as(POINTER(c_double)), history_cap, byref(info))
         self._check(st, (HZ_OK, HZ_EMAXIT, HZ_ENONFINITE) if allow_fail else (HZ_OK,))
         d = {"cycles": int(info.iterations), "relres_true": info.relres_true, "status": st}
@@ -450,10 +459,17 @@ class Ray:
     """Ray correction of a :class:`Problem` (hz_ray_create): the Galerkin plane-wave coarse problem of
     Sec. 6 on the ray grid of factor ``m`` (0 = the kH <= 2.5 rule)."""
 
-    def __init__(self, problem: Problem, k_ref: float, m: int = 0):
+    def __init__(self, problem: Problem, k_ref: float, m: int = 0, arena=None):
+        import torch
+
         problem._stream()
+        nb = int(lib().hz_ray_footprint_bytes(problem.n, float(k_ref), int(m)))
+        if nb == 0:
+            raise HzError(HZ_EINVAL, "invalid ray grid factor for this grid")
+        self.arena = arena if arena is not None else torch.empty(nb, dtype=torch.uint8, device="cuda")
         h = c_void_p()
-        problem._check(lib().hz_ray_create(problem._h, float(k_ref), int(m), byref(h)))
+        problem._check(lib().hz_ray_create(problem._h, float(k_ref), int(m), c_void_p(self.arena.data_ptr()), nb,
+                                           byref(h)))
         self._h = h
         self.problem = problem
         info = RayInfo()

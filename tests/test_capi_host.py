@@ -126,3 +126,23 @@ def test_ray_grid_rule_matches_the_oracle(L):
     for n, k in cases:
         assert hz.ray_spacing(n, k) == o.ray_spacing(n, k), (n, k)
     assert hz.ray_spacing(1, 1.0) == 0 and hz.ray_spacing(64, 0.0) == 0 and hz.ray_spacing(64, float("inf")) == 0
+
+
+def test_ray_footprint_and_cycle_scratch_sizes(L):
+    # six sets of (nc + 1) dense blocks of (8 (nc + 1))^2 complex128 dominate the ray arena; the
+    # plane-wave table is 8 (n + 1)^2 complex128
+    for k, n in I.PAPER_TABLE7:
+        m = o.ray_spacing(n, k)
+        Nr = n // m + 1
+        blocks = 6 * Nr * (8 * Nr) ** 2 * 16
+        waves = 8 * (n + 1) ** 2 * 16
+        got = L.hz_ray_footprint_bytes(n, k, 0)
+        assert got == L.hz_ray_footprint_bytes(n, k, m)
+        vectors = 5 * 8 * Nr * Nr * 16  # five ray vectors of Nr rows of 8 Nr unknowns
+        assert blocks + waves + vectors <= got <= blocks + waves + vectors + 64 * 1024
+    assert L.hz_ray_footprint_bytes(64, 20.0, 3) == 0  # not a power of two
+    assert L.hz_ray_footprint_bytes(64, 20.0, 128) == 0  # does not divide n
+    assert L.hz_ray_footprint_bytes(1024, 20.0, 4) == 0  # n / m above HZ_RAY_MAX_NC
+    n = 200
+    assert L.hz_cycle_scratch_bytes(n) >= 3 * 16 * (n + 1) ** 2
+    assert L.hz_cycle_scratch_bytes(1) == 0
