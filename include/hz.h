@@ -409,7 +409,8 @@ size_t hz_ray_footprint_bytes(int n, double k_ref, int m);
 hz_status hz_ray_create(hz_problem* p, double k_ref, int m, void* arena, size_t arena_bytes, hz_ray** out);
 hz_status hz_ray_get_info(const hz_ray* r, hz_ray_info* info);
 
-/* g = P^H res (res: device (n+1)^2 complex128; g: device 8 (nc+1)^2 complex128, ordered 8 C + j). */
+/* g = P^H res (res: device (n+1)^2 complex128; g: device 8 (nc+1)^2 complex128, ordered 8 C + j).
+ * Here and in the calls below an output that shares a byte with an input is refused (HZ_EINVAL). */
 hz_status hz_ray_restrict(hz_ray* r, const double* res, double* g);
 /* z = (P^H A P)^{-1} g (device, 8 (nc+1)^2 complex128 each, not aliased). */
 hz_status hz_ray_coarse_solve(hz_ray* r, const double* g, double* z);
@@ -429,9 +430,10 @@ size_t hz_cycle_scratch_bytes(int n);
  * residual (hz_vcycle; the hierarchy's variant and precision) and then, when ray is not NULL, the
  * ray correction of the new residual; after each cycle the FP64 residual |rhs - L^h x| / |rhs| is
  * read back and the solve stops when it is <= tol.
- *  rhs, x  : device (n+1)^2 complex128, not aliased; x receives the last iterate.
+ *  rhs, x  : device (n+1)^2 complex128 sharing no byte; x receives the last iterate.
  *  scratch : device buffer of at least hz_cycle_scratch_bytes(n) bytes, 256-byte aligned, owned
- *            by the caller; NULL = the library allocates and frees it within the call.
+ *            by the caller and sharing no byte with rhs or x; NULL = the library allocates and
+ *            frees it within the call.
  *  history : host, capacity history_cap (may be NULL/0): the relative residual after each cycle.
  *  info    : host, may be NULL; iterations = cycles, relres_true = the last relative residual.
  * Returns HZ_OK, HZ_EMAXIT (maxc cycles, or the residual grew above 1e8 |rhs|: diverged),

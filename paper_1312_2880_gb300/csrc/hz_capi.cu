@@ -1990,6 +1990,12 @@ int hz_ray_spacing(int n, double k_ref) {
   return ray_rule(n, k_ref);
 }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+static bool bytes_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
 static bool ray_factor_ok(int n, int m) { return n >= 2 && m >= 1 && !(m & (m - 1)) && n % m == 0 && n / m <= HZ_RAY_MAX_NC; }
 
 size_t hz_ray_footprint_bytes(int n, double k_ref, int m) {
@@ -2052,7 +2058,8 @@ hz_status hz_ray_get_info(const hz_ray* R, hz_ray_info* info) {
 hz_status hz_ray_restrict(hz_ray* R, const double* res, double* g) {
   if (!R) return HZ_EINVAL;
   hz_problem* P = R->P;
-  if (!res || !g || (const double*)g == res) return fail(P, HZ_EINVAL, "bad ray restriction arguments");
+  const size_t fb = sizeof(double2) * (size_t)(R->B.n + 1) * (R->B.n + 1), rb = sizeof(double2) * (size_t)R->B.Bs * R->B.Nr;
+  if (!res || !g || bytes_overlap(g, rb, res, fb)) return fail(P, HZ_EINVAL, "bad ray restriction arguments");
   StreamScope scope(P);
   CK(launch_ray_restrict((double2*)g, (const double2*)res, R->ph, R->B.n, R->B.m, P->stream));
   return HZ_OK;
@@ -2061,7 +2068,8 @@ hz_status hz_ray_restrict(hz_ray* R, const double* res, double* g) {
 hz_status hz_ray_coarse_solve(hz_ray* R, const double* g, double* z) {
   if (!R) return HZ_EINVAL;
   hz_problem* P = R->P;
-  if (!g || !z || (const double*)z == g) return fail(P, HZ_EINVAL, "bad ray solve arguments");
+  const size_t rb = sizeof(double2) * (size_t)R->B.Bs * R->B.Nr;
+  if (!g || !z || bytes_overlap(z, rb, g, rb)) return fail(P, HZ_EINVAL, "bad ray solve arguments");
   StreamScope scope(P);
   const size_t bytes = sizeof(double2) * (size_t)R->B.Bs * R->B.Nr;
   CK(cudaMemcpyAsync(R->B.g, g, bytes, cudaMemcpyDeviceToDevice, P->stream));
@@ -2084,7 +2092,8 @@ hz_status hz_ray_blocks(hz_ray* R, double* lower, double* diag, double* upper) {
 hz_status hz_ray_correct(hz_ray* R, const double* res, double* x) {
   if (!R) return HZ_EINVAL;
   hz_problem* P = R->P;
-  if (!res || !x || (const double*)x == res) return fail(P, HZ_EINVAL, "bad ray correction arguments");
+  const size_t fb = sizeof(double2) * (size_t)(R->B.n + 1) * (R->B.n + 1);
+  if (!res || !x || bytes_overlap(x, fb, res, fb)) return fail(P, HZ_EINVAL, "bad ray correction arguments");
   StreamScope scope(P);
   CK(ray_apply(R, (double2*)x, (const double2*)res));
   return HZ_OK;
@@ -2162,10 +2171,13 @@ hz_status hz_cycle_solve(hz_problem* P, hz_ray* R, const double* rhs, double* x,
   if (!P) return HZ_EINVAL;
   if (!P->setup) return fail(P, HZ_ENOTSETUP, "hz_setup_hierarchy has not been called");
   if (P->plan.batch != 1) return fail(P, HZ_EINVAL, "batched hierarchy: the cycle solver takes one right-hand side");
-  if (!rhs || !x || (const double*)x == rhs || maxc < 1 || !(tol >= 0))
-    return fail(P, HZ_EINVAL, "bad cycle-solve arguments");
-  if (R && R->P != P) return fail(P, HZ_EINVAL, "ray correction built for another problem");
+  const size_t fb = sizeof(double2) * (size_t)(P->n + 1) * (P->n + 1);
   const size_t need = hz_cycle_scratch_bytes(P->n);
+  if (!rhs || !x || bytes_overlap(x, fb, rhs, fb) || maxc < 1 || !(tol >= 0))
+    return fail(P, HZ_EINVAL, "bad cycle-solve arguments");
+  if (scratch && (bytes_overlap(scratch, need, x, fb) || bytes_overlap(scratch, need, rhs, fb)))
+    return fail(P, HZ_EINVAL, "cycle-solve scratch overlaps rhs or x");
+  if (R && R->P != P) return fail(P, HZ_EINVAL, "ray correction built for another problem");
   if (scratch && scratch_bytes < need) return fail(P, HZ_ENOMEM, "scratch smaller than hz_cycle_scratch_bytes");
   if (scratch && ((uintptr_t)scratch & 255)) return fail(P, HZ_EINVAL, "scratch must be 256-byte aligned");
   StreamScope scope(P);

@@ -215,4 +215,12 @@ def test_bad_ray_arguments_are_refused():
         with pytest.raises(hz.HzError) as ei:
             hz.Ray(P, k_ref, m)
         assert ei.value.status == hz.HZ_EINVAL
+    # outputs that share bytes with inputs are refused before anything is launched
+    R = hz.Ray(P, wl.k_ref)
+    r = dev(rand_c((wl.n + 1, wl.n + 1), 12))
+    for call in (lambda: R.correct(r, r), lambda: P.cycle_solve(r, R, x=r)):
+        with pytest.raises(hz.HzError) as ei:
+            call()
+        assert ei.value.status == hz.HZ_EINVAL
+    R.close()
     P.close()
