@@ -162,7 +162,8 @@ def test_table7_cycle_solve_matches_oracle(k, variant):
 
 @pytest.mark.parametrize("variant", ["hlm", "sl", "hyb"])
 def test_table7_every_column_takes_the_stored_oracle_cycle_count(variant):
-    # k = 20 .. 160 (n = 64 .. 512): the oracle's counts and histories from make_table7_oracle.py
+    # k = 20 .. 160 (n = 64 .. 512): the oracle's counts, histories and sampled solutions from
+    # make_table7_oracle.py
     from paper_1312_2880_gb300 import hz
 
     golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table7_oracle.json")))
@@ -174,6 +175,10 @@ def test_table7_every_column_takes_the_stored_oracle_cycle_count(variant):
         x, info, hist = P.cycle_solve(dev(wl.rhs), R, tol=wl.tol, maxc=60)
         assert info["status"] == hz.HZ_OK and info["cycles"] == ref["cycles"], col
         assert np.allclose(hist, ref["history"], rtol=1e-6, atol=0), col
+        # the solution on the stored lattice of nodes (every n/8-th node each way)
+        smp = np.array(ref["sampled"])
+        xs = x.cpu().numpy()[smp[:, 1].astype(int), smp[:, 0].astype(int)]
+        assert np.abs(xs - (smp[:, 2] + 1j * smp[:, 3])).max() <= 1e-8 * ref["max_abs_x"], col
         R.close()
         P.close()
 
